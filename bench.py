@@ -1,0 +1,291 @@
+#!/usr/bin/env python
+"""Benchmark of the 3D-FSR-l2-TV hot path (Algorithm 1 of arXiv:2010.15491) on GB300.
+
+Workload (256^3): HR 256x256x256 phantom of 200 random ellipsoids plus a smooth
+field of amplitude 0.1, Gaussian PSF sigma 1.5 (11^3 taps), decimation 2x2x2
+to a 128^3 LR volume, 40 dB noise.  One step = one solve through the C ABI:
+LR spectrum, Tikhonov start (tau 1e-2, nearest-neighbour prior), then 100
+ADMM-TV iterations (lambda 5e-4, rho 1e-2), FP32 with FP64 reductions.
+
+Metric: voxel*iterations per second = 256^3 * 100 * steps / time.  The
+working set (x, two dual buffers, Theta, Lambda, spectrum: ~0.65 GB) is far
+larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line on stdout (rank 0).  Under torchrun with N > 1 every rank solves
+its own replica (the single-volume path does not shard: replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ADMM-TV voxel·iters/s at 256³"
+UNIT = "voxel·iters/s"
+# algorithmic HBM bytes per voxel per launch of each ADMM-loop kernel (FP32,
+# half spectrum = 4 B/voxel); they sum to 80 B per voxel-iteration
+ALG_BYTES = {"tv": 32, "rfft_m_fwd": 8, "fft_n_fwd": 8, "fft_s": 16, "fft_n_inv": 8, "rfft_m_inv": 8}
+STEP_BYTES = 80
+
+
+def workload_desc(w):
+    return (f"{w.name}: HR {w.dims[0]}x{w.dims[1]}x{w.dims[2]}, d={w.dec[0]}x{w.dec[1]}x{w.dec[2]}, "
+            f"PSF sigma {w.sigma[0]} ({len(w.psf())}^3 taps), {w.n_ellipsoids} ellipsoids + field {w.field}, "
+            f"{w.snr_db:g} dB; Tikhonov tau {w.tau:g} (nearest-neighbour prior) + {w.iters} ADMM-TV iterations "
+            f"lambda {w.lam:g} rho {w.mu:g}")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(w, plan, torch):
+    """Phantom and PSF (seeded), y = DHx + n with the library's own forward operator."""
+    import numpy as np
+    from synth import noise_sigma
+    x_true = torch.tensor(w.phantom(), dtype=torch.float32, device="cuda")
+    y = plan.forward(x_true)
+    sig = noise_sigma(y.double().cpu().numpy(), w.snr_db)
+    y += torch.tensor(sig * w.noise(), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    del x_true
+    return y
+
+
+def cpu_baseline(w, y_host, iters=2):
+    """The FP64 oracle as it stands, timed on this host for `iters` ADMM-TV iterations."""
+    import oracle as O
+    psf = w.psf()
+    x0 = O.tikhonov(y_host, psf, w.dec, w.tau, O.nearest_neighbour(y_host, w.dec))
+    t = time.perf_counter()
+    O.admm_tv(y_host, psf, w.dec, w.lam, w.mu, iters, x0)
+    dt = time.perf_counter() - t
+    return {"value": w.voxels * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{iters} ADMM-TV iterations of the same 256^3 workload (Tikhonov start untimed), "
+                      f"{dt:.1f} s; numpy FFT, single thread; host has {os.cpu_count()} cores"}
+
+
+def run_reference(args, w, rank):
+    """--impl reference: the FP64 oracle on the host cores, one ADMM-TV iteration per step."""
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    from synth import noise_sigma
+    psf = w.psf()
+    x = w.phantom()
+    clean = O.forward(x, psf, w.dec)
+    y = clean + noise_sigma(clean, w.snr_db) * w.noise()
+    x0 = O.tikhonov(y, psf, w.dec, w.tau, O.nearest_neighbour(y, w.dec))
+    lam = O.otf(psf, x.shape)
+    state = {"x": x0, "u": O.grad(x0), "d": np.zeros((3,) + x.shape)}
+
+    def step():
+        th = O.grad_adj(state["u"] - state["d"])
+        state["x"] = O.admm_xstep(y, lam, th, w.mu, w.dec)
+        g = O.grad(state["x"])
+        state["u"] = O.shrink(g + state["d"], w.lam / w.mu)
+        state["d"] = state["d"] + g - state["u"]
+
+    for _ in range(args.warmup):
+        step()
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t
+    val = w.voxels * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_desc(w), "step": "one ADMM-TV iteration of the FP64 oracle"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} timed iterations at 256^3, numpy single thread"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, w, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2010_15491_gb300.build import build
+    import paper_2010_15491_gb300 as sr3d
+    build()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream()
+    plan = sr3d.Plan(w.dims, w.dec, w.psf(), "f32", stream=stream)
+    with torch.cuda.stream(stream):
+        y = make_inputs(w, plan, torch)
+        x = plan.empty_hr()
+
+    def step():
+        plan.admm_tv(y, x, w.lam, w.mu, w.iters, tau_init=w.tau)
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    plan.profile(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = ev0.elapsed_time(ev1)
+    prof = plan.profile_read()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * w.voxels * w.iters * args.steps / (ms / 1e3)
+    launches = sum(n for _, n in prof.values())
+
+    # end to end through the public host-buffer entry point: pinned host y in,
+    # x out, copies inside the timed region
+    yh = y.cpu().pin_memory()
+    xh = torch.empty(plan.hr_shape, dtype=torch.float32).pin_memory()
+    plan.profile(False)
+    plan.admm_tv_host(yh, xh, w.lam, w.mu, w.iters, tau_init=w.tau)
+    if world > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.admm_tv_host(yh, xh, w.lam, w.mu, w.iters, tau_init=w.tau)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * w.voxels * w.iters * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": yh.numel() * yh.element_size(),
+           "d2h_bytes_per_step": xh.numel() * xh.element_size()}
+
+    peak, peak_src = peaks()
+    kern = {}
+    for k, (kms, n) in prof.items():
+        if n:
+            kern[k] = {"launches": n, "ms_total": kms, "ms_per_launch": kms / n if kms else None}
+    timed = {k: v for k, v in kern.items() if k in ALG_BYTES and v["ms_per_launch"]}
+    dom = max(timed, key=lambda k: timed[k]["ms_total"])
+    per_launch_s = timed[dom]["ms_per_launch"] / 1e3
+    achieved = ALG_BYTES[dom] * w.voxels / per_launch_s / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                "alg_bytes_per_launch": ALG_BYTES[dom] * w.voxels,
+                "step_frac": value / world * STEP_BYTES / (peak * 1e9)}
+    if rank != 0:
+        plan.close()
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(w), "voxels": w.voxels, "iters_per_step": w.iters,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "working set ~0.65 GB > L2; no flush"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "kernels": kern}
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, y.double().cpu().numpy())
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    from synth import HEADLINE_256 as w
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, w, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    run_ours(args, w, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

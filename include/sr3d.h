@@ -1,0 +1,189 @@
+/*
+ * sr3d.h -- C ABI of the GB300 (sm_103a) library for the fast 3D single-image
+ * super-resolution method of Tuador, Pham, Michetti, Basarab and Kouame,
+ * "A Novel Fast 3D Single Image Super-Resolution Algorithm" (arXiv:2010.15491).
+ *
+ * Problem (Sec. II-A, eq. 1):  y = D H x + n.
+ *   x   HR volume, sizes (m_h, n_h, s_h), stored C-order as x[s][n][m]
+ *       (m fastest: the paper's lexicographic ordering).
+ *   y   LR volume, sizes (m_h/dr, n_h/dc, s_h/ds), stored y[s][n][m].
+ *   H   cyclic convolution with the PSF (eq. 2); the PSF centre tap, index
+ *       floor(p/2) per axis, sits at the origin of the circulant.
+ *   D   keeps sample 0 of every dr x dc x ds block (dr on m, dc on n, ds on s).
+ *
+ * Conventions shared by every entry point:
+ *   - Real arrays hold the plan's element type: float for SR3D_F32 plans,
+ *     double for SR3D_F64 plans.  Arguments named *_dev are device pointers
+ *     owned by the caller, contiguous, 16-byte aligned; *_host are host
+ *     pointers (pinned memory gives asynchronous copies).
+ *   - The ADMM dual variable d holds 3*N_h elements, component-major:
+ *     d[0..N_h) is the m-difference component, then n, then s
+ *     (L = [D_m; D_n; D_s], periodic forward differences).
+ *   - Every call is ordered on the plan's stream and returns after its result
+ *     is complete.  A plan is not thread-safe; distinct plans are.
+ *   - Return value: SR3D_OK (0) or a negative SR3D_ERR_* code; the message of
+ *     the last failure on the calling thread is sr3d_last_error().  On error
+ *     the outputs are unspecified; the plan stays usable unless the error is
+ *     SR3D_ERR_CUDA.
+ *
+ * Supported sizes: every HR size is 2^a or 3*2^a, m_h a multiple of 32, n_h a
+ * multiple of 8, 4 <= s_h, each HR size at most 2048; m_h/dr even;
+ * d = dr*dc*ds at most 8.
+ */
+#ifndef SR3D_H
+#define SR3D_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SR3D_OK                    0
+#define SR3D_ERR_INVALID_ARG      -1  /* NULL pointer, non-positive size or weight */
+#define SR3D_ERR_NOT_DIVISIBLE    -2  /* an HR size is not a multiple of its decimation factor */
+#define SR3D_ERR_UNSUPPORTED_SIZE -3  /* a size outside the supported set above */
+#define SR3D_ERR_SINGULAR         -4  /* sum of PSF taps is zero (ADMM DC class), or tau <= 0 */
+#define SR3D_ERR_CUDA             -5  /* a CUDA runtime call failed */
+#define SR3D_ERR_OOM              -6  /* device allocation failed */
+#define SR3D_ERR_TIMEOUT          -7  /* a bounded device wait ran out */
+#define SR3D_ERR_NUMERIC          -8  /* NaN or Inf in the objective / residual reductions */
+#define SR3D_ERR_NOT_CONVERGED    -9  /* tol > 0 and max_iters reached; x and d are still written */
+
+typedef struct sr3d_plan_s* sr3d_plan_t;
+
+typedef enum { SR3D_F32 = 0, SR3D_F64 = 1 } sr3d_dtype;
+
+/* Plan descriptor: the inputs of Algorithm 1 that do not change between
+ * solves (y, H and the decimation; Sec. II-A and Algorithm 1 "Input"). */
+typedef struct {
+  int m_h, n_h, s_h;        /* HR sizes */
+  int dr, dc, ds;           /* integer decimation factors, dividing m_h, n_h, s_h */
+  const double* psf;        /* host PSF taps, psf[p_s][p_n][p_m]; copied at plan time */
+  int p_m, p_n, p_s;        /* PSF sizes, 1 <= p_a <= HR size of axis a */
+  int dtype;                /* sr3d_dtype: element type of every real array */
+  void* stream;             /* cudaStream_t to run on; NULL = a stream the plan owns */
+} sr3d_desc;
+
+/* Statistics of sr3d_admm_tv.  Inputs: eval_every (evaluate the objective
+ * and residuals every k-th iteration; 0 = only after the last one),
+ * objective_hist (host array of hist_len doubles or NULL; entry i receives
+ * the objective at the i-th evaluation).  Outputs: the rest, at the last
+ * evaluation.  Residuals follow Boyd et al. (2011, Sec. 3.3) with A = L,
+ * B = -I: primal ||Lx - u||, dual mu ||L^T (u - u_prev)||; the relative
+ * values divide by max(||Lx||, ||u||) and mu ||L^T d||. */
+typedef struct {
+  int eval_every;
+  double* objective_hist;
+  int hist_len;
+  int iters;                /* iterations run */
+  int evals;                /* evaluations written */
+  double objective;         /* 1/2 ||y - DHx||^2 + lambda sum_j ||(Lx)_j||_2 */
+  double data_term;         /* 1/2 ||y - DHx||^2 */
+  double tv_term;           /* sum_j ||(Lx)_j||_2 */
+  double primal, dual;
+  double primal_rel, dual_rel;
+} sr3d_stats;
+
+/* Plan: computes Lambda = DFT(PSF) (Algorithm 1 step 1, eq. 2), the Laplacian
+ * symbol tables (steps 3-4) and FFT twiddles on the device, and allocates the
+ * work buffers.  *out receives the plan.  Errors: INVALID_ARG, NOT_DIVISIBLE,
+ * UNSUPPORTED_SIZE, OOM, CUDA. */
+int sr3d_plan(sr3d_plan_t* out, const sr3d_desc* desc);
+
+/* Frees the plan and everything it owns (safe with NULL). */
+int sr3d_destroy(sr3d_plan_t plan);
+
+/* Degradation operator of eq. (1) without noise: y_dev = D H x_dev
+ * (HR x in, LR y out).  Used to synthesise observations. */
+int sr3d_forward(sr3d_plan_t plan, const void* x_dev, void* y_dev);
+
+/* Sentinel for xbar_dev: the prior xbar is the nearest-neighbour replication
+ * of y (each LR voxel copied to its dr x dc x ds block). */
+#define SR3D_XBAR_NEAREST ((const void*)1)
+
+/* 3D-FSR-l2-l2 (Sec. III-A, eq. 12): x_dev = argmin_x 1/2 ||y - DHx||^2
+ * + tau/2 ||x - xbar||^2, tau = 2*lambda of eq. (5).  One batch of 3D FFT
+ * passes, the per-aliasing-class solve of eq. (12), one inverse 3D FFT.
+ * xbar_dev: NULL for xbar = 0, SR3D_XBAR_NEAREST, or a device HR array.
+ * Errors: INVALID_ARG (tau <= 0 or NULL y/x), CUDA. */
+int sr3d_tikhonov(sr3d_plan_t plan, const void* y_dev, const void* xbar_dev, double tau, void* x_dev);
+
+/* 3D-FSR-l2-TV (Sec. III-B, Algorithm 1): ADMM for
+ * min_x 1/2 ||y - DHx||^2 + lambda sum_j ||(Lx)_j||_2 with penalty rho (the
+ * paper's mu).  Each iteration: x-update by eq. (12) with Gamma weights
+ * (step 5a), isotropic soft threshold (5b), dual update (5c).
+ *   x_dev   in: x0 when tau_init <= 0; out: x after the last iteration.
+ *           With tau_init > 0, x0 = sr3d_tikhonov(y, SR3D_XBAR_NEAREST, tau_init).
+ *   d_dev   NULL: d0 = 0 and the final d is discarded; else in: d0, out: d.
+ *   u0 = L x0.  max_iters >= 0 iterations; tol > 0 stops early when both
+ *   relative residuals fall below tol (tested every max(1, eval_every)
+ *   iterations; NOT_CONVERGED if max_iters is reached first); tol <= 0 runs
+ *   exactly max_iters iterations.  stats may be NULL.
+ * Errors: INVALID_ARG, SINGULAR (sum of PSF taps zero), NUMERIC, CUDA,
+ * NOT_CONVERGED. */
+int sr3d_admm_tv(sr3d_plan_t plan, const void* y_dev, void* x_dev, void* d_dev,
+                 double lambda, double rho, int max_iters, double tol, double tau_init,
+                 sr3d_stats* stats);
+
+/* sr3d_admm_tv on host buffers: copies y_host (and x_host when
+ * tau_init <= 0) to plan-owned device buffers, solves, copies x back to
+ * x_host.  Same arguments and errors otherwise (d0 = 0, d discarded). */
+int sr3d_admm_tv_host(sr3d_plan_t plan, const void* y_host, void* x_host,
+                      double lambda, double rho, int max_iters, double tol, double tau_init,
+                      sr3d_stats* stats);
+
+/* Message of the last failure on the calling thread ("" if none). */
+const char* sr3d_last_error(void);
+
+/* ---- Diagnostic entry points: one step of the hot path each, for parity
+ * ---- tests against the oracle.  Same conventions as above. */
+
+/* Lambda (eq. 2) in natural half-spectrum layout:
+ * out_dev[k_s][k_n][k_m], k_m in [0, m_h/2], complex pairs (re, im) of the
+ * plan's element type, unnormalised DFT. */
+int sr3d_get_otf(sr3d_plan_t plan, void* out_dev);
+
+/* Unnormalised forward 3D DFT of the real HR x_dev, same layout as
+ * sr3d_get_otf. */
+int sr3d_fft3(sr3d_plan_t plan, const void* x_dev, void* out_dev);
+
+/* x-update of Algorithm 1 step 5a: x_dev = argmin 1/2||y - DHx||^2 +
+ * rho/2 ||Lx - (u - d)||^2 given theta_dev = L^T (u - d) (HR real). */
+int sr3d_xstep(sr3d_plan_t plan, const void* y_dev, const void* theta_dev, double rho, void* x_dev);
+
+/* Steps 5b-5c of Algorithm 1 followed by the next step's Theta:
+ * u = shrink(Lx + d_in, lambda/rho), d_out = d_in + Lx - u,
+ * theta_out = L^T (u - d_out).  d_in and d_out must not overlap. */
+int sr3d_tv_step(sr3d_plan_t plan, const void* x_dev, const void* d_in_dev, void* d_out_dev,
+                 double lambda, double rho, void* theta_out_dev);
+
+/* Per-kernel accounting.  Kernel kinds: SR3D_K_TV (fused u/d/Theta step),
+ * SR3D_K_RFFT_FWD / SR3D_K_RFFT_INV (real FFT along m), SR3D_K_FFTN_FWD /
+ * SR3D_K_FFTN_INV (FFT along n), SR3D_K_FFTS (FFT along s, with the class
+ * solve when solving), SR3D_K_OTHER (reductions, tables, copies),
+ * SR3D_K_SETUP (every launch of sr3d_admm_tv before its first iteration:
+ * LR spectrum, Tikhonov start, initial Theta).  Launches
+ * are always counted.  With sr3d_profile(plan, 1) every launch made by an
+ * entry point is also bracketed by CUDA events on the plan's stream and its
+ * duration added to its kind (events add a few microseconds per launch).
+ * sr3d_profile resets the totals; sr3d_profile_read copies them out
+ * (ms[k] in milliseconds, launches[k]) for k < SR3D_NKINDS. */
+#define SR3D_K_TV 0
+#define SR3D_K_RFFT_FWD 1
+#define SR3D_K_FFTN_FWD 2
+#define SR3D_K_FFTS 3
+#define SR3D_K_FFTN_INV 4
+#define SR3D_K_RFFT_INV 5
+#define SR3D_K_OTHER 6
+#define SR3D_K_SETUP 7
+#define SR3D_NKINDS 8
+int sr3d_profile(sr3d_plan_t plan, int on);
+int sr3d_profile_read(sr3d_plan_t plan, double ms[SR3D_NKINDS], long long launches[SR3D_NKINDS]);
+
+/* Plan facts for callers and tests: sizes[0..8] = m_h, n_h, s_h, m_l, n_l,
+ * s_l, m-slots, m-pitch, dtype; bytes = device memory the plan holds. */
+int sr3d_plan_info(sr3d_plan_t plan, int sizes[9], long long* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SR3D_H */

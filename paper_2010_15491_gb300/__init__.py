@@ -1,0 +1,277 @@
+"""GB300-native fast 3D single-image super-resolution (Tuador et al., arXiv:2010.15491).
+
+Thin Python binding of the C-ABI library libsr3d.so (include/sr3d.h).  It only
+marshals arguments: every step of the method runs in the library's CUDA
+kernels.  Device arrays are torch CUDA tensors (PyTorch provides device memory
+and streams); layouts follow the header: a volume with HR sizes (m, n, s) is a
+contiguous tensor of shape (s, n, m), the ADMM dual d has shape (3, s, n, m).
+
+Importing the package does not load the library; the first call does, and it
+raises if libsr3d.so has not been built (paper_2010_15491_gb300.build.build()).
+There is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libsr3d.so")
+
+SR3D_OK = 0
+ERRORS = {
+    -1: "INVALID_ARG", -2: "NOT_DIVISIBLE", -3: "UNSUPPORTED_SIZE", -4: "SINGULAR", -5: "CUDA",
+    -6: "OOM", -7: "TIMEOUT", -8: "NUMERIC", -9: "NOT_CONVERGED",
+}
+XBAR_NEAREST = ctypes.c_void_p(1)
+
+EXPORTED = [
+    "sr3d_plan", "sr3d_destroy", "sr3d_forward", "sr3d_tikhonov", "sr3d_admm_tv", "sr3d_admm_tv_host",
+    "sr3d_last_error", "sr3d_get_otf", "sr3d_fft3", "sr3d_xstep", "sr3d_tv_step", "sr3d_plan_info",
+    "sr3d_profile", "sr3d_profile_read",
+]
+KINDS = ["tv", "rfft_m_fwd", "fft_n_fwd", "fft_s", "fft_n_inv", "rfft_m_inv", "other", "setup"]
+
+
+class Sr3dError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+        self.name = ERRORS.get(code, str(code))
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("m_h", ctypes.c_int), ("n_h", ctypes.c_int), ("s_h", ctypes.c_int),
+                ("dr", ctypes.c_int), ("dc", ctypes.c_int), ("ds", ctypes.c_int),
+                ("psf", ctypes.POINTER(ctypes.c_double)),
+                ("p_m", ctypes.c_int), ("p_n", ctypes.c_int), ("p_s", ctypes.c_int),
+                ("dtype", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("eval_every", ctypes.c_int), ("objective_hist", ctypes.POINTER(ctypes.c_double)),
+                ("hist_len", ctypes.c_int), ("iters", ctypes.c_int), ("evals", ctypes.c_int),
+                ("objective", ctypes.c_double), ("data_term", ctypes.c_double), ("tv_term", ctypes.c_double),
+                ("primal", ctypes.c_double), ("dual", ctypes.c_double),
+                ("primal_rel", ctypes.c_double), ("dual_rel", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Loads libsr3d.so once; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built: run paper_2010_15491_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "sr3d_plan": (i, [ctypes.POINTER(vp), ctypes.POINTER(Desc)]),
+        "sr3d_destroy": (i, [vp]),
+        "sr3d_forward": (i, [vp, vp, vp]),
+        "sr3d_tikhonov": (i, [vp, vp, vp, d, vp]),
+        "sr3d_admm_tv": (i, [vp, vp, vp, vp, d, d, i, d, d, ctypes.POINTER(Stats)]),
+        "sr3d_admm_tv_host": (i, [vp, vp, vp, d, d, i, d, d, ctypes.POINTER(Stats)]),
+        "sr3d_last_error": (ctypes.c_char_p, []),
+        "sr3d_get_otf": (i, [vp, vp]),
+        "sr3d_fft3": (i, [vp, vp, vp]),
+        "sr3d_xstep": (i, [vp, vp, vp, d, vp]),
+        "sr3d_tv_step": (i, [vp, vp, vp, vp, d, d, vp]),
+        "sr3d_plan_info": (i, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
+        "sr3d_profile": (i, [vp, i]),
+        "sr3d_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int, allow=()):
+    if rc != SR3D_OK and rc not in allow:
+        raise Sr3dError(rc, load().sr3d_last_error().decode())
+    return rc
+
+
+def _ptr(t, dtype=None, shape: Optional[Sequence[int]] = None, device: bool = True) -> int:
+    """Device (or host) address of a contiguous torch tensor after checks."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    if device and not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not device and t.is_cuda:
+        raise ValueError("expected a host tensor")
+    return t.data_ptr()
+
+
+class Plan:
+    """One problem geometry: HR sizes dims = (m, n, s), decimation dec = (dr, dc, ds),
+    PSF taps psf of shape (p_s, p_n, p_m).  dtype "f32" or "f64"."""
+
+    def __init__(self, dims, dec, psf, dtype: str = "f32", stream=None):
+        import torch
+        self._torch = torch
+        L = load()
+        psf = np.ascontiguousarray(psf, dtype=np.float64)
+        if psf.ndim != 3:
+            raise ValueError("psf must be 3-D (p_s, p_n, p_m)")
+        self.dims = tuple(int(v) for v in dims)
+        self.dec = tuple(int(v) for v in dec)
+        self.dtype_name = dtype
+        self.tdtype = {"f32": torch.float32, "f64": torch.float64}[dtype]
+        m, n, s = self.dims
+        dr, dc, ds = self.dec
+        self.hr_shape = (s, n, m)
+        self.lr_shape = (s // ds, n // dc, m // dr)
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        desc = Desc(m, n, s, dr, dc, ds, psf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                    psf.shape[2], psf.shape[1], psf.shape[0], 0 if dtype == "f32" else 1,
+                    ctypes.c_void_p(handle) if handle else None)
+        self._psf_keep = psf
+        h = ctypes.c_void_p()
+        _check(L.sr3d_plan(ctypes.byref(h), ctypes.byref(desc)))
+        self._h = h
+
+    # -- helpers
+    def _hr(self, t):
+        return _ptr(t, self.tdtype, self.hr_shape)
+
+    def _lr(self, t):
+        return _ptr(t, self.tdtype, self.lr_shape)
+
+    def empty_hr(self):
+        return self._torch.empty(self.hr_shape, dtype=self.tdtype, device="cuda")
+
+    def empty_lr(self):
+        return self._torch.empty(self.lr_shape, dtype=self.tdtype, device="cuda")
+
+    def info(self):
+        sizes = (ctypes.c_int * 9)()
+        b = ctypes.c_longlong()
+        _check(load().sr3d_plan_info(self._h, sizes, ctypes.byref(b)))
+        keys = ["m_h", "n_h", "s_h", "m_l", "n_l", "s_l", "m_slots", "m_pitch", "dtype"]
+        out = dict(zip(keys, list(sizes)))
+        out["bytes"] = b.value
+        return out
+
+    def profile(self, on: bool = True):
+        """Resets the per-kernel accounting; with on=True also times every launch."""
+        _check(load().sr3d_profile(self._h, 1 if on else 0))
+
+    def profile_read(self):
+        """{kind: (milliseconds, launches)} since the last profile() call."""
+        ms = (ctypes.c_double * len(KINDS))()
+        n = (ctypes.c_longlong * len(KINDS))()
+        _check(load().sr3d_profile_read(self._h, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KINDS)}
+
+    # -- entry points
+    def forward(self, x, y=None):
+        """y = D H x (eq. 1 without noise)."""
+        y = self.empty_lr() if y is None else y
+        _check(load().sr3d_forward(self._h, self._hr(x), self._lr(y)))
+        return y
+
+    def tikhonov(self, y, tau: float, x=None, xbar=None):
+        """eq. (12); xbar None (zero prior), "nearest" or an HR tensor."""
+        x = self.empty_hr() if x is None else x
+        if isinstance(xbar, str):
+            if xbar != "nearest":
+                raise ValueError("xbar must be None, 'nearest' or a tensor")
+            xb = XBAR_NEAREST
+        else:
+            xb = self._hr(xbar) if xbar is not None else None
+        _check(load().sr3d_tikhonov(self._h, self._lr(y), xb, float(tau), self._hr(x)))
+        return x
+
+    def admm_tv(self, y, x, lam: float, rho: float, iters: int, d=None, tol: float = 0.0,
+                tau_init: float = 0.0, eval_every: int = -1, hist_len: int = 0):
+        """Algorithm 1.  Returns a dict of statistics when eval_every >= 0 or tol > 0, else None."""
+        st, hist = self._stats(eval_every, hist_len, tol)
+        dptr = _ptr(d, self.tdtype, (3,) + self.hr_shape) if d is not None else None
+        rc = load().sr3d_admm_tv(self._h, self._lr(y), self._hr(x), dptr, float(lam), float(rho), int(iters),
+                                 float(tol), float(tau_init), ctypes.byref(st) if st is not None else None)
+        _check(rc, allow=(-9,))
+        return self._stats_dict(st, hist, rc)
+
+    def admm_tv_host(self, y_host, x_host, lam: float, rho: float, iters: int, tol: float = 0.0,
+                     tau_init: float = 0.0, eval_every: int = -1, hist_len: int = 0):
+        """Algorithm 1 on host tensors (pinned for asynchronous copies)."""
+        st, hist = self._stats(eval_every, hist_len, tol)
+        rc = load().sr3d_admm_tv_host(self._h, _ptr(y_host, self.tdtype, self.lr_shape, device=False),
+                                      _ptr(x_host, self.tdtype, self.hr_shape, device=False), float(lam),
+                                      float(rho), int(iters), float(tol), float(tau_init),
+                                      ctypes.byref(st) if st is not None else None)
+        _check(rc, allow=(-9,))
+        return self._stats_dict(st, hist, rc)
+
+    def get_otf(self):
+        """Lambda in natural half-spectrum layout, complex tensor (s, n, m/2+1)."""
+        s, n, m = self.hr_shape
+        out = self._torch.empty((s, n, m // 2 + 1, 2), dtype=self.tdtype, device="cuda")
+        _check(load().sr3d_get_otf(self._h, out.data_ptr()))
+        return self._torch.view_as_complex(out)
+
+    def fft3(self, x):
+        s, n, m = self.hr_shape
+        out = self._torch.empty((s, n, m // 2 + 1, 2), dtype=self.tdtype, device="cuda")
+        _check(load().sr3d_fft3(self._h, self._hr(x), out.data_ptr()))
+        return self._torch.view_as_complex(out)
+
+    def xstep(self, y, theta, rho: float, x=None):
+        x = self.empty_hr() if x is None else x
+        _check(load().sr3d_xstep(self._h, self._lr(y), self._hr(theta), float(rho), self._hr(x)))
+        return x
+
+    def tv_step(self, x, d_in, lam: float, rho: float, d_out=None, theta=None):
+        d_out = self._torch.empty_like(d_in) if d_out is None else d_out
+        theta = self.empty_hr() if theta is None else theta
+        shp = (3,) + self.hr_shape
+        _check(load().sr3d_tv_step(self._h, self._hr(x), _ptr(d_in, self.tdtype, shp),
+                                   _ptr(d_out, self.tdtype, shp), float(lam), float(rho), self._hr(theta)))
+        return d_out, theta
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sr3d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- statistics marshalling
+    @staticmethod
+    def _stats(eval_every, hist_len, tol):
+        if eval_every < 0 and tol <= 0:
+            return None, None
+        hist = (ctypes.c_double * max(hist_len, 1))()
+        st = Stats(max(eval_every, 0), hist if hist_len > 0 else None, hist_len)
+        return st, hist
+
+    @staticmethod
+    def _stats_dict(st, hist, rc):
+        if st is None:
+            return None
+        out = {k: getattr(st, k) for k in ("iters", "evals", "objective", "data_term", "tv_term", "primal",
+                                             "dual", "primal_rel", "dual_rel")}
+        out["converged"] = rc == SR3D_OK
+        if st.hist_len > 0:
+            out["objective_hist"] = [hist[i] for i in range(min(st.evals, st.hist_len))]
+        return out

@@ -1,0 +1,580 @@
+// C ABI of libsr3d (declared in include/sr3d.h): plan construction and the
+// solver entry points.  Every numerical step runs in the kernels of
+// kernels_fft.cu and kernels_tv.cu; this file validates arguments, owns
+// device memory and sequences launches on the plan's stream.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "sr3d.h"
+
+using namespace sr3d;
+
+struct sr3d_plan_s {
+  Plan p;
+};
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return fail(e_ == cudaErrorMemoryAllocation ? SR3D_ERR_OOM : SR3D_ERR_CUDA, "%s: %s", #call, \
+                  cudaGetErrorString(e_));                                                        \
+  } while (0)
+
+// Launch accounting: counts every launch by kind and, when profiling is on,
+// brackets it with events on the plan's stream (resolved at sync_plan).
+static cudaError_t prof_begin(Plan& p, int kind) {
+  if (p.kind_override >= 0) kind = p.kind_override;
+  p.launches[kind]++;
+  if (!p.prof_on || p.prof_n >= p.prof_cap) return cudaSuccess;
+  p.prof_kind[p.prof_n] = kind;
+  return cudaEventRecord(p.prof_ev[2 * p.prof_n], p.stream);
+}
+static cudaError_t prof_end(Plan& p) {
+  if (!p.prof_on || p.prof_n >= p.prof_cap) return cudaSuccess;
+  cudaError_t e = cudaEventRecord(p.prof_ev[2 * p.prof_n + 1], p.stream);
+  p.prof_n++;
+  return e;
+}
+#define LAUNCH(kind, call)                                   \
+  do {                                                       \
+    CK(prof_begin(p, kind));                                 \
+    CK(call);                                                \
+    CK(prof_end(p));                                         \
+  } while (0)
+
+#define TRY(call)              \
+  do {                         \
+    int r_ = (call);           \
+    if (r_ != SR3D_OK) return r_; \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// geometry
+// ---------------------------------------------------------------------------
+static bool is_pow2(int n) { return n > 0 && (n & (n - 1)) == 0; }
+static bool supported_len(int n) { return is_pow2(n) || (n % 3 == 0 && is_pow2(n / 3)); }
+
+// Elements per thread e (largest allowed that divides n) and Stockham radices
+// (each dividing e).  Powers of two: e <= 16 (float) or 8 (double); 3 * 2^a:
+// e <= 12.  Must agree with Emax<T> in common.cuh.
+static FftAxis make_axis(int n, size_t esz) {
+  FftAxis f;
+  memset(&f, 0, sizeof(f));
+  f.n = n;
+  if (n % 3 == 0) {
+    const int cand[3] = {12, 6, 3};
+    for (int c : cand)
+      if (c <= n && n % c == 0) { f.e = c; break; }
+  } else {
+    const int p2 = esz == 4 ? 16 : 8;
+    const int cand[5] = {16, 8, 4, 2, 1};
+    for (int c : cand)
+      if (c <= p2 && c <= n && n % c == 0) { f.e = c; break; }
+  }
+  int rest = n;
+  if (rest % 3 == 0) { f.radix[f.nst++] = 3; rest /= 3; }
+  const int rads[4] = {16, 8, 4, 2};
+  for (int r : rads)
+    while (rest % r == 0 && f.e % r == 0) { f.radix[f.nst++] = r; rest /= r; }
+  return f;
+}
+
+static Geometry make_geom(int M, int N, int S, int dr, int dc, int ds, size_t csz) {
+  Geometry g;
+  memset(&g, 0, sizeof(g));
+  g.M = M; g.N = N; g.S = S;
+  g.dr = dr; g.dc = dc; g.ds = ds;
+  g.Ml = M / dr; g.Nl = N / dc; g.Sl = S / ds;
+  g.Ms = (g.Ml / 2 + 1) * dr;
+  g.Mp = (g.Ms + 1) & ~1;
+  g.fm = make_axis(M / 2, csz / 2);
+  g.fn = make_axis(N, csz / 2);
+  g.fs = make_axis(S, csz / 2);
+  // n pass: TW slots x N rows, TW * N / e threads
+  {
+    const int tpl = N / g.fn.e;
+    int tw = 256 / tpl;
+    tw = tw < 1 ? 1 : (tw > 64 ? 64 : tw);
+    if (tw > 1) tw &= ~1;
+    while (tw > 1 && (size_t)tw * N * csz > 96 * 1024) tw /= 2;
+    const int cap = (g.Ms + 1) & ~1;
+    if (tw > cap) tw = cap;
+    g.tw_n = tw;
+  }
+  // s pass: TW (multiple of dr) slots x G = dc n-slots x S planes
+  {
+    const int tpl = S / g.fs.e;
+    g.g_s = dc;
+    int target = 256 / (dc * tpl);
+    if (target < 1) target = 1;
+    int tw = ((target + dr - 1) / dr) * dr;
+    if (tw % 2) tw += dr;  // even when possible: keeps rows 16-byte aligned
+    const int cap = ((g.Ms + 2 * dr - 1) / (2 * dr)) * (2 * dr);
+    if (tw > cap) tw = cap;
+    while (tw > dr && ((long long)tw * dc * tpl > 512 || (size_t)tw * dc * S * csz > 160 * 1024)) tw -= dr;
+    g.tw_s = tw;
+  }
+  return g;
+}
+
+static int validate_lengths(const Geometry& g, size_t csz) {
+  const int lens[3] = {g.M / 2, g.N, g.S};
+  for (int n : lens)
+    if (n >= 1 && !supported_len(n)) return fail(SR3D_ERR_UNSUPPORTED_SIZE, "FFT length %d is not 2^a or 3*2^a", n);
+  if ((long long)g.tw_s * g.g_s * (g.S / g.fs.e) > 512 || (size_t)g.tw_s * g.g_s * g.S * csz > 200 * 1024 ||
+      (long long)g.tw_n * (g.N / g.fn.e) > 256 || (g.M / 2) / g.fm.e > 256)
+    return fail(SR3D_ERR_UNSUPPORTED_SIZE, "s-pass tile does not fit (S=%d, dc=%d)", g.S, g.dc);
+  return SR3D_OK;
+}
+
+static int dmalloc(Plan& p, void** ptr, size_t bytes) {
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? SR3D_ERR_OOM : SR3D_ERR_CUDA, "cudaMalloc(%zu): %s", bytes,
+                cudaGetErrorString(e));
+  }
+  p.bytes += (long long)bytes;
+  return SR3D_OK;
+}
+
+static void free_plan(Plan& p) {
+  void* bufs[] = {p.twM, p.twN, p.twS, p.twMl, p.twNl, p.twSl, p.symM, p.symN, p.symS, p.lam, p.yhat, p.spec,
+                  p.theta, p.dbuf[0], p.dbuf[1], p.psi, p.xh, p.yh, p.partial, p.partial_s, p.result, p.hist};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
+  for (int i = 0; i < 2 * p.prof_cap; ++i) cudaEventDestroy(p.prof_ev[i]);
+  delete[] p.prof_ev;
+  delete[] p.prof_kind;
+}
+
+static SolveArgs solve_args(const Plan& p, int mode_alpha_nn, double alpha) {
+  SolveArgs sv;
+  memset(&sv, 0, sizeof(sv));
+  const Geometry& g = p.hr;
+  sv.lam = p.lam;
+  sv.yhat = p.yhat;
+  sv.lr_out = p.yhat;
+  sv.symM = p.symM; sv.symN = p.symN; sv.symS = p.symS;
+  sv.twM = p.twM; sv.twN = p.twN; sv.twS = p.twS;
+  sv.alpha = alpha;
+  sv.nn_prior = mode_alpha_nn;
+  sv.M = g.M; sv.N = g.N; sv.S = g.S;
+  sv.Ml = g.Ml; sv.Nl = g.Nl; sv.Sl = g.Sl;
+  sv.dr = g.dr; sv.dc = g.dc; sv.ds = g.ds;
+  sv.Mlp = p.lr.Mp;
+  sv.partial = p.partial_s;
+  return sv;
+}
+
+// ---------------------------------------------------------------------------
+// pipelines
+// ---------------------------------------------------------------------------
+static int lr_spectrum(Plan& p, const void* y) {
+  LAUNCH(SR3D_K_RFFT_FWD, launch_rfft_m_fwd(p, p.lr, y, p.yhat, p.twMl));
+  LAUNCH(SR3D_K_FFTN_FWD, launch_fft_n(p, p.lr, p.yhat, p.twNl, false));
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.lr, p.yhat, p.twSl, S_FWD, false, nullptr));
+  return SR3D_OK;
+}
+
+static int hr_forward_partial(Plan& p, const void* x) {
+  LAUNCH(SR3D_K_RFFT_FWD, launch_rfft_m_fwd(p, p.hr, x, p.spec, p.twM));
+  LAUNCH(SR3D_K_FFTN_FWD, launch_fft_n(p, p.hr, p.spec, p.twN, false));
+  return SR3D_OK;
+}
+
+static int hr_inverse_partial(Plan& p, void* x) {
+  LAUNCH(SR3D_K_FFTN_INV, launch_fft_n(p, p.hr, p.spec, p.twN, true));
+  LAUNCH(SR3D_K_RFFT_INV, launch_rfft_m_inv(p, p.hr, p.spec, x, p.twM, 1.0 / (double)p.hr.V()));
+  return SR3D_OK;
+}
+
+static int tikhonov_core(Plan& p, const void* xbar, double tau, void* x) {
+  if (xbar && xbar != SR3D_XBAR_NEAREST) {
+    TRY(hr_forward_partial(p, xbar));
+    SolveArgs sv = solve_args(p, 0, tau);
+    LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_TIK_USER, false, &sv));
+  } else {
+    SolveArgs sv = solve_args(p, xbar == SR3D_XBAR_NEAREST ? 1 : 0, tau);
+    LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_TIK_GEN, false, &sv));
+  }
+  return hr_inverse_partial(p, x);
+}
+
+static int xstep_core(Plan& p, const void* theta, double mu, void* x, bool stats) {
+  TRY(hr_forward_partial(p, theta));
+  SolveArgs sv = solve_args(p, 0, mu);
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_ADMM, stats, &sv));
+  return hr_inverse_partial(p, x);
+}
+
+static int sync_plan(Plan& p) {
+  CK(cudaStreamSynchronize(p.stream));
+  for (int i = 0; i < p.prof_n; ++i) {
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, p.prof_ev[2 * i], p.prof_ev[2 * i + 1]));
+    p.prof_ms[p.prof_kind[i]] += ms;
+  }
+  p.prof_n = 0;
+  return SR3D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* sr3d_last_error(void) { return g_err.c_str(); }
+
+int sr3d_plan(sr3d_plan_t* out, const sr3d_desc* d) {
+  if (!out || !d) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (d->m_h <= 0 || d->n_h <= 0 || d->s_h <= 0 || d->dr <= 0 || d->dc <= 0 || d->ds <= 0)
+    return fail(SR3D_ERR_INVALID_ARG, "sizes and decimation factors must be positive");
+  if (!d->psf || d->p_m <= 0 || d->p_n <= 0 || d->p_s <= 0) return fail(SR3D_ERR_INVALID_ARG, "missing PSF");
+  if (d->dtype != SR3D_F32 && d->dtype != SR3D_F64) return fail(SR3D_ERR_INVALID_ARG, "dtype must be F32 or F64");
+  if (d->m_h % d->dr || d->n_h % d->dc || d->s_h % d->ds)
+    return fail(SR3D_ERR_NOT_DIVISIBLE, "HR sizes (%d,%d,%d) not divisible by (%d,%d,%d)", d->m_h, d->n_h, d->s_h,
+                d->dr, d->dc, d->ds);
+  if (d->p_m > d->m_h || d->p_n > d->n_h || d->p_s > d->s_h)
+    return fail(SR3D_ERR_INVALID_ARG, "PSF larger than the volume");
+  if (d->m_h % 32 || d->n_h % 8 || d->s_h < 4 || d->m_h > 2048 || d->n_h > 2048 || d->s_h > 2048 ||
+      !supported_len(d->m_h) || !supported_len(d->n_h) || !supported_len(d->s_h))
+    return fail(SR3D_ERR_UNSUPPORTED_SIZE,
+                "HR sizes must be 2^a or 3*2^a, m_h %% 32 == 0, n_h %% 8 == 0, 4 <= s_h, all <= 2048");
+  if ((d->m_h / d->dr) % 2) return fail(SR3D_ERR_UNSUPPORTED_SIZE, "m_h / dr must be even");
+  if (d->dr * d->dc * d->ds > 8) return fail(SR3D_ERR_UNSUPPORTED_SIZE, "dr*dc*ds must be at most 8");
+
+  sr3d_plan_s* h = new sr3d_plan_s();
+  Plan& p = h->p;
+  p.dtype = d->dtype;
+  p.esz = p.dtype ? 8 : 4;
+  const size_t csz = 2 * p.esz;
+  p.hr = make_geom(d->m_h, d->n_h, d->s_h, d->dr, d->dc, d->ds, csz);
+  p.lr = make_geom(p.hr.Ml, p.hr.Nl, p.hr.Sl, 1, 1, 1, csz);
+  int rc = validate_lengths(p.hr, csz);
+  if (rc == SR3D_OK) rc = validate_lengths(p.lr, csz);
+  if (rc != SR3D_OK) {
+    delete h;
+    return rc;
+  }
+  double psum = 0;
+  const long long np = (long long)d->p_m * d->p_n * d->p_s;
+  for (long long i = 0; i < np; ++i) psum += d->psf[i];
+  p.psf_sum = psum;
+
+  if (d->stream) {
+    p.stream = (cudaStream_t)d->stream;
+    p.own_stream = false;
+  } else {
+    cudaError_t e = cudaStreamCreateWithFlags(&p.stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(SR3D_ERR_CUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    p.own_stream = true;
+  }
+
+  auto body = [&]() -> int {
+    const Geometry& g = p.hr;
+    const Geometry& l = p.lr;
+    TRY(dmalloc(p, &p.twM, (size_t)g.M * csz));
+    TRY(dmalloc(p, &p.twN, (size_t)g.N * csz));
+    TRY(dmalloc(p, &p.twS, (size_t)g.S * csz));
+    TRY(dmalloc(p, &p.twMl, (size_t)l.M * csz));
+    TRY(dmalloc(p, &p.twNl, (size_t)l.N * csz));
+    TRY(dmalloc(p, &p.twSl, (size_t)l.S * csz));
+    TRY(dmalloc(p, &p.symM, (size_t)g.M * p.esz));
+    TRY(dmalloc(p, &p.symN, (size_t)g.N * p.esz));
+    TRY(dmalloc(p, &p.symS, (size_t)g.S * p.esz));
+    TRY(dmalloc(p, &p.lam, (size_t)g.spec_elems() * csz));
+    TRY(dmalloc(p, &p.spec, (size_t)g.spec_elems() * csz));
+    TRY(dmalloc(p, &p.yhat, (size_t)l.spec_elems() * csz));
+    TRY(dmalloc(p, &p.theta, (size_t)g.V() * p.esz));
+    p.n_tv_blocks = tv_blocks(g);
+    p.n_s_blocks = s_pass_blocks(g);
+    TRY(dmalloc(p, (void**)&p.partial, (size_t)p.n_tv_blocks * 6 * sizeof(double)));
+    TRY(dmalloc(p, (void**)&p.partial_s, (size_t)p.n_s_blocks * sizeof(double)));
+    TRY(dmalloc(p, (void**)&p.result, 16 * sizeof(double)));
+    CK(launch_twiddle(p, p.twM, g.M));
+    CK(launch_twiddle(p, p.twN, g.N));
+    CK(launch_twiddle(p, p.twS, g.S));
+    CK(launch_twiddle(p, p.twMl, l.M));
+    CK(launch_twiddle(p, p.twNl, l.N));
+    CK(launch_twiddle(p, p.twSl, l.S));
+    CK(launch_symbol(p, p.symM, g.M));
+    CK(launch_symbol(p, p.symN, g.N));
+    CK(launch_symbol(p, p.symS, g.S));
+    // Lambda = DFT of the origin-wrapped PSF (Algorithm 1 step 1)
+    void* psf_dev = nullptr;
+    TRY(dmalloc(p, &psf_dev, (size_t)np * sizeof(double)));
+    p.bytes -= (long long)np * sizeof(double);
+    cudaError_t e = cudaMemcpyAsync(psf_dev, d->psf, (size_t)np * sizeof(double), cudaMemcpyHostToDevice, p.stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p.theta, 0, (size_t)g.V() * p.esz, p.stream);
+    if (e == cudaSuccess) e = launch_wrap_psf(p, p.theta, (const double*)psf_dev, d->p_m, d->p_n, d->p_s);
+    if (e == cudaSuccess) e = launch_rfft_m_fwd(p, g, p.theta, p.lam, p.twM);
+    if (e == cudaSuccess) e = launch_fft_n(p, g, p.lam, p.twN, false);
+    if (e == cudaSuccess) e = launch_fft_s(p, g, p.lam, p.twS, S_FWD, false, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
+    cudaFree(psf_dev);
+    if (e != cudaSuccess) return fail(SR3D_ERR_CUDA, "plan setup: %s", cudaGetErrorString(e));
+    return SR3D_OK;
+  };
+  rc = body();
+  if (rc != SR3D_OK) {
+    free_plan(p);
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return SR3D_OK;
+}
+
+int sr3d_destroy(sr3d_plan_t plan) {
+  if (!plan) return SR3D_OK;
+  cudaStreamSynchronize(plan->p.stream);
+  free_plan(plan->p);
+  delete plan;
+  return SR3D_OK;
+}
+
+int sr3d_profile(sr3d_plan_t plan, int on) {
+  if (!plan) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  TRY(sync_plan(p));
+  if (on && !p.prof_ev) {
+    const int cap = 4096;
+    p.prof_ev = new cudaEvent_t[2 * cap];
+    p.prof_kind = new int[cap];
+    for (int i = 0; i < 2 * cap; ++i) {
+      cudaError_t e = cudaEventCreate(&p.prof_ev[i]);
+      if (e != cudaSuccess) {
+        p.prof_cap = i / 2;
+        return fail(SR3D_ERR_CUDA, "cudaEventCreate: %s", cudaGetErrorString(e));
+      }
+      p.prof_cap = (i + 1) / 2;
+    }
+  }
+  p.prof_on = on != 0;
+  p.prof_n = 0;
+  for (int k = 0; k < 8; ++k) {
+    p.prof_ms[k] = 0;
+    p.launches[k] = 0;
+  }
+  return SR3D_OK;
+}
+
+int sr3d_profile_read(sr3d_plan_t plan, double ms[SR3D_NKINDS], long long launches[SR3D_NKINDS]) {
+  if (!plan || !ms || !launches) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  TRY(sync_plan(p));
+  for (int k = 0; k < SR3D_NKINDS; ++k) {
+    ms[k] = p.prof_ms[k];
+    launches[k] = p.launches[k];
+  }
+  return SR3D_OK;
+}
+
+int sr3d_plan_info(sr3d_plan_t plan, int sizes[9], long long* bytes) {
+  if (!plan || !sizes) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  const Plan& p = plan->p;
+  const int v[9] = {p.hr.M, p.hr.N, p.hr.S, p.hr.Ml, p.hr.Nl, p.hr.Sl, p.hr.Ms, p.hr.Mp, p.dtype};
+  for (int i = 0; i < 9; ++i) sizes[i] = v[i];
+  if (bytes) *bytes = p.bytes;
+  return SR3D_OK;
+}
+
+int sr3d_forward(sr3d_plan_t plan, const void* x, void* y) {
+  if (!plan || !x || !y) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  TRY(hr_forward_partial(p, x));
+  SolveArgs sv = solve_args(p, 0, 1.0);
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_FOLD, false, &sv));
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.lr, p.yhat, p.twSl, S_INV, false, nullptr));
+  LAUNCH(SR3D_K_FFTN_INV, launch_fft_n(p, p.lr, p.yhat, p.twNl, true));
+  LAUNCH(SR3D_K_RFFT_INV, launch_rfft_m_inv(p, p.lr, p.yhat, y, p.twMl, 1.0 / (double)p.lr.V()));
+  return sync_plan(p);
+}
+
+int sr3d_tikhonov(sr3d_plan_t plan, const void* y, const void* xbar, double tau, void* x) {
+  if (!plan || !y || !x) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  if (!(tau > 0) || !std::isfinite(tau)) return fail(SR3D_ERR_INVALID_ARG, "tau must be positive and finite");
+  Plan& p = plan->p;
+  TRY(lr_spectrum(p, y));
+  TRY(tikhonov_core(p, xbar, tau, x));
+  return sync_plan(p);
+}
+
+int sr3d_get_otf(sr3d_plan_t plan, void* out) {
+  if (!plan || !out) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  LAUNCH(SR3D_K_OTHER, launch_export_half(p, p.lam, out));
+  return sync_plan(p);
+}
+
+int sr3d_fft3(sr3d_plan_t plan, const void* x, void* out) {
+  if (!plan || !x || !out) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  TRY(hr_forward_partial(p, x));
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_FWD, false, nullptr));
+  LAUNCH(SR3D_K_OTHER, launch_export_half(p, p.spec, out));
+  return sync_plan(p);
+}
+
+int sr3d_xstep(sr3d_plan_t plan, const void* y, const void* theta, double rho, void* x) {
+  if (!plan || !y || !theta || !x) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  if (!(rho > 0)) return fail(SR3D_ERR_INVALID_ARG, "rho must be positive");
+  Plan& p = plan->p;
+  if (p.psf_sum == 0.0) return fail(SR3D_ERR_SINGULAR, "PSF taps sum to zero");
+  TRY(lr_spectrum(p, y));
+  TRY(xstep_core(p, theta, rho, x, false));
+  return sync_plan(p);
+}
+
+int sr3d_tv_step(sr3d_plan_t plan, const void* x, const void* din, void* dout, double lambda, double rho,
+                 void* theta) {
+  if (!plan || !x || !din || !dout || !theta) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  if (!(rho > 0) || lambda < 0) return fail(SR3D_ERR_INVALID_ARG, "need rho > 0 and lambda >= 0");
+  if (din == dout) return fail(SR3D_ERR_INVALID_ARG, "d_in and d_out must differ");
+  Plan& p = plan->p;
+  LAUNCH(SR3D_K_TV, launch_tv(p, x, din, dout, theta, nullptr, lambda / rho, 0, false));
+  return sync_plan(p);
+}
+
+static int ensure_admm_buffers(Plan& p, bool need_psi) {
+  const size_t dbytes = (size_t)3 * p.hr.V() * p.esz;
+  if (!p.dbuf[0]) TRY(dmalloc(p, &p.dbuf[0], dbytes));
+  if (!p.dbuf[1]) TRY(dmalloc(p, &p.dbuf[1], dbytes));
+  if (need_psi && !p.psi) TRY(dmalloc(p, &p.psi, (size_t)p.hr.V() * p.esz));
+  return SR3D_OK;
+}
+
+static int ensure_hist(Plan& p, int n) {
+  if (n <= p.hist_cap) return SR3D_OK;
+  if (p.hist) {
+    cudaFree(p.hist);
+    p.bytes -= (long long)p.hist_cap * sizeof(double);
+    p.hist = nullptr;
+  }
+  TRY(dmalloc(p, (void**)&p.hist, (size_t)n * sizeof(double)));
+  p.hist_cap = n;
+  return SR3D_OK;
+}
+
+int sr3d_admm_tv(sr3d_plan_t plan, const void* y, void* x, void* d_dev, double lambda, double rho, int max_iters,
+                 double tol, double tau_init, sr3d_stats* stats) {
+  if (!plan || !y || !x) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  if (!(rho > 0) || !(lambda >= 0) || max_iters < 0 || !std::isfinite(rho) || !std::isfinite(lambda))
+    return fail(SR3D_ERR_INVALID_ARG, "need rho > 0, lambda >= 0, max_iters >= 0");
+  Plan& p = plan->p;
+  if (p.psf_sum == 0.0) return fail(SR3D_ERR_SINGULAR, "PSF taps sum to zero: the zero-frequency class is singular");
+  const bool want_stats = stats != nullptr || tol > 0;
+  int every = stats ? stats->eval_every : 0;
+  if (tol > 0 && every <= 0) every = 1;
+  TRY(ensure_admm_buffers(p, want_stats));
+  const int max_evals = want_stats ? (every > 0 ? max_iters / every + 1 : 1) : 0;
+  if (want_stats) TRY(ensure_hist(p, max_evals > 0 ? max_evals : 1));
+
+  void* dcur = d_dev ? d_dev : p.dbuf[0];
+  void* dnext = d_dev ? p.dbuf[0] : p.dbuf[1];
+  const double thr = lambda / rho;
+  {
+    p.kind_override = SR3D_K_SETUP;
+    struct Reset { Plan& p; ~Reset() { p.kind_override = -1; } } reset{p};
+    TRY(lr_spectrum(p, y));
+    if (tau_init > 0) TRY(tikhonov_core(p, SR3D_XBAR_NEAREST, tau_init, x));
+    if (!d_dev) CK(cudaMemsetAsync(dcur, 0, (size_t)3 * p.hr.V() * p.esz, p.stream));
+    // Theta^0 = L^T (u0 - d0) with u0 = L x0
+    LAUNCH(SR3D_K_TV, launch_tv(p, x, dcur, nullptr, p.theta, p.psi, thr, 1, want_stats));
+  }
+  int evals = 0, it = 0;
+  bool converged = false;
+  double res[16] = {0};
+  for (int k = 1; k <= max_iters; ++k) {
+    const bool eval_now = want_stats && ((every > 0 && k % every == 0) || k == max_iters);
+    const bool stats_now = want_stats && (eval_now || (every > 0 && (k + 1) % every == 0) || k + 1 == max_iters);
+    TRY(xstep_core(p, p.theta, rho, x, eval_now));
+    LAUNCH(SR3D_K_TV, launch_tv(p, x, dcur, dnext, p.theta, p.psi, thr, 0, stats_now));
+    void* t = dcur;
+    dcur = dnext;
+    dnext = t;
+    it = k;
+    if (eval_now) {
+      LAUNCH(SR3D_K_OTHER, launch_finalize(p, evals < p.hist_cap ? evals : -1, lambda, rho, 1.0 / (double)p.lr.V(), true));
+      ++evals;
+      if (tol > 0) {
+        CK(cudaMemcpyAsync(res, p.result, 11 * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+        TRY(sync_plan(p));
+        if (res[10] != 0.0) return fail(SR3D_ERR_NUMERIC, "NaN/Inf in the objective or residuals at iteration %d", k);
+        if (res[8] < tol && res[9] < tol) {
+          converged = true;
+          break;
+        }
+      }
+    }
+  }
+  if (d_dev && dcur != d_dev)
+    CK(cudaMemcpyAsync(d_dev, dcur, (size_t)3 * p.hr.V() * p.esz, cudaMemcpyDeviceToDevice, p.stream));
+  if (want_stats && evals > 0) {
+    CK(cudaMemcpyAsync(res, p.result, 11 * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+    if (stats && stats->objective_hist && stats->hist_len > 0) {
+      const int n = evals < stats->hist_len ? evals : stats->hist_len;
+      CK(cudaMemcpyAsync(stats->objective_hist, p.hist, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
+                         p.stream));
+    }
+  }
+  TRY(sync_plan(p));
+  if (stats) {
+    stats->iters = it;
+    stats->evals = evals;
+    stats->objective = res[0];
+    stats->data_term = res[1];
+    stats->tv_term = res[2];
+    stats->primal = res[3];
+    stats->dual = res[4];
+    stats->primal_rel = res[8];
+    stats->dual_rel = res[9];
+  }
+  if (want_stats && evals > 0 && res[10] != 0.0) return fail(SR3D_ERR_NUMERIC, "NaN/Inf in the objective or residuals");
+  if (tol > 0 && !converged) return fail(SR3D_ERR_NOT_CONVERGED, "max_iters=%d reached before tol=%g", max_iters, tol);
+  return SR3D_OK;
+}
+
+int sr3d_admm_tv_host(sr3d_plan_t plan, const void* y_host, void* x_host, double lambda, double rho, int max_iters,
+                      double tol, double tau_init, sr3d_stats* stats) {
+  if (!plan || !y_host || !x_host) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  const size_t xb = (size_t)p.hr.V() * p.esz, yb = (size_t)p.lr.V() * p.esz;
+  if (!p.xh) TRY(dmalloc(p, &p.xh, xb));
+  if (!p.yh) TRY(dmalloc(p, &p.yh, yb));
+  CK(cudaMemcpyAsync(p.yh, y_host, yb, cudaMemcpyHostToDevice, p.stream));
+  if (!(tau_init > 0)) CK(cudaMemcpyAsync(p.xh, x_host, xb, cudaMemcpyHostToDevice, p.stream));
+  const int rc = sr3d_admm_tv(plan, p.yh, p.xh, nullptr, lambda, rho, max_iters, tol, tau_init, stats);
+  if (rc != SR3D_OK && rc != SR3D_ERR_NOT_CONVERGED) return rc;
+  CK(cudaMemcpyAsync(x_host, p.xh, xb, cudaMemcpyDeviceToHost, p.stream));
+  TRY(sync_plan(p));
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,111 @@
+// Internal host-side interfaces of libsr3d: the plan object and the kernel
+// launchers shared by the API translation unit and the kernel units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sr3d {
+
+// s-pass modes (kernel k_fft_s)
+enum SMode {
+  S_FWD = 0,       // forward transform along s
+  S_INV = 1,       // inverse (unnormalised) transform along s
+  S_TIK_GEN = 2,   // Tikhonov with zero / nearest-neighbour prior: build B, solve, inverse
+  S_TIK_USER = 3,  // Tikhonov with a user prior: forward, B = conj(L) Y + tau Xbar, solve, inverse
+  S_ADMM = 4,      // ADMM x-update: forward, B = conj(L) Y + mu Theta^, Gamma-weighted solve, inverse
+  S_FOLD = 5,      // forward, then (1/d) sum_p L_p X_p per class into the LR spectrum
+};
+
+// Arguments of the per-aliasing-class solve inside the s pass.
+struct SolveArgs {
+  const void* lam;     // Lambda, HR spectral layout
+  const void* yhat;    // LR spectrum [Sl][Nl][Mlp]
+  void* lr_out;        // S_FOLD output, LR spectral layout
+  const void* symM;    // 4 sin^2(pi k / M) tables (element type T)
+  const void* symN;
+  const void* symS;
+  const void* twM;     // exp(-2 pi i q / M) tables (complex T)
+  const void* twN;
+  const void* twS;
+  double alpha;        // tau (Tikhonov) or mu (ADMM)
+  int nn_prior;        // S_TIK_GEN: 1 = nearest-neighbour prior, 0 = zero prior
+  int M, N, S;
+  int Ml, Nl, Sl;
+  int dr, dc, ds;
+  int Mlp;
+  double* partial;     // per-CTA data-term partial sums (S_ADMM with statistics)
+};
+
+struct Geometry {
+  int M, N, S;        // sizes of the real volume
+  int dr, dc, ds;     // aliasing groups (1,1,1 for LR transforms)
+  int Ml, Nl, Sl;
+  int Ms, Mp;         // m slots / pitch of the spectral layout
+  FftAxis fm, fn, fs; // fm has length M/2
+  int tw_s;           // s-pass tile width (multiple of dr)
+  int g_s;            // s-pass tile height in n slots (multiple of dc)
+  int tw_n;           // n-pass tile width
+  long long V() const { return (long long)M * N * S; }
+  long long spec_elems() const { return (long long)S * N * Mp; }
+};
+
+struct Plan {
+  int dtype;     // 0 float, 1 double
+  size_t esz;    // element size
+  Geometry hr, lr;
+  double psf_sum;
+  cudaStream_t stream;
+  bool own_stream;
+  // device buffers
+  void* twM = nullptr; void* twN = nullptr; void* twS = nullptr;     // HR twiddles
+  void* twMl = nullptr; void* twNl = nullptr; void* twSl = nullptr;  // LR twiddles
+  void* symM = nullptr; void* symN = nullptr; void* symS = nullptr;
+  void* lam = nullptr;    // HR spectral
+  void* yhat = nullptr;   // LR spectral
+  void* spec = nullptr;   // HR spectral work
+  void* theta = nullptr;  // HR real
+  void* dbuf[2] = {nullptr, nullptr};  // ADMM dual, 3 V each
+  void* psi = nullptr;                  // L^T u of the previous iteration
+  void* xh = nullptr; void* yh = nullptr;  // staging for host-buffer calls
+  double* partial = nullptr;  // TV-kernel partial sums
+  double* partial_s = nullptr;  // s-pass partial sums
+  double* result = nullptr;   // finalize output (16 doubles)
+  double* hist = nullptr;     // objective history (device)
+  int hist_cap = 0;
+  long long n_tv_blocks = 0, n_s_blocks = 0;
+  long long bytes = 0;
+  // per-kernel accounting (sr3d_profile)
+  bool prof_on = false;
+  int kind_override = -1;  // >= 0: account every launch to this kind
+  int prof_cap = 0, prof_n = 0;
+  cudaEvent_t* prof_ev = nullptr;  // 2 * prof_cap events
+  int* prof_kind = nullptr;
+  double prof_ms[8] = {0};
+  long long launches[8] = {0};
+};
+
+// ---- launchers (kernels_fft.cu) ----
+cudaError_t launch_rfft_m_fwd(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw);
+cudaError_t launch_rfft_m_inv(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw,
+                              double scale);
+cudaError_t launch_fft_n(const Plan& p, const Geometry& g, void* spec, const void* tw, bool inverse);
+cudaError_t launch_fft_s(const Plan& p, const Geometry& g, void* spec, const void* tw, int mode, bool stats,
+                         const SolveArgs* sv);
+long long s_pass_blocks(const Geometry& g);
+
+// ---- launchers (kernels_tv.cu) ----
+// mode 0: ADMM step (shrink + dual update); mode 1: initial Theta = L^T (L x - d)
+cudaError_t launch_tv(const Plan& p, const void* x, const void* din, void* dout, void* theta, void* psi,
+                      double thr, int mode, bool stats);
+long long tv_blocks(const Geometry& g);
+cudaError_t launch_finalize(const Plan& p, int hist_index, double lam_tv, double mu, double inv_nl,
+                            bool with_data);
+cudaError_t launch_twiddle(const Plan& p, void* tw, int n);
+cudaError_t launch_symbol(const Plan& p, void* sym, int n);
+cudaError_t launch_wrap_psf(const Plan& p, void* out, const double* psf_dev, int pm, int pn, int ps);
+cudaError_t launch_export_half(const Plan& p, const void* spec, void* out);
+
+}  // namespace sr3d

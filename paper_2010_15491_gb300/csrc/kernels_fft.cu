@@ -1,0 +1,504 @@
+// FFT passes of the 3D transforms and the per-aliasing-class solve.
+//
+// Spectral layout of a real volume x[s][n][m] (sizes M, N, S): complex
+// spec[k_s][n-slot][m-slot] with
+//   m-slot g*dr + p  <->  m-frequency g + p*Ml, g in [0, Ml/2]   (Ml = M/dr)
+//   n-slot (k % Nl)*dc + k / Nl  <->  n-frequency k               (Nl = N/dc)
+//   k_s natural.
+// Every frequency either is stored or has its conjugate stored (the m axis
+// is real), and the d = dr*dc*ds members of each aliasing class of eq. (8)
+// sit in one dr x dc block of slots on ds planes, so the s pass can solve a
+// class from one shared-memory tile.
+//
+// Per solve the passes are: real FFT along m (packed half-length complex
+// transform), strided FFT along n, FFT along s fused with the class solve
+// and the inverse s FFT, inverse n FFT, inverse real FFT along m.
+#include "fft.cuh"
+#include "internal.h"
+
+namespace sr3d {
+
+template <typename T> struct Lim;
+template <> struct Lim<float> { static constexpr float big = 3.0e38f; };
+template <> struct Lim<double> { static constexpr double big = 1.0e300; };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// m pass, forward: L real lines of length M -> Ms slots each.
+// ---------------------------------------------------------------------------
+template <typename T, int EMAX>
+__global__ void __launch_bounds__(256, 2) k_rfft_m_fwd(const T* __restrict__ in, long long nlines, cplx<T>* __restrict__ out, MAxis a,
+                             int L, int Hp, const cplx<T>* __restrict__ twM) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int H = a.H;
+  const int tpl = H / a.f.e;
+  const long long line0 = (long long)blockIdx.x * L;
+  const C* inc = reinterpret_cast<const C*>(in);  // (x[2j], x[2j+1]) as one complex
+  for (int i = threadIdx.x; i < L * H; i += blockDim.x) {
+    const int l = i / H, j = i - l * H;
+    const long long gl = line0 + l;
+    C v = czero<C>();
+    if (gl < nlines) v = inc[gl * H + j];
+    sm[l * Hp + j] = v;
+  }
+  __syncthreads();
+  {
+    const int l = threadIdx.x / tpl, tl = threadIdx.x - l * tpl;
+    fft_line<T, EMAX>(sm + l * Hp, 1, a.f, tl, tpl, twM, 2);
+  }
+  // split the packed transform: X[k] = E[k] + W^k O[k], E/O from Z[k], conj(Z[H-k])
+  for (int i = threadIdx.x; i < L * a.Ms; i += blockDim.x) {
+    const int l = i / a.Ms, slot = i - l * a.Ms;
+    const long long gl = line0 + l;
+    if (gl >= nlines) continue;
+    const int grp = slot / a.dr, p = slot - grp * a.dr;
+    int k = grp + p * a.Ml;
+    const bool cj = k > H;
+    if (cj) k = a.M - k;
+    const C zk = sm[l * Hp + (k == H ? 0 : k)];
+    const C zc = conjc(sm[l * Hp + (k == 0 ? 0 : H - k)]);
+    const C e = (zk + zc) * (T)0.5;
+    const C o = mul_mi(zk - zc) * (T)0.5;
+    const C X = e + cmul(__ldg(&twM[k]), o);
+    out[gl * a.Mp + slot] = cj ? conjc(X) : X;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// m pass, inverse: Ms slots -> M reals per line, times `scale`.
+// ---------------------------------------------------------------------------
+template <typename T, int EMAX>
+__global__ void __launch_bounds__(256, 2) k_rfft_m_inv(const cplx<T>* __restrict__ in, long long nlines, T* __restrict__ out, MAxis a,
+                             int L, int Hp, const cplx<T>* __restrict__ twM, T scale) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int H = a.H;
+  const int tpl = H / a.f.e;
+  const long long line0 = (long long)blockIdx.x * L;
+  for (int i = threadIdx.x; i < L * H; i += blockDim.x) {
+    const int l = i / H, k = i - l * H;
+    const long long gl = line0 + l;
+    C z = czero<C>();
+    if (gl < nlines) {
+      const C* row = in + gl * a.Mp;
+      bool c1, c2;
+      const int s1 = mslot_of(k, a.M, a.Ml, a.dr, c1);
+      const int s2 = mslot_of(H - k, a.M, a.Ml, a.dr, c2);
+      C xk = row[s1];
+      if (c1) xk = conjc(xk);
+      C xh = row[s2];
+      if (!c2) xh = conjc(xh);  // conj(X[H-k])
+      const C e = xk + xh;
+      const C o = cmulc(__ldg(&twM[k]), xk - xh);  // W^-k (X[k] - conj(X[H-k]))
+      z = e + mul_i(o);
+    }
+    sm[l * Hp + k] = conjc(z);  // inverse through the forward engine
+  }
+  __syncthreads();
+  {
+    const int l = threadIdx.x / tpl, tl = threadIdx.x - l * tpl;
+    fft_line<T, EMAX>(sm + l * Hp, 1, a.f, tl, tpl, twM, 2);
+  }
+  C* outc = reinterpret_cast<C*>(out);
+  for (int i = threadIdx.x; i < L * H; i += blockDim.x) {
+    const int l = i / H, j = i - l * H;
+    const long long gl = line0 + l;
+    if (gl >= nlines) continue;
+    const C r = sm[l * Hp + j];
+    outc[gl * H + j] = mkc(r.x * scale, -r.y * scale);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// n pass: tile of TW m-slots x all N rows of one s plane.  Forward reads n in
+// natural order and writes n-slots; inverse reads n-slots, writes natural n.
+// ---------------------------------------------------------------------------
+template <typename T, int EMAX, bool INV>
+__global__ void __launch_bounds__(256, 2) k_fft_n(cplx<T>* __restrict__ spec, LAxis a, int Ms, int Mp, int TW,
+                        const cplx<T>* __restrict__ twN) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int N = a.N;
+  const int a0 = blockIdx.x * TW;
+  const int tv = min(TW, Ms - a0);
+  C* base = spec + (long long)blockIdx.y * N * Mp + a0;
+  for (int i = threadIdx.x; i < N * TW; i += blockDim.x) {
+    const int n = i / TW, t = i - n * TW;
+    C v = czero<C>();
+    if (t < tv) {
+      const int row = INV ? nslot(n, a.Nl, a.dc) : n;
+      v = base[(long long)row * Mp + t];
+      if (INV) v = conjc(v);
+    }
+    sm[i] = v;
+  }
+  __syncthreads();
+  {
+    const int t = threadIdx.x % TW, tl = threadIdx.x / TW, tpl = N / a.f.e;
+    fft_line<T, EMAX>(sm + t, TW, a.f, tl, tpl, twN, 1);
+  }
+  for (int i = threadIdx.x; i < N * TW; i += blockDim.x) {
+    const int n = i / TW, t = i - n * TW;
+    if (t < tv) {
+      const int row = INV ? n : nslot(n, a.Nl, a.dc);
+      C v = sm[i];
+      if (INV) v = conjc(v);
+      base[(long long)row * Mp + t] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// s pass with the class solve.  Tile: m-slots [a0, a0+TW) x n-slots
+// [b0, b0+G) x all S planes; TW is a multiple of dr and G of dc, so the tile
+// holds whole aliasing classes.
+// ---------------------------------------------------------------------------
+template <typename C, typename T>
+__device__ __forceinline__ C box_factor(const C* __restrict__ tw, int n, int da, int k) {
+  // sum_{q < da} exp(-2 pi i k q / n): DFT of the nearest-neighbour block along one axis
+  C r = czero<C>();
+  for (int q = 0; q < da; ++q) r = r + __ldg(&tw[(int)(((long long)k * q) % n)]);
+  return r;
+}
+
+constexpr int DMAX = 8;  // largest supported d = dr*dc*ds
+
+template <typename T, int EMAX, int MODE, bool STATS>
+__global__ void __launch_bounds__(512) k_fft_s(cplx<T>* __restrict__ spec, LAxis a, int Ms, int Mp, int Nn, int TW, int G, SolveArgs sv,
+                        const cplx<T>* __restrict__ twS) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int S = a.N;
+  const int a0 = blockIdx.x * TW, b0 = blockIdx.y * G;
+  const int tv = min(TW, Ms - a0);
+  const int nthr = blockDim.x, tid = threadIdx.x;
+  const int rowlen = G * TW;
+  const long long plane = (long long)Nn * Mp;
+  C* gbase = spec + (long long)b0 * Mp + a0;
+
+  for (int i = tid; i < S * rowlen; i += nthr) {
+    const int s = i / rowlen, r = i - s * rowlen, gi = r / TW, t = r - gi * TW;
+    C v = czero<C>();
+    if (MODE != S_TIK_GEN && t < tv) {
+      v = gbase[s * plane + (long long)gi * Mp + t];
+      if (MODE == S_INV) v = conjc(v);
+    }
+    sm[i] = v;
+  }
+  __syncthreads();
+  const int t = tid % TW, gi = (tid / TW) % G, tl = tid / (TW * G), tpl = S / a.f.e;
+  C* line = sm + gi * TW + t;
+  if (MODE != S_TIK_GEN) fft_line<T, EMAX>(line, rowlen, a.f, tl, tpl, twS, 1);
+
+  if (MODE >= S_TIK_GEN) {
+    const int d = sv.dr * sv.dc * sv.ds;
+    const T dd = (T)d;
+    const int GMc = TW / sv.dr, GNc = G / sv.dc;
+    const int Gm = Ms / sv.dr;
+    const int ncls = GMc * GNc * sv.Sl;
+    const C* __restrict__ lam = reinterpret_cast<const C*>(sv.lam);
+    const C* __restrict__ yh = reinterpret_cast<const C*>(sv.yhat);
+    const T* __restrict__ symM = reinterpret_cast<const T*>(sv.symM);
+    const T* __restrict__ symN = reinterpret_cast<const T*>(sv.symN);
+    const T* __restrict__ symS = reinterpret_cast<const T*>(sv.symS);
+    const T alpha = (T)sv.alpha;
+    const T ialpha = (T)(1.0 / sv.alpha);
+    double acc = 0.0;
+    for (int c = tid; c < ncls; c += nthr) {
+      const int gm = c % GMc;
+      const int rest = c / GMc;
+      const int gn = rest % GNc;
+      const int is = rest / GNc;
+      const int g = a0 / sv.dr + gm;
+      if (g >= Gm) continue;
+      const int jl = b0 / sv.dc + gn;
+      if (MODE == S_FOLD) {
+        C tsum = czero<C>();
+        for (int q = 0; q < d; ++q) {
+          const int pm = q % sv.dr, pn = (q / sv.dr) % sv.dc, ps = q / (sv.dr * sv.dc);
+          const int ks = is + ps * sv.Sl, lrow = gn * sv.dc + pn, lcol = gm * sv.dr + pm;
+          const C av = __ldg(&lam[(long long)ks * plane + (long long)(b0 + lrow) * Mp + a0 + lcol]);
+          tsum = tsum + cmul(av, sm[(ks * G + lrow) * TW + lcol]);
+        }
+        reinterpret_cast<C*>(sv.lr_out)[((long long)is * sv.Nl + jl) * sv.Mlp + g] = tsum * (T)(1.0 / d);
+        continue;
+      }
+      const C Yc = __ldg(&yh[((long long)is * sv.Nl + jl) * sv.Mlp + g]);
+      const bool dc_cls = (MODE == S_ADMM) && g == 0 && jl == 0 && is == 0;
+      C av[DMAX], bv[DMAX];
+      T wv[DMAX];
+      int si[DMAX];
+      int qs = 0;
+      T best = (T)-1;
+#pragma unroll
+      for (int q = 0; q < DMAX; ++q) {
+        if (q < d) {
+          const int pm = q % sv.dr, pn = (q / sv.dr) % sv.dc, ps = q / (sv.dr * sv.dc);
+          const int ks = is + ps * sv.Sl, kn = jl + pn * sv.Nl, km = g + pm * sv.Ml;
+          const int lrow = gn * sv.dc + pn, lcol = gm * sv.dr + pm;
+          si[q] = (ks * G + lrow) * TW + lcol;
+          const C a_ = __ldg(&lam[(long long)ks * plane + (long long)(b0 + lrow) * Mp + a0 + lcol]);
+          C B = cmulc(a_, Yc);  // conj(Lambda_p) Y: F H^H D^H y at this frequency
+          T w;
+          if (MODE == S_ADMM) {
+            B = B + sm[si[q]] * alpha;  // + mu F Theta
+            const T sy = __ldg(&symM[km]) + __ldg(&symN[kn]) + __ldg(&symS[ks]);
+            w = (dc_cls && q == 0) ? (T)0 : (T)1 / (alpha * sy);  // Gamma / mu
+          } else {
+            if (MODE == S_TIK_USER) B = B + sm[si[q]] * alpha;  // + tau F xbar
+            if (MODE == S_TIK_GEN && sv.nn_prior) {
+              const C bx = cmul(cmul(box_factor<C, T>(reinterpret_cast<const C*>(sv.twM), sv.M, sv.dr, km),
+                                     box_factor<C, T>(reinterpret_cast<const C*>(sv.twN), sv.N, sv.dc, kn)),
+                                box_factor<C, T>(reinterpret_cast<const C*>(sv.twS), sv.S, sv.ds, ks));
+              B = B + cmul(Yc, bx) * alpha;  // + tau F xbar, xbar = nearest-neighbour y
+            }
+            w = ialpha;
+          }
+          const T key = (dc_cls && q == 0) ? Lim<T>::big : norm2(a_) * w;
+          if (key > best) { best = key; qs = q; }
+          av[q] = a_;
+          bv[q] = B;
+          wv[q] = w;
+        }
+      }
+      // Sherman-Morrison on the class block diag(1/w) + (1/d) conj(a) a^T with
+      // the dominant member p* = qs kept out of the sums (no cancellation).
+      T Sp = 0;
+      C Tp = czero<C>(), as = czero<C>(), bs = czero<C>();
+      T ws = 0;
+#pragma unroll
+      for (int q = 0; q < DMAX; ++q) {
+        if (q < d) {
+          if (q == qs) {
+            as = av[q]; bs = bv[q]; ws = wv[q];
+          } else {
+            Sp += norm2(av[q]) * wv[q];
+            Tp = Tp + cmul(av[q], bv[q]) * wv[q];
+          }
+        }
+      }
+      C Xs, ratio;
+      if (dc_cls) {
+        // zero frequency: Gamma singular, the class is solved exactly
+        const T inv = (T)1 / norm2(as);
+        Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * inv;
+        ratio = cmul(bs, as) * inv;  // B_* / conj(Lambda_*)
+      } else {
+        const T iD = (T)1 / (dd + Sp + norm2(as) * ws);
+        Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * (ws * iD);
+        ratio = (Tp + cmul(as, bs) * ws) * iD;
+      }
+      C tsum = czero<C>();
+#pragma unroll
+      for (int q = 0; q < DMAX; ++q) {
+        if (q < d) {
+          const C X = (q == qs) ? Xs : (bv[q] - cmulc(av[q], ratio)) * wv[q];
+          sm[si[q]] = conjc(X);  // conjugated: the inverse runs through the forward engine
+          if (STATS) tsum = tsum + cmul(av[q], X);
+        }
+      }
+      if (STATS) {
+        const C R = Yc - tsum * (T)(1.0 / d);
+        const double wgt = (g == 0 || 2 * g == sv.Ml) ? 1.0 : 2.0;
+        acc += wgt * (double)norm2(R);
+      }
+    }
+    if (STATS) {
+      __shared__ double red[32];
+      acc = warp_sum(acc);
+      const int lane = tid & 31, warp = tid >> 5;
+      if (lane == 0) red[warp] = acc;
+      __syncthreads();
+      if (warp == 0) {
+        double v = (lane < (nthr + 31) / 32) ? red[lane] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) sv.partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (MODE == S_FOLD) return;
+  if (MODE >= S_TIK_GEN) fft_line<T, EMAX>(line, rowlen, a.f, tl, tpl, twS, 1);
+
+  for (int i = tid; i < S * rowlen; i += nthr) {
+    const int s = i / rowlen, r = i - s * rowlen, gi2 = r / TW, t2 = r - gi2 * TW;
+    if (t2 < tv) {
+      C v = sm[i];
+      if (MODE != S_FWD) v = conjc(v);
+      gbase[s * plane + (long long)gi2 * Mp + t2] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename K> static cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+static MAxis maxis(const Geometry& g) {
+  MAxis a;
+  a.M = g.M; a.H = g.M / 2; a.Ml = g.Ml; a.dr = g.dr; a.Ms = g.Ms; a.Mp = g.Mp; a.f = g.fm;
+  return a;
+}
+
+static LAxis laxis(int n, int nl, int dc, const FftAxis& f) {
+  LAxis a;
+  a.N = n; a.Nl = nl; a.dc = dc; a.f = f;
+  return a;
+}
+
+static inline bool fam3(const FftAxis& f) { return f.n % 3 == 0; }
+
+static void m_launch_shape(const Geometry& g, size_t csz, int& L, int& Hp, int& threads, size_t& smem) {
+  const int H = g.M / 2;
+  const int tpl = H / g.fm.e;
+  L = tpl >= 256 ? 1 : 256 / tpl;
+  Hp = H + (H >= 32 ? (int)(64 / csz) : 0);
+  threads = L * tpl;
+  smem = (size_t)L * Hp * csz;
+}
+
+template <typename T>
+static cudaError_t rfft_fwd_t(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw) {
+  int L, Hp, threads;
+  size_t smem;
+  m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
+  const long long nlines = (long long)g.S * g.N;
+  const unsigned blocks = (unsigned)((nlines + L - 1) / L);
+  MAxis a = maxis(g);
+  cudaError_t e;
+  if (fam3(g.fm)) {
+    if ((e = allow_smem(k_rfft_m_fwd<T, Emax<T>::p3>, smem)) != cudaSuccess) return e;
+    k_rfft_m_fwd<T, Emax<T>::p3><<<blocks, threads, smem, p.stream>>>((const T*)in, nlines, (cplx<T>*)out, a, L, Hp,
+                                                            (const cplx<T>*)tw);
+  } else {
+    if ((e = allow_smem(k_rfft_m_fwd<T, Emax<T>::p2>, smem)) != cudaSuccess) return e;
+    k_rfft_m_fwd<T, Emax<T>::p2><<<blocks, threads, smem, p.stream>>>((const T*)in, nlines, (cplx<T>*)out, a, L, Hp,
+                                                            (const cplx<T>*)tw);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t rfft_inv_t(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw,
+                              double scale) {
+  int L, Hp, threads;
+  size_t smem;
+  m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
+  const long long nlines = (long long)g.S * g.N;
+  const unsigned blocks = (unsigned)((nlines + L - 1) / L);
+  MAxis a = maxis(g);
+  cudaError_t e;
+  if (fam3(g.fm)) {
+    if ((e = allow_smem(k_rfft_m_inv<T, Emax<T>::p3>, smem)) != cudaSuccess) return e;
+    k_rfft_m_inv<T, Emax<T>::p3><<<blocks, threads, smem, p.stream>>>((const cplx<T>*)in, nlines, (T*)out, a, L, Hp,
+                                                            (const cplx<T>*)tw, (T)scale);
+  } else {
+    if ((e = allow_smem(k_rfft_m_inv<T, Emax<T>::p2>, smem)) != cudaSuccess) return e;
+    k_rfft_m_inv<T, Emax<T>::p2><<<blocks, threads, smem, p.stream>>>((const cplx<T>*)in, nlines, (T*)out, a, L, Hp,
+                                                            (const cplx<T>*)tw, (T)scale);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int EMAX>
+static cudaError_t fft_n_e(const Plan& p, const Geometry& g, void* spec, const void* tw, bool inverse) {
+  const int tpl = g.N / g.fn.e;
+  const int TW = g.tw_n;
+  const size_t smem = (size_t)g.N * TW * sizeof(cplx<T>);
+  dim3 grid((g.Ms + TW - 1) / TW, g.S);
+  LAxis a = laxis(g.N, g.Nl, g.dc, g.fn);
+  cudaError_t e;
+  if (inverse) {
+    if ((e = allow_smem(k_fft_n<T, EMAX, true>, smem)) != cudaSuccess) return e;
+    k_fft_n<T, EMAX, true><<<grid, TW * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, TW,
+                                                              (const cplx<T>*)tw);
+  } else {
+    if ((e = allow_smem(k_fft_n<T, EMAX, false>, smem)) != cudaSuccess) return e;
+    k_fft_n<T, EMAX, false><<<grid, TW * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, TW,
+                                                               (const cplx<T>*)tw);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int EMAX, int MODE, bool STATS>
+static cudaError_t fft_s_k(const Plan& p, const Geometry& g, void* spec, const void* tw, const SolveArgs& sv) {
+  const int tpl = g.S / g.fs.e;
+  const int TW = g.tw_s, G = g.g_s;
+  const size_t smem = (size_t)g.S * TW * G * sizeof(cplx<T>);
+  dim3 grid((g.Ms + TW - 1) / TW, g.N / G);
+  LAxis a = laxis(g.S, g.Sl, g.ds, g.fs);
+  cudaError_t e;
+  if ((e = allow_smem(k_fft_s<T, EMAX, MODE, STATS>, smem)) != cudaSuccess) return e;
+  k_fft_s<T, EMAX, MODE, STATS><<<grid, TW * G * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, g.N, TW, G,
+                                                                      sv, (const cplx<T>*)tw);
+  return cudaGetLastError();
+}
+
+template <typename T, int EMAX>
+static cudaError_t fft_s_e(const Plan& p, const Geometry& g, void* spec, const void* tw, int mode, bool stats,
+                           const SolveArgs& sv) {
+  switch (mode) {
+    case S_FWD: return fft_s_k<T, EMAX, S_FWD, false>(p, g, spec, tw, sv);
+    case S_INV: return fft_s_k<T, EMAX, S_INV, false>(p, g, spec, tw, sv);
+    case S_TIK_GEN: return fft_s_k<T, EMAX, S_TIK_GEN, false>(p, g, spec, tw, sv);
+    case S_TIK_USER: return fft_s_k<T, EMAX, S_TIK_USER, false>(p, g, spec, tw, sv);
+    case S_ADMM:
+      return stats ? fft_s_k<T, EMAX, S_ADMM, true>(p, g, spec, tw, sv)
+                   : fft_s_k<T, EMAX, S_ADMM, false>(p, g, spec, tw, sv);
+    case S_FOLD: return fft_s_k<T, EMAX, S_FOLD, false>(p, g, spec, tw, sv);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rfft_m_fwd(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw) {
+  return p.dtype ? rfft_fwd_t<double>(p, g, in, out, tw) : rfft_fwd_t<float>(p, g, in, out, tw);
+}
+
+cudaError_t launch_rfft_m_inv(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw,
+                              double scale) {
+  return p.dtype ? rfft_inv_t<double>(p, g, in, out, tw, scale) : rfft_inv_t<float>(p, g, in, out, tw, scale);
+}
+
+cudaError_t launch_fft_n(const Plan& p, const Geometry& g, void* spec, const void* tw, bool inverse) {
+  const bool f3 = fam3(g.fn);
+  if (p.dtype)
+    return f3 ? fft_n_e<double, Emax<double>::p3>(p, g, spec, tw, inverse)
+              : fft_n_e<double, Emax<double>::p2>(p, g, spec, tw, inverse);
+  return f3 ? fft_n_e<float, Emax<float>::p3>(p, g, spec, tw, inverse)
+            : fft_n_e<float, Emax<float>::p2>(p, g, spec, tw, inverse);
+}
+
+cudaError_t launch_fft_s(const Plan& p, const Geometry& g, void* spec, const void* tw, int mode, bool stats,
+                         const SolveArgs* sv) {
+  SolveArgs z;
+  if (!sv) {
+    memset(&z, 0, sizeof(z));
+    sv = &z;
+  }
+  const bool f3 = fam3(g.fs);
+  if (p.dtype)
+    return f3 ? fft_s_e<double, Emax<double>::p3>(p, g, spec, tw, mode, stats, *sv)
+              : fft_s_e<double, Emax<double>::p2>(p, g, spec, tw, mode, stats, *sv);
+  return f3 ? fft_s_e<float, Emax<float>::p3>(p, g, spec, tw, mode, stats, *sv)
+            : fft_s_e<float, Emax<float>::p2>(p, g, spec, tw, mode, stats, *sv);
+}
+
+long long s_pass_blocks(const Geometry& g) {
+  return (long long)((g.Ms + g.tw_s - 1) / g.tw_s) * (g.N / g.g_s);
+}
+
+}  // namespace sr3d

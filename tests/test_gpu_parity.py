@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP32 plans must match the FP64 oracle within 1e-5 relative L2;
+FP64 plans within 1e-11.  Inputs are seeded synthetic phantoms; every expected
+value comes from oracle/.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests._problems import make_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"f32": 1e-5, "f64": 1e-11}
+
+# (dims (m, n, s), dec (dr, dc, ds), dtype): several tiles with ragged tails,
+# mixed radix (96, 48, 24, 12), anisotropic and no decimation.
+CASES = [
+    ((32, 16, 8), (2, 2, 2), "f32"),
+    ((96, 24, 12), (2, 1, 3), "f32"),
+    ((64, 32, 32), (1, 1, 4), "f32"),
+    ((64, 48, 16), (2, 2, 1), "f32"),
+    ((128, 64, 32), (4, 2, 1), "f32"),
+    ((32, 16, 8), (1, 1, 1), "f32"),
+    ((32, 32, 32), (2, 2, 2), "f64"),
+    ((96, 24, 12), (2, 1, 3), "f64"),
+]
+IDS = [f"{d[0]}x{d[1]}x{d[2]}_d{c[0]}{c[1]}{c[2]}_{t}" for d, c, t in CASES]
+
+
+def T(a, dtype):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a), dtype={"f32": torch.float32, "f64": torch.float64}[dtype],
+                        device="cuda")
+
+
+def H(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+@pytest.fixture(scope="module", params=list(range(len(CASES))), ids=IDS)
+def case(request, lib):
+    dims, dec, dtype = CASES[request.param]
+    psf, x, y = make_problem(dims, dec, sigma=(1.0, 0.8, 1.2), seed=11 + request.param, asym=True)
+    plan = lib.Plan(dims, dec, psf, dtype)
+    yield dict(dims=dims, dec=dec, dtype=dtype, psf=psf, x=x, y=y, plan=plan)
+    plan.close()
+
+
+def test_otf(case):
+    m = case["dims"][0]
+    ref = O.otf(case["psf"], case["x"].shape)[..., : m // 2 + 1]
+    got = case["plan"].get_otf().cpu().numpy()
+    assert rel_l2(got, ref) < TOL[case["dtype"]]
+
+
+def test_fft3(case):
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(case["x"].shape)
+    m = case["dims"][0]
+    got = case["plan"].fft3(T(x, case["dtype"])).cpu().numpy()
+    assert rel_l2(got, np.fft.fftn(x)[..., : m // 2 + 1]) < TOL[case["dtype"]]
+
+
+def test_forward_model(case):
+    got = H(case["plan"].forward(T(case["x"], case["dtype"])))
+    assert rel_l2(got, O.forward(case["x"], case["psf"], case["dec"])) < TOL[case["dtype"]]
+
+
+@pytest.mark.parametrize("prior", ["zero", "nearest", "user"])
+@pytest.mark.parametrize("tau", [1e-2, 0.5])
+def test_tikhonov(case, prior, tau):
+    y, dec, dt = case["y"], case["dec"], case["dtype"]
+    if prior == "zero":
+        xbar_o, xbar_g = None, None
+    elif prior == "nearest":
+        xbar_o, xbar_g = O.nearest_neighbour(y, dec), "nearest"
+    else:
+        xbar_o = np.random.default_rng(5).standard_normal(case["x"].shape)
+        xbar_g = T(xbar_o, dt)
+    ref = O.tikhonov(y, case["psf"], dec, tau, xbar_o)
+    got = H(case["plan"].tikhonov(T(y, dt), tau, xbar=xbar_g))
+    assert rel_l2(got, ref) < TOL[dt]
+
+
+def test_xstep(case):
+    rng = np.random.default_rng(6)
+    shape = case["x"].shape
+    rho = 0.05 * rng.standard_normal((3,) + shape)
+    theta = O.grad_adj(rho)
+    mu = 2e-2
+    ref = O.admm_xstep(case["y"], O.otf(case["psf"], shape), theta, mu, case["dec"])
+    got = H(case["plan"].xstep(T(case["y"], case["dtype"]), T(theta, case["dtype"]), mu))
+    assert rel_l2(got, ref) < TOL[case["dtype"]]
+
+
+def test_tv_step(case):
+    rng = np.random.default_rng(7)
+    x, dt = case["x"], case["dtype"]
+    d = 0.01 * rng.standard_normal((3,) + x.shape)
+    lam, mu = 1e-3, 1e-2
+    g = O.grad(x)
+    u = O.shrink(g + d, lam / mu)
+    d_new = d + g - u
+    theta = O.grad_adj(u - d_new)
+    d_got, th_got = case["plan"].tv_step(T(x, dt), T(d, dt), lam, mu)
+    assert rel_l2(H(d_got), d_new) < TOL[dt]
+    assert rel_l2(H(th_got), theta) < TOL[dt]
+
+
+def test_admm_iterates(case):
+    y, psf, dec, dt = case["y"], case["psf"], case["dec"], case["dtype"]
+    lam, mu, tau0, iters = 1e-3, 1e-2, 1e-2, 10
+    x0 = O.tikhonov(y, psf, dec, tau0, O.nearest_neighbour(y, dec))
+    ref = O.admm_tv(y, psf, dec, lam, mu, iters, x0, record=True)
+    import torch
+    x = T(np.zeros_like(x0), dt)
+    d = torch.zeros((3,) + x0.shape, dtype=x.dtype, device="cuda")
+    st = case["plan"].admm_tv(T(y, dt), x, lam, mu, iters, d=d, tau_init=tau0, eval_every=1, hist_len=iters)
+    assert rel_l2(H(x), ref["x"]) < TOL[dt]
+    assert rel_l2(H(d), ref["d"]) < (TOL[dt] * 10 if dt == "f32" else TOL[dt])
+    hist = np.array(st["objective_hist"])
+    assert np.allclose(hist, ref["hist"]["objective"], rtol=TOL[dt] * 10, atol=0)
+    assert st["iters"] == iters and st["evals"] == iters
+    assert np.isclose(st["primal"], ref["hist"]["primal"][-1], rtol=1e-4)
+    assert np.isclose(st["dual"], ref["hist"]["dual"][-1], rtol=1e-3)
+
+
+def test_admm_from_given_x0_and_d0(case):
+    y, psf, dec, dt = case["y"], case["psf"], case["dec"], case["dtype"]
+    rng = np.random.default_rng(8)
+    x0 = case["x"] + 0.05 * rng.standard_normal(case["x"].shape)
+    d0 = 0.02 * rng.standard_normal((3,) + x0.shape)
+    ref = O.admm_tv(y, psf, dec, 2e-3, 5e-2, 4, x0, d0=d0)
+    x = T(x0, dt)
+    d = T(d0, dt)
+    case["plan"].admm_tv(T(y, dt), x, 2e-3, 5e-2, 4, d=d, tau_init=0.0)
+    assert rel_l2(H(x), ref["x"]) < TOL[dt]
+    assert rel_l2(H(d), ref["d"]) < (TOL[dt] * 10 if dt == "f32" else TOL[dt])
+
+
+def test_host_buffers_match_device_call(lib):
+    import torch
+    dims, dec = (64, 32, 16), (2, 2, 2)
+    psf, xt, y = make_problem(dims, dec, seed=21)
+    plan = lib.Plan(dims, dec, psf, "f32")
+    yd = T(y, "f32")
+    xd = plan.empty_hr()
+    plan.admm_tv(yd, xd, 1e-3, 1e-2, 5, tau_init=1e-2)
+    yh = yd.cpu().pin_memory()
+    xh = torch.empty(xd.shape, dtype=torch.float32).pin_memory()
+    plan.admm_tv_host(yh, xh, 1e-3, 1e-2, 5, tau_init=1e-2)
+    assert torch.equal(xh, xd.cpu())
+    plan.close()
+
+
+def test_tolerance_stop_and_zero_iterations(lib):
+    dims, dec = (32, 32, 32), (2, 2, 2)
+    psf, xt, y = make_problem(dims, dec, seed=22)
+    plan = lib.Plan(dims, dec, psf, "f64")
+    x = plan.empty_hr()
+    st = plan.admm_tv(T(y, "f64"), x, 1e-3, 1e-2, 400, tol=1e-3, tau_init=1e-2, eval_every=5)
+    assert st["converged"] and st["iters"] % 5 == 0 and st["iters"] < 400
+    assert st["primal_rel"] < 1e-3 and st["dual_rel"] < 1e-3
+    x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
+    ref = O.admm_tv(y, psf, dec, 1e-3, 1e-2, st["iters"], x0, record=True)
+    assert rel_l2(H(x), ref["x"]) < 1e-10
+    rel_p = ref["hist"]["primal"][-1] / max(ref["hist"]["norm_Lx"][-1], ref["hist"]["norm_u"][-1])
+    assert np.isclose(st["primal_rel"], rel_p, rtol=1e-6)
+    # zero iterations returns the Tikhonov start
+    x2 = plan.empty_hr()
+    plan.admm_tv(T(y, "f64"), x2, 1e-3, 1e-2, 0, tau_init=1e-2)
+    assert rel_l2(H(x2), x0) < 1e-11
+    plan.close()
+
+
+def test_errors(lib):
+    import torch
+    dims, dec = (32, 16, 8), (2, 2, 2)
+    psf, xt, y = make_problem(dims, dec, seed=23)
+    plan = lib.Plan(dims, dec, psf, "f32")
+    yd = T(y, "f32")
+    with pytest.raises(lib.Sr3dError) as e:
+        plan.tikhonov(yd, 0.0)
+    assert e.value.name == "INVALID_ARG"
+    with pytest.raises(lib.Sr3dError):
+        plan.admm_tv(yd, plan.empty_hr(), 1e-3, -1.0, 3)
+    plan.close()
+    zero = np.zeros((3, 3, 3))
+    zero[1, 1, 0], zero[1, 1, 2] = 1.0, -1.0  # taps summing to zero
+    p2 = lib.Plan(dims, dec, zero, "f32")
+    with pytest.raises(lib.Sr3dError) as e:
+        p2.admm_tv(yd, p2.empty_hr(), 1e-3, 1e-2, 3)
+    assert e.value.name == "SINGULAR"
+    p2.close()
+    with pytest.raises(ValueError):
+        lib.Plan(dims, dec, psf, "f32").tikhonov(torch.zeros(3, device="cuda"), 1.0)
+
+
+def test_headline_size_against_oracle(lib):
+    """256^3, d = 2x2x2, sigma 1.5, the benchmark's launch configuration:
+    Tikhonov start plus two ADMM-TV iterations, compared element by element."""
+    from synth import HEADLINE_256 as W
+    psf = W.psf()
+    x = W.phantom()
+    clean = O.forward(x, psf, W.dec)
+    from synth import noise_sigma
+    y = clean + noise_sigma(clean, W.snr_db) * W.noise()
+    plan = lib.Plan(W.dims, W.dec, psf, "f32")
+    x0 = O.tikhonov(y, psf, W.dec, W.tau, O.nearest_neighbour(y, W.dec))
+    xg = plan.empty_hr()
+    plan.tikhonov(T(y, "f32"), W.tau, xg, xbar="nearest")
+    assert rel_l2(H(xg), x0) < TOL["f32"]
+    ref = O.admm_tv(y, psf, W.dec, W.lam, W.mu, 2, x0)
+    plan.admm_tv(T(y, "f32"), xg, W.lam, W.mu, 2, tau_init=W.tau)
+    assert rel_l2(H(xg), ref["x"]) < TOL["f32"]
+    plan.close()
