@@ -21,3 +21,15 @@ def lib():
         pytest.skip("no CUDA device")
     import paper_2010_15491_gb300 as sr3d
     return sr3d
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """With SR3D_PARITY_REPORT=path, write every recorded parity error there (JSON)."""
+    path = os.environ.get("SR3D_PARITY_REPORT")
+    if not path:
+        return
+    from tests._problems import REPORT
+    if REPORT:
+        import json
+        with open(path, "w") as f:
+            json.dump(REPORT, f, indent=1, sort_keys=True)

@@ -39,6 +39,12 @@ def H(t):
     return t.detach().cpu().numpy().astype(np.float64)
 
 
+@pytest.fixture
+def tag(request):
+    """Name under which a test records its parity errors."""
+    return lambda what: f"{request.node.name}:{what}"
+
+
 @pytest.fixture(scope="module", params=list(range(len(CASES))), ids=IDS)
 def case(request, lib):
     dims, dec, dtype = CASES[request.param]
@@ -48,29 +54,29 @@ def case(request, lib):
     plan.close()
 
 
-def test_otf(case):
+def test_otf(case, tag):
     m = case["dims"][0]
     ref = O.otf(case["psf"], case["x"].shape)[..., : m // 2 + 1]
     got = case["plan"].get_otf().cpu().numpy()
-    assert rel_l2(got, ref) < TOL[case["dtype"]]
+    assert rel_l2(got, ref, tag("otf")) < TOL[case["dtype"]]
 
 
-def test_fft3(case):
+def test_fft3(case, tag):
     rng = np.random.default_rng(3)
     x = rng.standard_normal(case["x"].shape)
     m = case["dims"][0]
     got = case["plan"].fft3(T(x, case["dtype"])).cpu().numpy()
-    assert rel_l2(got, np.fft.fftn(x)[..., : m // 2 + 1]) < TOL[case["dtype"]]
+    assert rel_l2(got, np.fft.fftn(x)[..., : m // 2 + 1], tag("fft3")) < TOL[case["dtype"]]
 
 
-def test_forward_model(case):
+def test_forward_model(case, tag):
     got = H(case["plan"].forward(T(case["x"], case["dtype"])))
-    assert rel_l2(got, O.forward(case["x"], case["psf"], case["dec"])) < TOL[case["dtype"]]
+    assert rel_l2(got, O.forward(case["x"], case["psf"], case["dec"]), tag("DHx")) < TOL[case["dtype"]]
 
 
 @pytest.mark.parametrize("prior", ["zero", "nearest", "user"])
 @pytest.mark.parametrize("tau", [1e-2, 0.5])
-def test_tikhonov(case, prior, tau):
+def test_tikhonov(case, prior, tau, tag):
     y, dec, dt = case["y"], case["dec"], case["dtype"]
     if prior == "zero":
         xbar_o, xbar_g = None, None
@@ -81,10 +87,10 @@ def test_tikhonov(case, prior, tau):
         xbar_g = T(xbar_o, dt)
     ref = O.tikhonov(y, case["psf"], dec, tau, xbar_o)
     got = H(case["plan"].tikhonov(T(y, dt), tau, xbar=xbar_g))
-    assert rel_l2(got, ref) < TOL[dt]
+    assert rel_l2(got, ref, tag("x")) < TOL[dt]
 
 
-def test_xstep(case):
+def test_xstep(case, tag):
     rng = np.random.default_rng(6)
     shape = case["x"].shape
     rho = 0.05 * rng.standard_normal((3,) + shape)
@@ -92,10 +98,10 @@ def test_xstep(case):
     mu = 2e-2
     ref = O.admm_xstep(case["y"], O.otf(case["psf"], shape), theta, mu, case["dec"])
     got = H(case["plan"].xstep(T(case["y"], case["dtype"]), T(theta, case["dtype"]), mu))
-    assert rel_l2(got, ref) < TOL[case["dtype"]]
+    assert rel_l2(got, ref, tag("x")) < TOL[case["dtype"]]
 
 
-def test_tv_step(case):
+def test_tv_step(case, tag):
     rng = np.random.default_rng(7)
     x, dt = case["x"], case["dtype"]
     d = 0.01 * rng.standard_normal((3,) + x.shape)
@@ -105,11 +111,11 @@ def test_tv_step(case):
     d_new = d + g - u
     theta = O.grad_adj(u - d_new)
     d_got, th_got = case["plan"].tv_step(T(x, dt), T(d, dt), lam, mu)
-    assert rel_l2(H(d_got), d_new) < TOL[dt]
-    assert rel_l2(H(th_got), theta) < TOL[dt]
+    assert rel_l2(H(d_got), d_new, tag("d")) < TOL[dt]
+    assert rel_l2(H(th_got), theta, tag("theta")) < TOL[dt]
 
 
-def test_admm_iterates(case):
+def test_admm_iterates(case, tag):
     y, psf, dec, dt = case["y"], case["psf"], case["dec"], case["dtype"]
     lam, mu, tau0, iters = 1e-3, 1e-2, 1e-2, 10
     x0 = O.tikhonov(y, psf, dec, tau0, O.nearest_neighbour(y, dec))
@@ -118,8 +124,9 @@ def test_admm_iterates(case):
     x = T(np.zeros_like(x0), dt)
     d = torch.zeros((3,) + x0.shape, dtype=x.dtype, device="cuda")
     st = case["plan"].admm_tv(T(y, dt), x, lam, mu, iters, d=d, tau_init=tau0, eval_every=1, hist_len=iters)
-    assert rel_l2(H(x), ref["x"]) < TOL[dt]
-    assert rel_l2(H(d), ref["d"]) < (TOL[dt] * 10 if dt == "f32" else TOL[dt])
+    assert rel_l2(H(x), ref["x"], tag("x")) < TOL[dt]
+    assert rel_l2(H(d), ref["d"], tag("d")) < (TOL[dt] * 10 if dt == "f32" else TOL[dt])
+    rel_l2(hist_np := np.array(st["objective_hist"]), np.array(ref["hist"]["objective"]), tag("objective"))
     hist = np.array(st["objective_hist"])
     assert np.allclose(hist, ref["hist"]["objective"], rtol=TOL[dt] * 10, atol=0)
     assert st["iters"] == iters and st["evals"] == iters
@@ -127,7 +134,7 @@ def test_admm_iterates(case):
     assert np.isclose(st["dual"], ref["hist"]["dual"][-1], rtol=1e-3)
 
 
-def test_admm_from_given_x0_and_d0(case):
+def test_admm_from_given_x0_and_d0(case, tag):
     y, psf, dec, dt = case["y"], case["psf"], case["dec"], case["dtype"]
     rng = np.random.default_rng(8)
     x0 = case["x"] + 0.05 * rng.standard_normal(case["x"].shape)
@@ -136,8 +143,8 @@ def test_admm_from_given_x0_and_d0(case):
     x = T(x0, dt)
     d = T(d0, dt)
     case["plan"].admm_tv(T(y, dt), x, 2e-3, 5e-2, 4, d=d, tau_init=0.0)
-    assert rel_l2(H(x), ref["x"]) < TOL[dt]
-    assert rel_l2(H(d), ref["d"]) < (TOL[dt] * 10 if dt == "f32" else TOL[dt])
+    assert rel_l2(H(x), ref["x"], tag("x")) < TOL[dt]
+    assert rel_l2(H(d), ref["d"], tag("d")) < (TOL[dt] * 10 if dt == "f32" else TOL[dt])
 
 
 def test_host_buffers_match_device_call(lib):
@@ -198,7 +205,7 @@ def test_errors(lib):
         lib.Plan(dims, dec, psf, "f32").tikhonov(torch.zeros(3, device="cuda"), 1.0)
 
 
-def test_headline_size_against_oracle(lib):
+def test_headline_size_against_oracle(lib, tag):
     """256^3, d = 2x2x2, sigma 1.5, the benchmark's launch configuration:
     Tikhonov start plus two ADMM-TV iterations, compared element by element."""
     from synth import HEADLINE_256 as W
@@ -211,8 +218,8 @@ def test_headline_size_against_oracle(lib):
     x0 = O.tikhonov(y, psf, W.dec, W.tau, O.nearest_neighbour(y, W.dec))
     xg = plan.empty_hr()
     plan.tikhonov(T(y, "f32"), W.tau, xg, xbar="nearest")
-    assert rel_l2(H(xg), x0) < TOL["f32"]
+    assert rel_l2(H(xg), x0, tag("tikhonov")) < TOL["f32"]
     ref = O.admm_tv(y, psf, W.dec, W.lam, W.mu, 2, x0)
     plan.admm_tv(T(y, "f32"), xg, W.lam, W.mu, 2, tau_init=W.tau)
-    assert rel_l2(H(xg), ref["x"]) < TOL["f32"]
+    assert rel_l2(H(xg), ref["x"], tag("admm2")) < TOL["f32"]
     plan.close()
