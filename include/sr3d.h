@@ -179,6 +179,27 @@ int sr3d_tv_step(sr3d_plan_t plan, const void* x_dev, const void* d_in_dev, void
 int sr3d_profile(sr3d_plan_t plan, int on);
 int sr3d_profile_read(sr3d_plan_t plan, double ms[SR3D_NKINDS], long long launches[SR3D_NKINDS]);
 
+/* Allocation-free Tikhonov solve (no counterpart in the paper: an
+ * interface for callers that cannot allocate device memory once running,
+ * such as real-time reconstruction loops with a fixed memory budget or code
+ * inside CUDA stream capture, where cudaMalloc is not allowed).  Same result
+ * as sr3d_plan + sr3d_tikhonov + sr3d_destroy for the descriptor `desc`
+ * (desc->stream NULL = the legacy default stream), but every piece of work
+ * memory is carved from one file-scope device array of SR3D_NOALLOC_BYTES
+ * (8 MiB), held by every GPU that loads the library until the process exits;
+ * the call makes no cudaMalloc/cudaFree and no allocating library call.
+ * The work memory is about 8 bytes per HR voxel in FP32 (16 in FP64), so
+ * volumes up to about 2^19 HR voxels in FP32 (e.g. 128 x 64 x 64) or 2^18 in
+ * FP64 fit; larger ones fail with SR3D_ERR_UNSUPPORTED_SIZE.
+ * The first call on a device looks up the array's device address (make it
+ * before any stream capture).  All calls share the array and every call
+ * overwrites it, so calls that overlap on the GPU (other streams, other host
+ * threads) race; serialise them.  Inputs and outputs are the caller's device
+ * arrays as in sr3d_tikhonov. */
+#define SR3D_NOALLOC_BYTES (8u << 20)
+int sr3d_tikhonov_noalloc(const sr3d_desc* desc, const void* y_dev, const void* xbar_dev, double tau,
+                          void* x_dev);
+
 /* Plan facts for callers and tests: sizes[0..8] = m_h, n_h, s_h, m_l, n_l,
  * s_l, m-slots, m-pitch, dtype; bytes = device memory the plan holds. */
 int sr3d_plan_info(sr3d_plan_t plan, int sizes[9], long long* bytes);

@@ -31,7 +31,7 @@ XBAR_NEAREST = ctypes.c_void_p(1)
 EXPORTED = [
     "sr3d_plan", "sr3d_destroy", "sr3d_forward", "sr3d_tikhonov", "sr3d_admm_tv", "sr3d_admm_tv_host",
     "sr3d_last_error", "sr3d_get_otf", "sr3d_fft3", "sr3d_xstep", "sr3d_tv_step", "sr3d_plan_info",
-    "sr3d_profile", "sr3d_profile_read",
+    "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc",
 ]
 KINDS = ["tv", "rfft_m_fwd", "fft_n_fwd", "fft_s", "fft_n_inv", "rfft_m_inv", "other", "setup"]
 
@@ -86,6 +86,7 @@ def load() -> ctypes.CDLL:
         "sr3d_plan_info": (i, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_longlong)]),
         "sr3d_profile": (i, [vp, i]),
         "sr3d_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
+        "sr3d_tikhonov_noalloc": (i, [ctypes.POINTER(Desc), vp, vp, d, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -275,3 +276,29 @@ class Plan:
         if st.hist_len > 0:
             out["objective_hist"] = [hist[i] for i in range(min(st.evals, st.hist_len))]
         return out
+
+
+def tikhonov_noalloc(dims, dec, psf, y, tau: float, x, xbar=None, dtype: str = "f32", stream=None):
+    """Allocation-free Tikhonov solve (sr3d_tikhonov_noalloc): same result as
+    Plan(dims, dec, psf, dtype).tikhonov(y, tau, x, xbar) but all device work
+    memory comes from the library's fixed scratch array; y and x are the
+    caller's CUDA tensors.  Calls that overlap on the GPU race."""
+    import torch
+    L = load()
+    psf = np.ascontiguousarray(psf, dtype=np.float64)
+    m, n, s = (int(v) for v in dims)
+    dr, dc, ds = (int(v) for v in dec)
+    td = {"f32": torch.float32, "f64": torch.float64}[dtype]
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    desc = Desc(m, n, s, dr, dc, ds, psf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                psf.shape[2], psf.shape[1], psf.shape[0], 0 if dtype == "f32" else 1,
+                ctypes.c_void_p(handle) if handle else None)
+    if isinstance(xbar, str):
+        if xbar != "nearest":
+            raise ValueError("xbar must be None, 'nearest' or a tensor")
+        xb = XBAR_NEAREST
+    else:
+        xb = _ptr(xbar, td, (s, n, m)) if xbar is not None else None
+    _check(L.sr3d_tikhonov_noalloc(ctypes.byref(desc), _ptr(y, td, (s // ds, n // dc, m // dr)), xb, float(tau),
+                                   _ptr(x, td, (s, n, m))))
+    return x

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -578,3 +579,116 @@ int sr3d_admm_tv_host(sr3d_plan_t plan, const void* y_host, void* x_host, double
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free Tikhonov solve.
+//
+// For callers that must not allocate device memory once they are running:
+// hard real-time reconstruction loops and embedded scanner software with a
+// fixed device-memory budget decided at start-up, and code that runs while a
+// CUDA stream is being captured, where cudaMalloc is not allowed.  All the
+// work memory (twiddle and symbol tables, Lambda, the LR spectrum, the HR
+// spectrum) lives in one file-scope device array of SR3D_NOALLOC_BYTES, so
+// every GPU that loads this library holds it until the process exits.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SR3D_NOALLOC_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_dev_ptr[256];  // device address of g_noalloc_scratch, per device
+
+// Set-up, once per device, with that device current: the host-side name of a
+// __device__ array is only a stand-in, so the kernels get its device address.
+static int noalloc_scratch(void** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 256) return fail(SR3D_ERR_INVALID_ARG, "device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_dev_ptr[dev]) {
+    void* ptr = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+      return fail(SR3D_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+    g_noalloc_dev_ptr[dev] = ptr;
+  }
+  *out = g_noalloc_dev_ptr[dev];
+  return SR3D_OK;
+}
+
+extern "C" int sr3d_tikhonov_noalloc(const sr3d_desc* d, const void* y, const void* xbar, double tau, void* x) {
+  if (!d || !y || !x || !d->psf) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  if (!(tau > 0) || !std::isfinite(tau)) return fail(SR3D_ERR_INVALID_ARG, "tau must be positive and finite");
+  if (d->m_h <= 0 || d->n_h <= 0 || d->s_h <= 0 || d->dr <= 0 || d->dc <= 0 || d->ds <= 0 || d->p_m <= 0 ||
+      d->p_n <= 0 || d->p_s <= 0)
+    return fail(SR3D_ERR_INVALID_ARG, "sizes and decimation factors must be positive");
+  if (d->dtype != SR3D_F32 && d->dtype != SR3D_F64) return fail(SR3D_ERR_INVALID_ARG, "dtype must be F32 or F64");
+  if (d->m_h % d->dr || d->n_h % d->dc || d->s_h % d->ds)
+    return fail(SR3D_ERR_NOT_DIVISIBLE, "HR sizes not divisible by the decimation factors");
+  if (d->p_m > d->m_h || d->p_n > d->n_h || d->p_s > d->s_h)
+    return fail(SR3D_ERR_INVALID_ARG, "PSF larger than the volume");
+  if (d->m_h % 32 || d->n_h % 8 || d->s_h < 4 || d->m_h > 2048 || d->n_h > 2048 || d->s_h > 2048 ||
+      !supported_len(d->m_h) || !supported_len(d->n_h) || !supported_len(d->s_h) || (d->m_h / d->dr) % 2 ||
+      d->dr * d->dc * d->ds > 8)
+    return fail(SR3D_ERR_UNSUPPORTED_SIZE, "sizes outside the supported set of sr3d_plan");
+
+  Plan p;
+  p.dtype = d->dtype;
+  p.esz = p.dtype ? 8 : 4;
+  const size_t csz = 2 * p.esz;
+  p.hr = make_geom(d->m_h, d->n_h, d->s_h, d->dr, d->dc, d->ds, csz);
+  p.lr = make_geom(p.hr.Ml, p.hr.Nl, p.hr.Sl, 1, 1, 1, csz);
+  TRY(validate_lengths(p.hr, csz));
+  TRY(validate_lengths(p.lr, csz));
+  p.stream = (cudaStream_t)d->stream;
+  p.own_stream = false;
+
+  // carve the scratch array: 256-byte aligned pieces
+  const long long np = (long long)d->p_m * d->p_n * d->p_s;
+  const Geometry& g = p.hr;
+  const Geometry& l = p.lr;
+  const size_t sizes[12] = {(size_t)g.M * csz, (size_t)g.N * csz, (size_t)g.S * csz, (size_t)l.M * csz,
+                            (size_t)l.N * csz, (size_t)l.S * csz, (size_t)g.M * p.esz, (size_t)g.N * p.esz,
+                            (size_t)g.S * p.esz, (size_t)g.spec_elems() * csz, (size_t)g.spec_elems() * csz,
+                            (size_t)l.spec_elems() * csz};
+  size_t need = 0, off[14];
+  for (int i = 0; i < 12; ++i) {
+    off[i] = need;
+    need += (sizes[i] + 255) & ~(size_t)255;
+  }
+  off[12] = need;
+  need += ((size_t)np * sizeof(double) + 255) & ~(size_t)255;
+  if (need > (size_t)SR3D_NOALLOC_BYTES)
+    return fail(SR3D_ERR_UNSUPPORTED_SIZE,
+                "volume needs %zu bytes of work memory; the allocation-free path holds %u (use sr3d_plan)", need,
+                (unsigned)SR3D_NOALLOC_BYTES);
+  void* base = nullptr;
+  TRY(noalloc_scratch(&base));
+  unsigned char* b = (unsigned char*)base;
+  p.twM = b + off[0]; p.twN = b + off[1]; p.twS = b + off[2];
+  p.twMl = b + off[3]; p.twNl = b + off[4]; p.twSl = b + off[5];
+  p.symM = b + off[6]; p.symN = b + off[7]; p.symS = b + off[8];
+  p.lam = b + off[9];
+  p.spec = b + off[10];
+  p.yhat = b + off[11];
+  p.theta = p.spec;  // the wrapped PSF (real HR volume) only lives until Lambda is formed
+  double* psf_dev = (double*)(b + off[12]);
+
+  CK(launch_twiddle(p, p.twM, g.M));
+  CK(launch_twiddle(p, p.twN, g.N));
+  CK(launch_twiddle(p, p.twS, g.S));
+  CK(launch_twiddle(p, p.twMl, l.M));
+  CK(launch_twiddle(p, p.twNl, l.N));
+  CK(launch_twiddle(p, p.twSl, l.S));
+  CK(launch_symbol(p, p.symM, g.M));
+  CK(launch_symbol(p, p.symN, g.N));
+  CK(launch_symbol(p, p.symS, g.S));
+  CK(cudaMemcpyAsync(psf_dev, d->psf, (size_t)np * sizeof(double), cudaMemcpyHostToDevice, p.stream));
+  CK(cudaMemsetAsync(p.theta, 0, (size_t)g.V() * p.esz, p.stream));  // the wrap fills only the PSF taps
+  CK(launch_wrap_psf(p, p.theta, psf_dev, d->p_m, d->p_n, d->p_s));
+  CK(launch_rfft_m_fwd(p, g, p.theta, p.lam, p.twM));
+  CK(launch_fft_n(p, g, p.lam, p.twN, false));
+  CK(launch_fft_s(p, g, p.lam, p.twS, S_FWD, false, nullptr));
+  TRY(lr_spectrum(p, y));
+  TRY(tikhonov_core(p, xbar, tau, x));
+  CK(cudaStreamSynchronize(p.stream));
+  return SR3D_OK;
+}
