@@ -92,10 +92,20 @@ static FftAxis make_axis(int n, size_t esz) {
       if (c <= p2 && c <= n && n % c == 0) { f.e = c; break; }
   }
   int rest = n;
-  if (rest % 3 == 0) { f.radix[f.nst++] = 3; rest /= 3; }
-  const int rads[4] = {16, 8, 4, 2};
-  for (int r : rads)
-    while (rest % r == 0 && f.e % r == 0) { f.radix[f.nst++] = r; rest /= r; }
+  if (rest % 3 == 0) {
+    f.radix[f.nst++] = 3;
+    rest /= 3;
+    const int rads[3] = {4, 2, 1};
+    for (int r : rads)
+      while (r > 1 && rest % r == 0 && f.e % r == 0) { f.radix[f.nst++] = r; rest /= r; }
+    return f;
+  }
+  // powers of two: [remainder, P, P, ...] with P = e when e is the full
+  // 16 (float) or 8 (double): later stages then use one radix only
+  int big = 0, pw = f.e;
+  while (rest % pw == 0 && pw > 1) { rest /= pw; ++big; }
+  if (rest > 1) f.radix[f.nst++] = rest;  // 2, 4 or 8 (< pw, divides e)
+  for (int i = 0; i < big; ++i) f.radix[f.nst++] = pw;
   return f;
 }
 

@@ -4,12 +4,17 @@
 // tpl = n / e threads; every Stockham stage (self-sorting, decimation in
 // time) loads e elements per thread into registers, applies the twiddles,
 // barriers, runs e / R radix-R butterflies and stores back in place, so the
-// shared footprint is one tile.  Radices 2, 3, 4, 8 and 16 cover every length
+// shared footprint is one tile.  The first stage reads its inputs straight
+// from global memory (all e loads of a thread in flight at once) and the last
+// stage writes straight to global memory, so a two-stage length such as
+// 256 = 16 x 16 crosses shared memory once.  Radices 2, 3, 4, 8 and 16 cover every length
 // 2^a and 3 * 2^a.  The transform is the unnormalised forward DFT
 // X[k] = sum_j x[j] exp(-2 pi i j k / n); inverses conjugate on the way in
 // and out.  Butterfly constants are the exact values cos(2 pi j / 16),
 // sin(2 pi j / 16) and sqrt(3)/2 written as decimal literals.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace sr3d {
@@ -145,28 +150,221 @@ __device__ __forceinline__ void fft_stage(cplx<T>* line, int es, int n, int Ns, 
   __syncthreads();
 }
 
-// Full forward transform of one line; every thread of the CTA must call it
-// (it contains barriers), with its own line pointer and thread-in-line index.
-template <typename T, int EMAX>
-__device__ __forceinline__ void fft_line(cplx<T>* line, int es, const FftAxis& ax, int tl, int tpl,
-                                         const cplx<T>* __restrict__ tw, int tws) {
-  int Ns = 1;
-  for (int st = 0; st < ax.nst; ++st) {
-    const int R = ax.radix[st];
-    const int nb = ax.e / R;
-    if (R == 2) {
-      fft_stage<T, 2, EMAX>(line, es, ax.n, Ns, tl, tpl, nb, tw, tws);
-    } else if (R == 4) {
-      if constexpr (EMAX % 4 == 0) fft_stage<T, 4, EMAX>(line, es, ax.n, Ns, tl, tpl, nb, tw, tws);
-    } else if (R == 8) {
-      if constexpr (EMAX % 8 == 0) fft_stage<T, 8, EMAX>(line, es, ax.n, Ns, tl, tpl, nb, tw, tws);
-    } else if (R == 16) {
-      if constexpr (EMAX % 16 == 0) fft_stage<T, 16, EMAX>(line, es, ax.n, Ns, tl, tpl, nb, tw, tws);
-    } else if (R == 3) {
-      if constexpr (EMAX % 3 == 0) fft_stage<T, 3, EMAX>(line, es, ax.n, Ns, tl, tpl, nb, tw, tws);
-    }
-    Ns *= R;
+// Calls f(std::integral_constant<int, R>) for the runtime radix R.
+template <int EMAX, class F> __device__ __forceinline__ void with_radix(int R, F&& f) {
+  if (R == 2) {
+    f(std::integral_constant<int, 2>{});
+  } else if (R == 4) {
+    if constexpr (EMAX % 4 == 0) f(std::integral_constant<int, 4>{});
+  } else if (R == 8) {
+    if constexpr (EMAX % 8 == 0) f(std::integral_constant<int, 8>{});
+  } else if (R == 16) {
+    if constexpr (EMAX % 16 == 0) f(std::integral_constant<int, 16>{});
+  } else if (R == 3) {
+    if constexpr (EMAX % 3 == 0) f(std::integral_constant<int, 3>{});
   }
+}
+
+// Radices after the first stage.  Power-of-two lengths are planned as
+// [remainder, P, P, ...] with P = EMAX (16 for float, 8 for double), so only
+// the first stage needs the small radices; this keeps the inlined stage
+// variants, and with them register pressure, down.
+template <int EMAX, class F> __device__ __forceinline__ void with_radix_tail(int R, F&& f) {
+  if constexpr (EMAX == 16 || EMAX == 8) {
+    if (R == EMAX) f(std::integral_constant<int, EMAX>{});
+  } else {
+    with_radix<EMAX>(R, f);
+  }
+}
+
+// First stage (no twiddles): ld(i) gives element i of the line; results go
+// to shared memory.  No barrier inside: the caller syncs afterwards.
+template <typename T, int R, int EMAX, class Ld>
+__device__ __forceinline__ void stage_first_to_smem(const Ld& ld, cplx<T>* line, int es, int n, int tl, int tpl,
+                                                    int nb) {
+  using C = cplx<T>;
+  constexpr int NBMAX = EMAX / R;
+  C v[NBMAX * R];
+  const int nr = n / R;
+#pragma unroll
+  for (int u = 0; u < NBMAX; ++u)
+    if (u < nb) {
+      const int j = tl + u * tpl;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[u * R + r] = ld(j + r * nr);
+    }
+#pragma unroll
+  for (int u = 0; u < NBMAX; ++u)
+    if (u < nb) {
+      Dft<R, C, T>::run(&v[u * R]);
+      const int j = tl + u * tpl;
+#pragma unroll
+      for (int r = 0; r < R; ++r) line[(j * R + r) * es] = v[u * R + r];
+    }
+}
+
+// Last stage: reads shared memory (twiddled), st(i, v) stores output element i.
+template <typename T, int R, int EMAX, class St>
+__device__ __forceinline__ void stage_last_to_global(const cplx<T>* line, int es, const St& st, int n, int Ns,
+                                                     int tl, int tpl, int nb, const cplx<T>* __restrict__ tw,
+                                                     int tws) {
+  using C = cplx<T>;
+  constexpr int NBMAX = EMAX / R;
+  C v[NBMAX * R];
+  const int nr = n / R;
+  const int step = (n / (Ns * R)) * tws;
+#pragma unroll
+  for (int u = 0; u < NBMAX; ++u)
+    if (u < nb) {
+      const int j = tl + u * tpl;
+      const int jm = j % Ns;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        C a = line[(j + r * nr) * es];
+        if (r > 0 && Ns > 1) a = cmul(a, __ldg(&tw[jm * r * step]));
+        v[u * R + r] = a;
+      }
+    }
+#pragma unroll
+  for (int u = 0; u < NBMAX; ++u)
+    if (u < nb) {
+      Dft<R, C, T>::run(&v[u * R]);
+      const int j = tl + u * tpl;
+      const int jm = j % Ns;
+      const int base = (j - jm) * R + jm;
+#pragma unroll
+      for (int r = 0; r < R; ++r) st(base + r * Ns, v[u * R + r]);
+    }
+}
+
+// Single-stage transform from ld to st; one barrier separates every load of
+// the CTA from every store, so ld and st may address the same memory.
+template <typename T, int R, int EMAX, class Ld, class St>
+__device__ __forceinline__ void stage_only(const Ld& ld, const St& st, int n, int tl, int tpl, int nb) {
+  using C = cplx<T>;
+  constexpr int NBMAX = EMAX / R;
+  C v[NBMAX * R];
+  const int nr = n / R;
+#pragma unroll
+  for (int u = 0; u < NBMAX; ++u)
+    if (u < nb) {
+      const int j = tl + u * tpl;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[u * R + r] = ld(j + r * nr);
+    }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < NBMAX; ++u)
+    if (u < nb) {
+      Dft<R, C, T>::run(&v[u * R]);
+      const int j = tl + u * tpl;
+#pragma unroll
+      for (int r = 0; r < R; ++r) st(j * R + r, v[u * R + r]);
+    }
+}
+
+// Global -> global transform of one line (shared memory as the exchange
+// buffer).  Every load of the CTA happens before its first barrier and every
+// store after it, so ld and st may address the same global memory.
+template <typename T, int EMAX, class Ld, class St>
+__device__ __forceinline__ void fft_line_gg(const Ld& ld, const St& st, cplx<T>* line, int es, const FftAxis& ax,
+                                            int tl, int tpl, const cplx<T>* __restrict__ tw, int tws) {
+  const int nst = ax.nst;
+  if (nst == 0) {
+    const cplx<T> v = ld(0);
+    __syncthreads();
+    st(0, v);
+    return;
+  }
+  if (nst == 1) {
+    with_radix<EMAX>(ax.radix[0], [&](auto RC) {
+      constexpr int R = decltype(RC)::value;
+      stage_only<T, R, EMAX>(ld, st, ax.n, tl, tpl, ax.e / R);
+    });
+    return;
+  }
+  with_radix<EMAX>(ax.radix[0], [&](auto RC) {
+    constexpr int R = decltype(RC)::value;
+    stage_first_to_smem<T, R, EMAX>(ld, line, es, ax.n, tl, tpl, ax.e / R);
+  });
+  __syncthreads();
+  int Ns = ax.radix[0];
+  for (int s = 1; s < nst - 1; ++s) {
+    const int R0 = ax.radix[s];
+    with_radix_tail<EMAX>(R0, [&](auto RC) {
+      constexpr int R = decltype(RC)::value;
+      fft_stage<T, R, EMAX>(line, es, ax.n, Ns, tl, tpl, ax.e / R, tw, tws);
+    });
+    Ns *= R0;
+  }
+  with_radix_tail<EMAX>(ax.radix[nst - 1], [&](auto RC) {
+    constexpr int R = decltype(RC)::value;
+    stage_last_to_global<T, R, EMAX>(line, es, st, ax.n, Ns, tl, tpl, ax.e / R, tw, tws);
+  });
+}
+
+// Global -> shared: the transformed line ends in natural order in `line`,
+// after a barrier.
+template <typename T, int EMAX, class Ld>
+__device__ __forceinline__ void fft_line_gs(const Ld& ld, cplx<T>* line, int es, const FftAxis& ax, int tl,
+                                            int tpl, const cplx<T>* __restrict__ tw, int tws) {
+  const int nst = ax.nst;
+  if (nst == 0) {
+    line[0] = ld(0);
+    __syncthreads();
+    return;
+  }
+  with_radix<EMAX>(ax.radix[0], [&](auto RC) {
+    constexpr int R = decltype(RC)::value;
+    stage_first_to_smem<T, R, EMAX>(ld, line, es, ax.n, tl, tpl, ax.e / R);
+  });
+  __syncthreads();
+  int Ns = ax.radix[0];
+  for (int s = 1; s < nst; ++s) {
+    const int R0 = ax.radix[s];
+    with_radix_tail<EMAX>(R0, [&](auto RC) {
+      constexpr int R = decltype(RC)::value;
+      fft_stage<T, R, EMAX>(line, es, ax.n, Ns, tl, tpl, ax.e / R, tw, tws);
+    });
+    Ns *= R0;
+  }
+}
+
+// Shared -> global: the line in `line` (complete, after a barrier) is
+// transformed and written through st.
+template <typename T, int EMAX, class St>
+__device__ __forceinline__ void fft_line_sg(cplx<T>* line, const St& st, int es, const FftAxis& ax, int tl,
+                                            int tpl, const cplx<T>* __restrict__ tw, int tws) {
+  const int nst = ax.nst;
+  if (nst == 0) {
+    st(0, line[0]);
+    return;
+  }
+  int Ns = 1;
+  if (nst == 1) {
+    with_radix<EMAX>(ax.radix[0], [&](auto RC) {
+      constexpr int R = decltype(RC)::value;
+      stage_last_to_global<T, R, EMAX>(line, es, st, ax.n, Ns, tl, tpl, ax.e / R, tw, tws);
+    });
+    return;
+  }
+  with_radix<EMAX>(ax.radix[0], [&](auto RC) {
+    constexpr int R = decltype(RC)::value;
+    fft_stage<T, R, EMAX>(line, es, ax.n, Ns, tl, tpl, ax.e / R, tw, tws);
+  });
+  Ns = ax.radix[0];
+  for (int s = 1; s < nst - 1; ++s) {
+    const int R0 = ax.radix[s];
+    with_radix_tail<EMAX>(R0, [&](auto RC) {
+      constexpr int R = decltype(RC)::value;
+      fft_stage<T, R, EMAX>(line, es, ax.n, Ns, tl, tpl, ax.e / R, tw, tws);
+    });
+    Ns *= R0;
+  }
+  with_radix_tail<EMAX>(ax.radix[nst - 1], [&](auto RC) {
+    constexpr int R = decltype(RC)::value;
+    stage_last_to_global<T, R, EMAX>(line, es, st, ax.n, Ns, tl, tpl, ax.e / R, tw, tws);
+  });
 }
 
 }  // namespace sr3d

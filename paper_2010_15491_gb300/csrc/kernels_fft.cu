@@ -14,6 +14,7 @@
 // transform), strided FFT along n, FFT along s fused with the class solve
 // and the inverse s FFT, inverse n FFT, inverse real FFT along m.
 #include "fft.cuh"
+#include "fft_ct.cuh"
 #include "internal.h"
 
 namespace sr3d {
@@ -31,27 +32,31 @@ __device__ __forceinline__ double warp_sum(double v) {
 // ---------------------------------------------------------------------------
 // m pass, forward: L real lines of length M -> Ms slots each.
 // ---------------------------------------------------------------------------
-template <typename T, int EMAX>
+template <typename T, int EMAX, int NC>
 __global__ void __launch_bounds__(256, 2) k_rfft_m_fwd(const T* __restrict__ in, long long nlines, cplx<T>* __restrict__ out, MAxis a,
                              int L, int Hp, const cplx<T>* __restrict__ twM) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int H = a.H;
-  const int tpl = H / a.f.e;
+  const int H = NC > 0 ? NC : a.H;
+  const int tpl = NC > 0 ? NC / 16 : H / a.f.e;
   const long long line0 = (long long)blockIdx.x * L;
   const C* inc = reinterpret_cast<const C*>(in);  // (x[2j], x[2j+1]) as one complex
-  for (int i = threadIdx.x; i < L * H; i += blockDim.x) {
-    const int l = i / H, j = i - l * H;
-    const long long gl = line0 + l;
-    C v = czero<C>();
-    if (gl < nlines) v = inc[gl * H + j];
-    sm[l * Hp + j] = v;
-  }
-  __syncthreads();
+  const C* tw = twM;
   {
     const int l = threadIdx.x / tpl, tl = threadIdx.x - l * tpl;
-    fft_line<T, EMAX>(sm + l * Hp, 1, a.f, tl, tpl, twM, 2);
+    const long long gl = line0 + l;
+    const bool ok = gl < nlines;
+    const C* src = inc + gl * H;
+    auto ld = [&](int j) -> C { return ok ? __ldg(&src[j]) : czero<C>(); };
+    if constexpr (NC > 0) {
+      C* tws = sm + L * Hp;  // table of the M = 2H roots
+      ct_load_twiddles(tws, twM, 2 * NC);
+      tw = tws;
+      ct_line_gs<NC>(ld, sm + l * Hp, 1, tl, tws, 2);
+    } else {
+      fft_line_gs<T, EMAX>(ld, sm + l * Hp, 1, a.f, tl, tpl, twM, 2);
+    }
   }
   // split the packed transform: X[k] = E[k] + W^k O[k], E/O from Z[k], conj(Z[H-k])
   for (int i = threadIdx.x; i < L * a.Ms; i += blockDim.x) {
@@ -66,7 +71,7 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_fwd(const T* __restrict__ in,
     const C zc = conjc(sm[l * Hp + (k == 0 ? 0 : H - k)]);
     const C e = (zk + zc) * (T)0.5;
     const C o = mul_mi(zk - zc) * (T)0.5;
-    const C X = e + cmul(__ldg(&twM[k]), o);
+    const C X = e + cmul(NC > 0 ? tw[k] : __ldg(&twM[k]), o);
     out[gl * a.Mp + slot] = cj ? conjc(X) : X;
   }
 }
@@ -74,86 +79,79 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_fwd(const T* __restrict__ in,
 // ---------------------------------------------------------------------------
 // m pass, inverse: Ms slots -> M reals per line, times `scale`.
 // ---------------------------------------------------------------------------
-template <typename T, int EMAX>
+template <typename T, int EMAX, int NC>
 __global__ void __launch_bounds__(256, 2) k_rfft_m_inv(const cplx<T>* __restrict__ in, long long nlines, T* __restrict__ out, MAxis a,
                              int L, int Hp, const cplx<T>* __restrict__ twM, T scale) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int H = a.H;
-  const int tpl = H / a.f.e;
+  const int H = NC > 0 ? NC : a.H;
+  const int tpl = NC > 0 ? NC / 16 : H / a.f.e;
+  const C* tw = twM;
+  if constexpr (NC > 0) {
+    C* tws = sm + L * Hp;
+    ct_load_twiddles(tws, twM, 2 * NC);
+    tw = tws;
+  }
   const long long line0 = (long long)blockIdx.x * L;
-  for (int i = threadIdx.x; i < L * H; i += blockDim.x) {
-    const int l = i / H, k = i - l * H;
-    const long long gl = line0 + l;
-    C z = czero<C>();
-    if (gl < nlines) {
-      const C* row = in + gl * a.Mp;
-      bool c1, c2;
-      const int s1 = mslot_of(k, a.M, a.Ml, a.dr, c1);
-      const int s2 = mslot_of(H - k, a.M, a.Ml, a.dr, c2);
-      C xk = row[s1];
-      if (c1) xk = conjc(xk);
-      C xh = row[s2];
-      if (!c2) xh = conjc(xh);  // conj(X[H-k])
-      const C e = xk + xh;
-      const C o = cmulc(__ldg(&twM[k]), xk - xh);  // W^-k (X[k] - conj(X[H-k]))
-      z = e + mul_i(o);
-    }
-    sm[l * Hp + k] = conjc(z);  // inverse through the forward engine
-  }
-  __syncthreads();
-  {
-    const int l = threadIdx.x / tpl, tl = threadIdx.x - l * tpl;
-    fft_line<T, EMAX>(sm + l * Hp, 1, a.f, tl, tpl, twM, 2);
-  }
-  C* outc = reinterpret_cast<C*>(out);
-  for (int i = threadIdx.x; i < L * H; i += blockDim.x) {
-    const int l = i / H, j = i - l * H;
-    const long long gl = line0 + l;
-    if (gl >= nlines) continue;
-    const C r = sm[l * Hp + j];
-    outc[gl * H + j] = mkc(r.x * scale, -r.y * scale);
-  }
+  const int l = threadIdx.x / tpl, tl = threadIdx.x - l * tpl;
+  const long long gl = line0 + l;
+  const bool ok = gl < nlines;
+  const C* row = in + gl * a.Mp;
+  // Z[k] = E'[k] + i O'[k] from X[k] and conj(X[H-k]); the inverse runs
+  // through the forward engine on conj(Z)
+  auto ld = [&](int k) -> C {
+    if (!ok) return czero<C>();
+    bool c1, c2;
+    const int s1 = mslot_of(k, a.M, a.Ml, a.dr, c1);
+    const int s2 = mslot_of(H - k, a.M, a.Ml, a.dr, c2);
+    C xk = __ldg(&row[s1]);
+    if (c1) xk = conjc(xk);
+    C xh = __ldg(&row[s2]);
+    if (!c2) xh = conjc(xh);  // conj(X[H-k])
+    const C e = xk + xh;
+    const C o = cmulc(NC > 0 ? tw[k] : __ldg(&twM[k]), xk - xh);  // W^-k (X[k] - conj(X[H-k]))
+    return conjc(e + mul_i(o));
+  };
+  C* outc = reinterpret_cast<C*>(out) + gl * H;
+  auto st = [&](int j, C r) {
+    if (ok) outc[j] = mkc(r.x * scale, -r.y * scale);
+  };
+  if constexpr (NC > 0) ct_line_gg<NC>(ld, st, sm + l * Hp, 1, tl, tw, 2);
+  else fft_line_gg<T, EMAX>(ld, st, sm + l * Hp, 1, a.f, tl, tpl, twM, 2);
 }
 
 // ---------------------------------------------------------------------------
 // n pass: tile of TW m-slots x all N rows of one s plane.  Forward reads n in
 // natural order and writes n-slots; inverse reads n-slots, writes natural n.
 // ---------------------------------------------------------------------------
-template <typename T, int EMAX, bool INV>
+template <typename T, int EMAX, bool INV, int NC>
 __global__ void __launch_bounds__(256, 2) k_fft_n(cplx<T>* __restrict__ spec, LAxis a, int Ms, int Mp, int TW,
                         const cplx<T>* __restrict__ twN) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int N = a.N;
+  const int N = NC > 0 ? NC : a.N;
   const int a0 = blockIdx.x * TW;
   const int tv = min(TW, Ms - a0);
   C* base = spec + (long long)blockIdx.y * N * Mp + a0;
-  for (int i = threadIdx.x; i < N * TW; i += blockDim.x) {
-    const int n = i / TW, t = i - n * TW;
-    C v = czero<C>();
-    if (t < tv) {
-      const int row = INV ? nslot(n, a.Nl, a.dc) : n;
-      v = base[(long long)row * Mp + t];
-      if (INV) v = conjc(v);
-    }
-    sm[i] = v;
-  }
-  __syncthreads();
-  {
-    const int t = threadIdx.x % TW, tl = threadIdx.x / TW, tpl = N / a.f.e;
-    fft_line<T, EMAX>(sm + t, TW, a.f, tl, tpl, twN, 1);
-  }
-  for (int i = threadIdx.x; i < N * TW; i += blockDim.x) {
-    const int n = i / TW, t = i - n * TW;
-    if (t < tv) {
-      const int row = INV ? n : nslot(n, a.Nl, a.dc);
-      C v = sm[i];
-      if (INV) v = conjc(v);
-      base[(long long)row * Mp + t] = v;
-    }
+  const int t = threadIdx.x % TW, tl = threadIdx.x / TW, tpl = NC > 0 ? NC / 16 : N / a.f.e;
+  const bool ok = t < tv;
+  C* col = base + t;
+  auto ld = [&](int k) -> C {
+    if (!ok) return czero<C>();
+    const C v = col[(long long)(INV ? nslot(k, a.Nl, a.dc) : k) * Mp];
+    return INV ? conjc(v) : v;
+  };
+  auto st = [&](int k, C v) {
+    if (ok) col[(long long)(INV ? k : nslot(k, a.Nl, a.dc)) * Mp] = INV ? conjc(v) : v;
+  };
+  if constexpr (NC > 0) {
+    C* tws = sm + N * TW;
+    ct_load_twiddles(tws, twN, NC);
+    ct_line_gg<NC>(ld, st, sm + t, TW, tl, tws, 1);
+  } else {
+    fft_line_gg<T, EMAX>(ld, st, sm + t, TW, a.f, tl, tpl, twN, 1);
   }
 }
 
@@ -172,33 +170,43 @@ __device__ __forceinline__ C box_factor(const C* __restrict__ tw, int n, int da,
 
 constexpr int DMAX = 8;  // largest supported d = dr*dc*ds
 
-template <typename T, int EMAX, int MODE, bool STATS>
+template <typename T, int EMAX, int MODE, bool STATS, int NC>
 __global__ void __launch_bounds__(512) k_fft_s(cplx<T>* __restrict__ spec, LAxis a, int Ms, int Mp, int Nn, int TW, int G, SolveArgs sv,
                         const cplx<T>* __restrict__ twS) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
-  const int S = a.N;
+  const int S = NC > 0 ? NC : a.N;
   const int a0 = blockIdx.x * TW, b0 = blockIdx.y * G;
   const int tv = min(TW, Ms - a0);
   const int nthr = blockDim.x, tid = threadIdx.x;
   const int rowlen = G * TW;
   const long long plane = (long long)Nn * Mp;
   C* gbase = spec + (long long)b0 * Mp + a0;
-
-  for (int i = tid; i < S * rowlen; i += nthr) {
-    const int s = i / rowlen, r = i - s * rowlen, gi = r / TW, t = r - gi * TW;
-    C v = czero<C>();
-    if (MODE != S_TIK_GEN && t < tv) {
-      v = gbase[s * plane + (long long)gi * Mp + t];
-      if (MODE == S_INV) v = conjc(v);
-    }
-    sm[i] = v;
-  }
-  __syncthreads();
-  const int t = tid % TW, gi = (tid / TW) % G, tl = tid / (TW * G), tpl = S / a.f.e;
+  const int t = tid % TW, gi = (tid / TW) % G, tl = tid / (TW * G), tpl = NC > 0 ? NC / 16 : S / a.f.e;
+  (void)tpl;
+  const bool ok = t < tv;
+  C* col = gbase + (long long)gi * Mp + t;
   C* line = sm + gi * TW + t;
-  if (MODE != S_TIK_GEN) fft_line<T, EMAX>(line, rowlen, a.f, tl, tpl, twS, 1);
+  C* tws = sm + S * rowlen;
+  if constexpr (NC > 0) ct_load_twiddles(tws, twS, NC);
+  auto ld = [&](int s) -> C {
+    if (!ok) return czero<C>();
+    const C v = col[s * plane];
+    return MODE == S_INV ? conjc(v) : v;
+  };
+  auto st = [&](int s, C v) {
+    if (ok) col[s * plane] = MODE == S_FWD ? v : conjc(v);
+  };
+  if (MODE == S_FWD || MODE == S_INV) {
+    if constexpr (NC > 0) ct_line_gg<NC>(ld, st, line, rowlen, tl, tws, 1);
+    else fft_line_gg<T, EMAX>(ld, st, line, rowlen, a.f, tl, tpl, twS, 1);
+    return;
+  }
+  if (MODE != S_TIK_GEN) {
+    if constexpr (NC > 0) ct_line_gs<NC>(ld, line, rowlen, tl, tws, 1);
+    else fft_line_gs<T, EMAX>(ld, line, rowlen, a.f, tl, tpl, twS, 1);
+  }
 
   if (MODE >= S_TIK_GEN) {
     const int d = sv.dr * sv.dc * sv.ds;
@@ -328,16 +336,8 @@ __global__ void __launch_bounds__(512) k_fft_s(cplx<T>* __restrict__ spec, LAxis
     __syncthreads();
   }
   if (MODE == S_FOLD) return;
-  if (MODE >= S_TIK_GEN) fft_line<T, EMAX>(line, rowlen, a.f, tl, tpl, twS, 1);
-
-  for (int i = tid; i < S * rowlen; i += nthr) {
-    const int s = i / rowlen, r = i - s * rowlen, gi2 = r / TW, t2 = r - gi2 * TW;
-    if (t2 < tv) {
-      C v = sm[i];
-      if (MODE != S_FWD) v = conjc(v);
-      gbase[s * plane + (long long)gi2 * Mp + t2] = v;
-    }
-  }
+  if constexpr (NC > 0) ct_line_sg<NC>(line, st, rowlen, tl, tws, 1);
+  else fft_line_sg<T, EMAX>(line, st, rowlen, a.f, tl, tpl, twS, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -371,80 +371,105 @@ static void m_launch_shape(const Geometry& g, size_t csz, int& L, int& Hp, int& 
   smem = (size_t)L * Hp * csz;
 }
 
-template <typename T>
-static cudaError_t rfft_fwd_t(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw) {
+// lengths with a compile-time plan (FP32 only)
+template <typename T> static int ct_len(int n, const FftAxis& f) {
+  if (sizeof(T) != 4 || f.e != 16) return 0;
+  return (n == 128 || n == 256 || n == 512) ? n : 0;
+}
+
+template <typename T, int EMAX, int NC>
+static cudaError_t rfft_fwd_k(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw) {
   int L, Hp, threads;
   size_t smem;
   m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
+  if (NC > 0) smem += (size_t)2 * NC * sizeof(cplx<T>);
   const long long nlines = (long long)g.S * g.N;
   const unsigned blocks = (unsigned)((nlines + L - 1) / L);
   MAxis a = maxis(g);
   cudaError_t e;
-  if (fam3(g.fm)) {
-    if ((e = allow_smem(k_rfft_m_fwd<T, Emax<T>::p3>, smem)) != cudaSuccess) return e;
-    k_rfft_m_fwd<T, Emax<T>::p3><<<blocks, threads, smem, p.stream>>>((const T*)in, nlines, (cplx<T>*)out, a, L, Hp,
-                                                            (const cplx<T>*)tw);
-  } else {
-    if ((e = allow_smem(k_rfft_m_fwd<T, Emax<T>::p2>, smem)) != cudaSuccess) return e;
-    k_rfft_m_fwd<T, Emax<T>::p2><<<blocks, threads, smem, p.stream>>>((const T*)in, nlines, (cplx<T>*)out, a, L, Hp,
-                                                            (const cplx<T>*)tw);
-  }
+  if ((e = allow_smem(k_rfft_m_fwd<T, EMAX, NC>, smem)) != cudaSuccess) return e;
+  k_rfft_m_fwd<T, EMAX, NC><<<blocks, threads, smem, p.stream>>>((const T*)in, nlines, (cplx<T>*)out, a, L, Hp,
+                                                                (const cplx<T>*)tw);
   return cudaGetLastError();
+}
+
+template <typename T, int EMAX, int NC>
+static cudaError_t rfft_inv_k(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw,
+                              double scale) {
+  int L, Hp, threads;
+  size_t smem;
+  m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
+  if (NC > 0) smem += (size_t)2 * NC * sizeof(cplx<T>);
+  const long long nlines = (long long)g.S * g.N;
+  const unsigned blocks = (unsigned)((nlines + L - 1) / L);
+  MAxis a = maxis(g);
+  cudaError_t e;
+  if ((e = allow_smem(k_rfft_m_inv<T, EMAX, NC>, smem)) != cudaSuccess) return e;
+  k_rfft_m_inv<T, EMAX, NC><<<blocks, threads, smem, p.stream>>>((const cplx<T>*)in, nlines, (T*)out, a, L, Hp,
+                                                                (const cplx<T>*)tw, (T)scale);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t rfft_fwd_t(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw) {
+  if (fam3(g.fm)) return rfft_fwd_k<T, Emax<T>::p3, 0>(p, g, in, out, tw);
+  if constexpr (sizeof(T) == 4) {
+    switch (ct_len<T>(g.M / 2, g.fm)) {
+      case 128: return rfft_fwd_k<T, 16, 128>(p, g, in, out, tw);
+      case 256: return rfft_fwd_k<T, 16, 256>(p, g, in, out, tw);
+      case 512: return rfft_fwd_k<T, 16, 512>(p, g, in, out, tw);
+    }
+  }
+  return rfft_fwd_k<T, Emax<T>::p2, 0>(p, g, in, out, tw);
 }
 
 template <typename T>
 static cudaError_t rfft_inv_t(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw,
                               double scale) {
-  int L, Hp, threads;
-  size_t smem;
-  m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
-  const long long nlines = (long long)g.S * g.N;
-  const unsigned blocks = (unsigned)((nlines + L - 1) / L);
-  MAxis a = maxis(g);
-  cudaError_t e;
-  if (fam3(g.fm)) {
-    if ((e = allow_smem(k_rfft_m_inv<T, Emax<T>::p3>, smem)) != cudaSuccess) return e;
-    k_rfft_m_inv<T, Emax<T>::p3><<<blocks, threads, smem, p.stream>>>((const cplx<T>*)in, nlines, (T*)out, a, L, Hp,
-                                                            (const cplx<T>*)tw, (T)scale);
-  } else {
-    if ((e = allow_smem(k_rfft_m_inv<T, Emax<T>::p2>, smem)) != cudaSuccess) return e;
-    k_rfft_m_inv<T, Emax<T>::p2><<<blocks, threads, smem, p.stream>>>((const cplx<T>*)in, nlines, (T*)out, a, L, Hp,
-                                                            (const cplx<T>*)tw, (T)scale);
+  if (fam3(g.fm)) return rfft_inv_k<T, Emax<T>::p3, 0>(p, g, in, out, tw, scale);
+  if constexpr (sizeof(T) == 4) {
+    switch (ct_len<T>(g.M / 2, g.fm)) {
+      case 128: return rfft_inv_k<T, 16, 128>(p, g, in, out, tw, scale);
+      case 256: return rfft_inv_k<T, 16, 256>(p, g, in, out, tw, scale);
+      case 512: return rfft_inv_k<T, 16, 512>(p, g, in, out, tw, scale);
+    }
   }
-  return cudaGetLastError();
+  return rfft_inv_k<T, Emax<T>::p2, 0>(p, g, in, out, tw, scale);
 }
 
-template <typename T, int EMAX>
+template <typename T, int EMAX, int NC>
 static cudaError_t fft_n_e(const Plan& p, const Geometry& g, void* spec, const void* tw, bool inverse) {
   const int tpl = g.N / g.fn.e;
   const int TW = g.tw_n;
-  const size_t smem = (size_t)g.N * TW * sizeof(cplx<T>);
+  size_t smem = (size_t)g.N * TW * sizeof(cplx<T>);
+  if (NC > 0) smem += (size_t)NC * sizeof(cplx<T>);
   dim3 grid((g.Ms + TW - 1) / TW, g.S);
   LAxis a = laxis(g.N, g.Nl, g.dc, g.fn);
   cudaError_t e;
   if (inverse) {
-    if ((e = allow_smem(k_fft_n<T, EMAX, true>, smem)) != cudaSuccess) return e;
-    k_fft_n<T, EMAX, true><<<grid, TW * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, TW,
-                                                              (const cplx<T>*)tw);
+    if ((e = allow_smem(k_fft_n<T, EMAX, true, NC>, smem)) != cudaSuccess) return e;
+    k_fft_n<T, EMAX, true, NC><<<grid, TW * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, TW,
+                                                                  (const cplx<T>*)tw);
   } else {
-    if ((e = allow_smem(k_fft_n<T, EMAX, false>, smem)) != cudaSuccess) return e;
-    k_fft_n<T, EMAX, false><<<grid, TW * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, TW,
-                                                               (const cplx<T>*)tw);
+    if ((e = allow_smem(k_fft_n<T, EMAX, false, NC>, smem)) != cudaSuccess) return e;
+    k_fft_n<T, EMAX, false, NC><<<grid, TW * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, TW,
+                                                                   (const cplx<T>*)tw);
   }
   return cudaGetLastError();
 }
 
-template <typename T, int EMAX, int MODE, bool STATS>
+template <typename T, int EMAX, int MODE, bool STATS, int NC>
 static cudaError_t fft_s_k(const Plan& p, const Geometry& g, void* spec, const void* tw, const SolveArgs& sv) {
   const int tpl = g.S / g.fs.e;
   const int TW = g.tw_s, G = g.g_s;
-  const size_t smem = (size_t)g.S * TW * G * sizeof(cplx<T>);
+  size_t smem = (size_t)g.S * TW * G * sizeof(cplx<T>);
+  if (NC > 0) smem += (size_t)NC * sizeof(cplx<T>);
   dim3 grid((g.Ms + TW - 1) / TW, g.N / G);
   LAxis a = laxis(g.S, g.Sl, g.ds, g.fs);
   cudaError_t e;
-  if ((e = allow_smem(k_fft_s<T, EMAX, MODE, STATS>, smem)) != cudaSuccess) return e;
-  k_fft_s<T, EMAX, MODE, STATS><<<grid, TW * G * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, g.N, TW, G,
-                                                                      sv, (const cplx<T>*)tw);
+  if ((e = allow_smem(k_fft_s<T, EMAX, MODE, STATS, NC>, smem)) != cudaSuccess) return e;
+  k_fft_s<T, EMAX, MODE, STATS, NC><<<grid, TW * G * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, g.N, TW,
+                                                                          G, sv, (const cplx<T>*)tw);
   return cudaGetLastError();
 }
 
@@ -452,14 +477,19 @@ template <typename T, int EMAX>
 static cudaError_t fft_s_e(const Plan& p, const Geometry& g, void* spec, const void* tw, int mode, bool stats,
                            const SolveArgs& sv) {
   switch (mode) {
-    case S_FWD: return fft_s_k<T, EMAX, S_FWD, false>(p, g, spec, tw, sv);
-    case S_INV: return fft_s_k<T, EMAX, S_INV, false>(p, g, spec, tw, sv);
-    case S_TIK_GEN: return fft_s_k<T, EMAX, S_TIK_GEN, false>(p, g, spec, tw, sv);
-    case S_TIK_USER: return fft_s_k<T, EMAX, S_TIK_USER, false>(p, g, spec, tw, sv);
+    case S_FWD: return fft_s_k<T, EMAX, S_FWD, false, 0>(p, g, spec, tw, sv);
+    case S_INV: return fft_s_k<T, EMAX, S_INV, false, 0>(p, g, spec, tw, sv);
+    case S_TIK_GEN: return fft_s_k<T, EMAX, S_TIK_GEN, false, 0>(p, g, spec, tw, sv);
+    case S_TIK_USER: return fft_s_k<T, EMAX, S_TIK_USER, false, 0>(p, g, spec, tw, sv);
     case S_ADMM:
-      return stats ? fft_s_k<T, EMAX, S_ADMM, true>(p, g, spec, tw, sv)
-                   : fft_s_k<T, EMAX, S_ADMM, false>(p, g, spec, tw, sv);
-    case S_FOLD: return fft_s_k<T, EMAX, S_FOLD, false>(p, g, spec, tw, sv);
+      if constexpr (sizeof(T) == 4 && EMAX == 16) {
+        if (ct_len<T>(g.S, g.fs) == 256)
+          return stats ? fft_s_k<T, EMAX, S_ADMM, true, 256>(p, g, spec, tw, sv)
+                       : fft_s_k<T, EMAX, S_ADMM, false, 256>(p, g, spec, tw, sv);
+      }
+      return stats ? fft_s_k<T, EMAX, S_ADMM, true, 0>(p, g, spec, tw, sv)
+                   : fft_s_k<T, EMAX, S_ADMM, false, 0>(p, g, spec, tw, sv);
+    case S_FOLD: return fft_s_k<T, EMAX, S_FOLD, false, 0>(p, g, spec, tw, sv);
   }
   return cudaErrorInvalidValue;
 }
@@ -476,10 +506,14 @@ cudaError_t launch_rfft_m_inv(const Plan& p, const Geometry& g, const void* in, 
 cudaError_t launch_fft_n(const Plan& p, const Geometry& g, void* spec, const void* tw, bool inverse) {
   const bool f3 = fam3(g.fn);
   if (p.dtype)
-    return f3 ? fft_n_e<double, Emax<double>::p3>(p, g, spec, tw, inverse)
-              : fft_n_e<double, Emax<double>::p2>(p, g, spec, tw, inverse);
-  return f3 ? fft_n_e<float, Emax<float>::p3>(p, g, spec, tw, inverse)
-            : fft_n_e<float, Emax<float>::p2>(p, g, spec, tw, inverse);
+    return f3 ? fft_n_e<double, Emax<double>::p3, 0>(p, g, spec, tw, inverse)
+              : fft_n_e<double, Emax<double>::p2, 0>(p, g, spec, tw, inverse);
+  if (f3) return fft_n_e<float, Emax<float>::p3, 0>(p, g, spec, tw, inverse);
+  switch (ct_len<float>(g.N, g.fn)) {
+    case 256: return fft_n_e<float, 16, 256>(p, g, spec, tw, inverse);
+    case 512: return fft_n_e<float, 16, 512>(p, g, spec, tw, inverse);
+  }
+  return fft_n_e<float, Emax<float>::p2, 0>(p, g, spec, tw, inverse);
 }
 
 cudaError_t launch_fft_s(const Plan& p, const Geometry& g, void* spec, const void* tw, int mode, bool stats,

@@ -26,6 +26,12 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // STATS: per-CTA FP64 sums of ||g||, ||d'-d||^2, ||g||^2, ||u||^2,
 // (L^T u - psi)^2, (L^T d')^2; psi (= L^T u of the previous iteration) is
 // read and overwritten in place.
+//
+// Thread (lm, ln) owns tile voxel (m0+lm, n0+ln): its loads are aligned,
+// coalesced rows.  The 41 halo voxels of the rho region and the 84 of the x
+// region are second positions of the first threads.  x of plane s+2 and d of
+// plane s+1 are loaded into registers while plane s is computed; x planes
+// rotate through three shared buffers.
 template <typename T, int MODE, bool STATS>
 __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T* __restrict__ din,
                                                T* __restrict__ dout, T* __restrict__ theta, T* __restrict__ psi,
@@ -33,7 +39,9 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
   constexpr int XW = TM + 2, XH = TN + 2;  // x plane with halo -1..+1
   constexpr int RW = TM + 1, RH = TN + 1;  // rho plane with halo -1
   constexpr int NC = STATS ? 6 : 3;
-  __shared__ T xs[2][XH * XW];
+  constexpr int NXH = 2 * XW + 2 * TN;      // x halo positions (84)
+  constexpr int NRH = RW + TN;              // rho halo positions (41)
+  __shared__ T xs[3][XH * XW];
   __shared__ T rs[NC][RH * RW];
   const int lm = threadIdx.x, ln = threadIdx.y, tid = ln * TM + lm;
   const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN, s0 = blockIdx.z * TS;
@@ -41,42 +49,84 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
   const long long P = (long long)M * N;
   const int s_end = min(S, s0 + TS);
 
-  auto load_x = [&](T* buf, int s) {
-    const int sw = (s + S) % S;
-    for (int i = tid; i < XH * XW; i += TM * TN) {
-      const int r = i / XW, c = i - r * XW;
-      const int n = (n0 - 1 + r + N) % N, m = (m0 - 1 + c + M) % M;
-      buf[i] = x[sw * P + (long long)n * M + m];
+  // x positions: interior (ln+1, lm+1) and, for tid < NXH, one halo cell
+  const bool has_xh = tid < NXH;
+  int xh_r = 0, xh_c = 0;
+  if (has_xh) {
+    if (tid < XW) { xh_r = 0; xh_c = tid; }
+    else if (tid < 2 * XW) { xh_r = XH - 1; xh_c = tid - XW; }
+    else if (tid < 2 * XW + TN) { xh_r = 1 + tid - 2 * XW; xh_c = 0; }
+    else { xh_r = 1 + tid - 2 * XW - TN; xh_c = XW - 1; }
+  }
+  const long long xo_in = (long long)((n0 + ln) % N) * M + (m0 + lm) % M;
+  const long long xo_h = (long long)((n0 - 1 + xh_r + N) % N) * M + (m0 - 1 + xh_c + M) % M;
+  // rho positions: interior (ln+1, lm+1) and, for tid < NRH, one halo cell
+  const bool has_rh = tid < NRH;
+  int rh_r = 0, rh_c = 0;
+  if (has_rh) {
+    if (tid < RW) { rh_r = 0; rh_c = tid; }
+    else { rh_r = 1 + tid - RW; rh_c = 0; }
+  }
+  const long long ro_h = (long long)((n0 - 1 + rh_r + N) % N) * M + (m0 - 1 + rh_c + M) % M;
+  const int own = (ln + 1) * RW + (lm + 1);
+  const int hpos = rh_r * RW + rh_c;
+
+  auto plane_of = [&](int s) -> long long { return (long long)((s + S) % S) * P; };
+  T xin_n = 0, xh_n = 0;  // prefetched x (plane s+2)
+  T di_n[3] = {0, 0, 0}, dh_n[3] = {0, 0, 0};  // prefetched d (plane s+1)
+  T di[3], dh[3];
+  auto load_x = [&](int s, T& a, T& b) {
+    const long long pl = plane_of(s);
+    a = __ldg(&x[pl + xo_in]);
+    if (has_xh) b = __ldg(&x[pl + xo_h]);
+  };
+  auto store_x = [&](T* buf, T a, T b) {
+    buf[(ln + 1) * XW + lm + 1] = a;
+    if (has_xh) buf[xh_r * XW + xh_c] = b;
+  };
+  auto load_d = [&](int s, T* a, T* b) {
+    const long long pl = plane_of(s);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      a[c] = __ldg(&din[c * V + pl + xo_in]);
+      if (has_rh) b[c] = __ldg(&din[c * V + pl + ro_h]);
     }
   };
 
   double q[NQ] = {0, 0, 0, 0, 0, 0};
   T r2prev = 0, u2prev = 0, d2prev = 0;
-  load_x(xs[0], s0 - 1);
-  load_x(xs[1], s0);
+  {
+    T a, b = 0;
+    load_x(s0 - 1, a, b);
+    store_x(xs[0], a, b);
+    load_x(s0, a, b);
+    store_x(xs[1], a, b);
+    load_d(s0 - 1, di, dh);
+  }
   __syncthreads();
-  int cur = 0;
+  int cur = 0;  // buffer of plane s; s+1 in (cur+1)%3, s+2 goes to (cur+2)%3
   for (int s = s0 - 1; s < s_end; ++s) {
+    const bool more_x = s + 2 <= s_end;
+    const bool more_d = s + 1 < s_end;
+    if (more_x) load_x(s + 2, xin_n, xh_n);
+    if (more_d) load_d(s + 1, di_n, dh_n);
     const T* xc = xs[cur];
-    const T* xn = xs[cur ^ 1];
-    const int sw = (s + S) % S;
+    const T* xn = xs[(cur + 1) % 3];
+    const long long pl = plane_of(s);
     const bool own_plane = s >= s0;
-    // phase 1: u, d', rho on the tile and its -1 halo
-    for (int i = tid; i < RH * RW; i += TM * TN) {
-      const int rr = i / RW, cc = i - rr * RW;  // voxel (n0-1+rr, m0-1+cc)
+    // phase 1: u, d', rho at a position of the rho region
+    auto point = [&](int rr, int cc, const T* dv, long long gi, bool interior) {
+      const int i = rr * RW + cc;
       const T xv = xc[rr * XW + cc];
       const T g0 = xc[rr * XW + cc + 1] - xv;
       const T g1 = xc[(rr + 1) * XW + cc] - xv;
       const T g2 = xn[rr * XW + cc] - xv;
-      const int n = (n0 - 1 + rr + N) % N, m = (m0 - 1 + cc + M) % M;
-      const long long gi = sw * P + (long long)n * M + m;
-      const T d0 = din[gi], d1 = din[V + gi], d2 = din[2 * V + gi];
       T u0, u1, u2, e0, e1, e2;
       if (MODE == 1) {
         u0 = g0; u1 = g1; u2 = g2;
-        e0 = d0; e1 = d1; e2 = d2;
+        e0 = dv[0]; e1 = dv[1]; e2 = dv[2];
       } else {
-        const T v0 = g0 + d0, v1 = g1 + d1, v2 = g2 + d2;
+        const T v0 = g0 + dv[0], v1 = g1 + dv[1], v2 = g2 + dv[2];
         const T nrm = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
         const T sc = nrm > thr ? (nrm - thr) / nrm : (T)0;
         u0 = v0 * sc; u1 = v1 * sc; u2 = v2 * sc;
@@ -88,26 +138,27 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
       } else {
         rs[0][i] = u0 - e0; rs[1][i] = u1 - e1; rs[2][i] = u2 - e2;
       }
-      if (rr >= 1 && cc >= 1 && own_plane) {
+      if (interior && own_plane) {
         if (MODE == 0) {
           dout[gi] = e0; dout[V + gi] = e1; dout[2 * V + gi] = e2;
         }
         if (STATS) {
           const double gg = (double)g0 * g0 + (double)g1 * g1 + (double)g2 * g2;
           q[0] += sqrt(gg);
-          const double p0 = (double)e0 - d0, p1 = (double)e1 - d1, p2 = (double)e2 - d2;
+          const double p0 = (double)e0 - dv[0], p1 = (double)e1 - dv[1], p2 = (double)e2 - dv[2];
           q[1] += p0 * p0 + p1 * p1 + p2 * p2;
           q[2] += gg;
           q[3] += (double)u0 * u0 + (double)u1 * u1 + (double)u2 * u2;
         }
       }
-    }
+    };
+    point(ln + 1, lm + 1, di, pl + xo_in, true);
+    if (has_rh) point(rh_r, rh_c, dh, pl + ro_h, false);
+    if (more_x) store_x(xs[(cur + 2) % 3], xin_n, xh_n);
     __syncthreads();
     // phase 2: Theta = L^T rho on the tile
     {
-      const int own = (ln + 1) * RW + (lm + 1), left = own - 1, down = own - RW;
-      const int n = n0 + ln, m = m0 + lm;
-      const bool inside = n < N && m < M;
+      const int left = own - 1, down = own - RW;
       T r2, u2c = 0, d2c = 0;
       if (STATS) {
         u2c = rs[2][own];
@@ -116,8 +167,8 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
       } else {
         r2 = rs[2][own];
       }
-      if (own_plane && inside) {
-        const long long gi = sw * P + (long long)n * M + m;
+      if (own_plane) {
+        const long long gi = pl + xo_in;
         T th;
         if (STATS) {
           const T psi_v = (rs[0][left] - rs[0][own]) + (rs[1][down] - rs[1][own]) + (u2prev - u2c);
@@ -138,10 +189,14 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
       u2prev = u2c;
       d2prev = d2c;
     }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      di[c] = di_n[c];
+      dh[c] = dh_n[c];
+    }
+    (void)hpos;
     __syncthreads();
-    if (s + 2 <= s_end) load_x(xs[cur], s + 2);
-    __syncthreads();
-    cur ^= 1;
+    cur = (cur + 1) % 3;
   }
   if (STATS) {
     __shared__ double red[NQ][TM * TN / 32];

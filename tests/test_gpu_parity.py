@@ -25,6 +25,11 @@ CASES = [
     ((32, 16, 8), (1, 1, 1), "f32"),
     ((32, 32, 32), (2, 2, 2), "f64"),
     ((96, 24, 12), (2, 1, 3), "f64"),
+    # lengths with compile-time FFT plans: m half-length 128 / 256, n 256 / 512, s 256
+    ((256, 256, 16), (2, 2, 2), "f32"),
+    ((64, 16, 256), (2, 2, 2), "f32"),
+    ((512, 32, 16), (1, 1, 4), "f32"),
+    ((32, 512, 8), (1, 2, 1), "f32"),
 ]
 IDS = [f"{d[0]}x{d[1]}x{d[2]}_d{c[0]}{c[1]}{c[2]}_{t}" for d, c, t in CASES]
 
