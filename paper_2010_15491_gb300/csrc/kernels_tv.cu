@@ -216,6 +216,259 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
   }
 }
 
+// ---------------------------------------------------------------------------
+// Vectorised variant for FP32 volumes with m_h a multiple of 128: a CTA of
+// 32 x 8 threads covers m in [m0, m0+128) x n in [n0, n0+8), each thread four
+// consecutive m voxels (float4 loads and stores).  Warp 0 also evaluates the
+// -n halo row of the rho region, warp 1 the -m halo column; x halo rows come
+// through warps 0 and 7, halo columns through warp 1.  Same algebra, modes
+// and statistics as k_tv.  Shared rows are padded so that m0 sits at column
+// 4 (16-byte aligned); column 3 is m0-1 and column 132 is m0+128.
+// ---------------------------------------------------------------------------
+constexpr int V4M = 128;
+constexpr int V4W = 136;  // padded row length (floats)
+
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float4 lds4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float f4(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+
+// asynchronous global -> shared copies (cp.async, completion by wait_group)
+__device__ __forceinline__ void cp16(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp4(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <int MODE, bool STATS>
+__global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const float* __restrict__ din,
+                                             float* __restrict__ dout, float* __restrict__ theta,
+                                             float* __restrict__ psi, int M, int N, int S, int TS, float thr,
+                                             double* __restrict__ partial) {
+  constexpr int XR = TN + 2;  // x rows n0-1 .. n0+8
+  constexpr int RR = TN + 1;  // rho / d rows n0-1 .. n0+7
+  extern __shared__ __align__(16) float sm4[];
+  float* xs = sm4;                       // [3][XR][V4W]: x planes s, s+1, s+2
+  float* ds = xs + 3 * XR * V4W;         // [2][3][RR][V4W]: d planes s, s+1
+  float* rs = ds + 2 * 3 * RR * V4W;     // [NC][RR][V4W]
+  constexpr int XP = XR * V4W, DP = 3 * RR * V4W, RP = RR * V4W;
+  const int lm = threadIdx.x, ln = threadIdx.y, tid = ln * 32 + lm;
+  const int m0 = blockIdx.x * V4M, n0 = blockIdx.y * TN, s0 = blockIdx.z * TS;
+  const long long V = (long long)M * N * S;
+  const long long P = (long long)M * N;
+  const int s_end = min(S, s0 + TS);
+  const int mc = 4 + 4 * lm;  // shared column of the thread's first voxel
+  const long long o_in = (long long)(n0 + ln) * M + m0 + 4 * lm;            // interior
+  const long long o_hr = (long long)((n0 - 1 + N) % N) * M + m0 + 4 * lm;  // row n0-1 (warp 0)
+  const long long o_xr = (long long)((n0 + TN) % N) * M + m0 + 4 * lm;     // row n0+8 (warp 7, x only)
+  // warp 1: lane < 10 -> x column m0-1 of row n0-1+lane; 10 <= lane < 20 -> column m0+128
+  const bool xcol = ln == 1 && lm < 20;
+  const int xc_row = lm < 10 ? lm : lm - 10;
+  const int xc_col = lm < 10 ? 3 : 4 + V4M;
+  const long long o_xc = (long long)((n0 - 1 + xc_row + N) % N) * M + (lm < 10 ? (m0 - 1 + M) % M : (m0 + V4M) % M);
+  // warp 1: lane < RR -> d (and rho) column m0-1 of row n0-1+lane
+  const bool rcol = ln == 1 && lm < RR;
+  const long long o_rc = (long long)((n0 - 1 + lm + N) % N) * M + (m0 - 1 + M) % M;
+  auto plane_of = [&](int s) -> long long { return (long long)((s + S) % S) * P; };
+
+  auto fetch_x = [&](int s, float* buf) {
+    const long long pl = plane_of(s);
+    cp16(buf + (ln + 1) * V4W + mc, x + pl + o_in);
+    if (ln == 0) cp16(buf + mc, x + pl + o_hr);
+    else if (ln == TN - 1) cp16(buf + (XR - 1) * V4W + mc, x + pl + o_xr);
+    if (xcol) cp4(buf + xc_row * V4W + xc_col, x + pl + o_xc);
+  };
+  auto fetch_d = [&](int s, float* buf) {
+    const long long pl = plane_of(s);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cp16(buf + k * RP + (ln + 1) * V4W + mc, din + k * V + pl + o_in);
+      if (ln == 0) cp16(buf + k * RP + mc, din + k * V + pl + o_hr);
+      if (rcol) cp4(buf + k * RP + lm * V4W + 3, din + k * V + pl + o_rc);
+    }
+  };
+
+  double q[NQ] = {0, 0, 0, 0, 0, 0};
+  float4 r2prev = make_float4(0, 0, 0, 0), u2prev = r2prev, e2prev = r2prev;
+  fetch_x(s0 - 1, xs);
+  fetch_x(s0, xs + XP);
+  fetch_d(s0 - 1, ds);
+  cp_commit();
+  cp_wait_all();
+  __syncthreads();
+  int cur = 0;
+  for (int s = s0 - 1; s < s_end; ++s) {
+    const int it = s - (s0 - 1);
+    if (s + 2 <= s_end) fetch_x(s + 2, xs + ((cur + 2) % 3) * XP);
+    if (s + 1 < s_end) fetch_d(s + 1, ds + ((it + 1) & 1) * DP);
+    cp_commit();
+    const float* xc = xs + cur * XP;
+    const float* xn = xs + ((cur + 1) % 3) * XP;
+    const float* dd = ds + (it & 1) * DP;
+    const long long pl = plane_of(s);
+    const bool own_plane = s >= s0;
+
+    // one voxel of the rho region: shrink, dual, rho into shared row rr, column cc
+    auto voxel = [&](int rr, int cc, float g0, float g1, float g2, float d0, float d1, float d2, float& u0,
+                     float& u1, float& u2, float& e0, float& e1, float& e2) {
+      if (MODE == 1) {
+        u0 = g0; u1 = g1; u2 = g2;
+        e0 = d0; e1 = d1; e2 = d2;
+      } else {
+        const float v0 = g0 + d0, v1 = g1 + d1, v2 = g2 + d2;
+        const float nrm = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
+        const float sc = nrm > thr ? (nrm - thr) / nrm : 0.f;
+        u0 = v0 * sc; u1 = v1 * sc; u2 = v2 * sc;
+        e0 = v0 - u0; e1 = v1 - u1; e2 = v2 - u2;
+      }
+      const int i = rr * V4W + cc;
+      if (STATS) {
+        rs[0 * RP + i] = u0; rs[1 * RP + i] = u1; rs[2 * RP + i] = u2;
+        rs[3 * RP + i] = e0; rs[4 * RP + i] = e1; rs[5 * RP + i] = e2;
+      } else {
+        rs[0 * RP + i] = u0 - e0; rs[1 * RP + i] = u1 - e1; rs[2 * RP + i] = u2 - e2;
+      }
+    };
+    // four voxels of shared row xr (x rows xr, xr+1; rho / d row xr), columns mc..mc+3
+    auto quad = [&](int xr, bool interior) {
+      const float4 a = lds4(xc + xr * V4W + mc);
+      const float a4 = xc[xr * V4W + mc + 4];
+      const float4 b = lds4(xc + (xr + 1) * V4W + mc);
+      const float4 c = lds4(xn + xr * V4W + mc);
+      const float4 dv0 = lds4(dd + 0 * RP + xr * V4W + mc);
+      const float4 dv1 = lds4(dd + 1 * RP + xr * V4W + mc);
+      const float4 dv2 = lds4(dd + 2 * RP + xr * V4W + mc);
+      float e0v[4], e1v[4], e2v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float xv = f4(a, i);
+        const float g0 = (i < 3 ? f4(a, i + 1) : a4) - xv;
+        const float g1 = f4(b, i) - xv;
+        const float g2 = f4(c, i) - xv;
+        float u0, u1, u2;
+        voxel(xr, mc + i, g0, g1, g2, f4(dv0, i), f4(dv1, i), f4(dv2, i), u0, u1, u2, e0v[i], e1v[i], e2v[i]);
+        if (STATS && interior && own_plane) {
+          const double gg = (double)g0 * g0 + (double)g1 * g1 + (double)g2 * g2;
+          q[0] += sqrt(gg);
+          const double p0 = (double)e0v[i] - f4(dv0, i), p1 = (double)e1v[i] - f4(dv1, i),
+                       p2 = (double)e2v[i] - f4(dv2, i);
+          q[1] += p0 * p0 + p1 * p1 + p2 * p2;
+          q[2] += gg;
+          q[3] += (double)u0 * u0 + (double)u1 * u1 + (double)u2 * u2;
+        }
+      }
+      if (MODE == 0 && interior && own_plane) {
+        const long long gi = pl + o_in;
+        st4(dout + gi, make_float4(e0v[0], e0v[1], e0v[2], e0v[3]));
+        st4(dout + V + gi, make_float4(e1v[0], e1v[1], e1v[2], e1v[3]));
+        st4(dout + 2 * V + gi, make_float4(e2v[0], e2v[1], e2v[2], e2v[3]));
+      }
+    };
+    quad(ln + 1, true);
+    if (ln == 0) quad(0, false);
+    if (rcol) {
+      // halo column m0-1 (shared column 3), row lm
+      const int xr = lm;
+      const float xv = xc[xr * V4W + 3];
+      float u0, u1, u2, e0, e1, e2;
+      voxel(xr, 3, xc[xr * V4W + 4] - xv, xc[(xr + 1) * V4W + 3] - xv, xn[xr * V4W + 3] - xv,
+            dd[0 * RP + xr * V4W + 3], dd[1 * RP + xr * V4W + 3], dd[2 * RP + xr * V4W + 3], u0, u1, u2, e0, e1,
+            e2);
+    }
+    __syncthreads();
+    // phase 2: Theta = L^T rho for the four interior voxels
+    {
+      const int row = (ln + 1) * V4W + mc;
+      const int up = ln * V4W + mc;
+      float4 own0, own1, own2, up1;
+      float4 u_0, u_1, u_2, e_0, e_1, e_2, uup1, eup1;
+      float left0;
+      if (STATS) {
+        u_0 = lds4(rs + 0 * RP + row); u_1 = lds4(rs + 1 * RP + row); u_2 = lds4(rs + 2 * RP + row);
+        e_0 = lds4(rs + 3 * RP + row); e_1 = lds4(rs + 4 * RP + row); e_2 = lds4(rs + 5 * RP + row);
+        uup1 = lds4(rs + 1 * RP + up); eup1 = lds4(rs + 4 * RP + up);
+        own0 = make_float4(u_0.x - e_0.x, u_0.y - e_0.y, u_0.z - e_0.z, u_0.w - e_0.w);
+        own1 = make_float4(u_1.x - e_1.x, u_1.y - e_1.y, u_1.z - e_1.z, u_1.w - e_1.w);
+        own2 = make_float4(u_2.x - e_2.x, u_2.y - e_2.y, u_2.z - e_2.z, u_2.w - e_2.w);
+        up1 = make_float4(uup1.x - eup1.x, uup1.y - eup1.y, uup1.z - eup1.z, uup1.w - eup1.w);
+        left0 = rs[0 * RP + row - 1] - rs[3 * RP + row - 1];
+      } else {
+        own0 = lds4(rs + 0 * RP + row); own1 = lds4(rs + 1 * RP + row); own2 = lds4(rs + 2 * RP + row);
+        up1 = lds4(rs + 1 * RP + up);
+        left0 = rs[0 * RP + row - 1];
+      }
+      if (own_plane) {
+        float th[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const float lft = i == 0 ? left0 : f4(own0, i - 1);
+          th[i] = (lft - f4(own0, i)) + (f4(up1, i) - f4(own1, i)) + (f4(r2prev, i) - f4(own2, i));
+        }
+        const long long gi = pl + o_in;
+        st4(theta + gi, make_float4(th[0], th[1], th[2], th[3]));
+        if (STATS) {
+          const float ul = rs[0 * RP + row - 1], el = rs[3 * RP + row - 1];
+          float pv[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const float lu = i == 0 ? ul : f4(u_0, i - 1);
+            const float le = i == 0 ? el : f4(e_0, i - 1);
+            const float psi_v = (lu - f4(u_0, i)) + (f4(uup1, i) - f4(u_1, i)) + (f4(u2prev, i) - f4(u_2, i));
+            const float ltd = (le - f4(e_0, i)) + (f4(eup1, i) - f4(e_1, i)) + (f4(e2prev, i) - f4(e_2, i));
+            pv[i] = psi_v;
+            q[5] += (double)ltd * ltd;
+          }
+          if (MODE == 0) {
+            const float4 old = ld4(psi + gi);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const double dl = (double)pv[i] - (double)f4(old, i);
+              q[4] += dl * dl;
+            }
+          }
+          st4(psi + gi, make_float4(pv[0], pv[1], pv[2], pv[3]));
+        }
+      }
+      r2prev = own2;
+      if (STATS) {
+        u2prev = u_2;
+        e2prev = e_2;
+      }
+    }
+    cp_wait_all();
+    __syncthreads();
+    cur = (cur + 1) % 3;
+  }
+  if (STATS) {
+    __shared__ double red[NQ][8];
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+      const double v = warp_sum_d(q[k]);
+      if (lane == 0) red[k][warp] = v;
+    }
+    __syncthreads();
+    if (tid < NQ) {
+      double v = 0;
+      for (int w = 0; w < 8; ++w) v += red[tid][w];
+      const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+      partial[b * NQ + tid] = v;
+    }
+  }
+}
+
+static size_t tv4_smem(bool stats) {
+  return sizeof(float) * ((size_t)3 * (TN + 2) * V4W + (size_t)2 * 3 * (TN + 1) * V4W +
+                          (size_t)(stats ? 6 : 3) * (TN + 1) * V4W);
+}
+
+static bool tv_vec4(const Plan& p) { return p.dtype == 0 && p.hr.M % V4M == 0 && p.hr.N % TN == 0; }
+
 static int tv_ts(const Geometry& g) {
   // planes per CTA: aim for a few CTAs per SM-slot while keeping the
   // one-plane priming overhead small
@@ -225,6 +478,7 @@ static int tv_ts(const Geometry& g) {
 }
 
 long long tv_blocks(const Geometry& g) {
+  // an upper bound covering both variants (the vectorised one has 4x fewer m tiles)
   const int ts = tv_ts(g);
   return (long long)((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN) * ((g.S + ts - 1) / ts);
 }
@@ -241,9 +495,32 @@ static cudaError_t tv_k(const Plan& p, const void* x, const void* din, void* dou
   return cudaGetLastError();
 }
 
+template <int MODE, bool STATS>
+static cudaError_t tv4_k(const Plan& p, const void* x, const void* din, void* dout, void* theta, void* psi,
+                         double thr) {
+  const Geometry& g = p.hr;
+  const int ts = tv_ts(g);
+  dim3 grid(g.M / V4M, g.N / TN, (g.S + ts - 1) / ts);
+  dim3 block(32, TN);
+  const size_t smem = tv4_smem(STATS);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_tv4<MODE, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_tv4<MODE, STATS><<<grid, block, smem, p.stream>>>((const float*)x, (const float*)din, (float*)dout,
+                                                   (float*)theta, (float*)psi, g.M, g.N, g.S, ts, (float)thr,
+                                                   p.partial);
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t tv_t(const Plan& p, const void* x, const void* din, void* dout, void* theta, void* psi,
                         double thr, int mode, bool stats) {
+  if (tv_vec4(p)) {
+    if (mode == 0)
+      return stats ? tv4_k<0, true>(p, x, din, dout, theta, psi, thr) : tv4_k<0, false>(p, x, din, dout, theta, psi, thr);
+    return stats ? tv4_k<1, true>(p, x, din, dout, theta, psi, thr) : tv4_k<1, false>(p, x, din, dout, theta, psi, thr);
+  }
   if (mode == 0)
     return stats ? tv_k<T, 0, true>(p, x, din, dout, theta, psi, thr)
                  : tv_k<T, 0, false>(p, x, din, dout, theta, psi, thr);
@@ -307,9 +584,17 @@ __global__ void k_finalize(const double* __restrict__ ptv, long long ntv, const 
   }
 }
 
+// number of CTAs (and partial-sum rows) of the TV variant the plan launches
+static long long tv_launch_blocks(const Plan& p) {
+  const Geometry& g = p.hr;
+  const int ts = tv_ts(g);
+  const long long mt = tv_vec4(p) ? g.M / V4M : (g.M + TM - 1) / TM;
+  return mt * ((g.N + TN - 1) / TN) * ((g.S + ts - 1) / ts);
+}
+
 cudaError_t launch_finalize(const Plan& p, int hist_index, double lam_tv, double mu, double inv_nl,
                             bool with_data) {
-  k_finalize<<<1, 256, 0, p.stream>>>(p.partial, p.n_tv_blocks, p.partial_s, p.n_s_blocks, lam_tv, mu, inv_nl,
+  k_finalize<<<1, 256, 0, p.stream>>>(p.partial, tv_launch_blocks(p), p.partial_s, p.n_s_blocks, lam_tv, mu, inv_nl,
                                       with_data ? 1 : 0, p.result, p.hist, hist_index);
   return cudaGetLastError();
 }
