@@ -170,7 +170,8 @@ static int dmalloc(Plan& p, void** ptr, size_t bytes) {
 }
 
 static void free_plan(Plan& p) {
-  void* bufs[] = {p.twM, p.twN, p.twS, p.twMl, p.twNl, p.twSl, p.symM, p.symN, p.symS, p.lam, p.yhat, p.spec,
+  void* bufs[] = {p.twM, p.twN, p.twS, p.twMl, p.twNl, p.twSl, p.symM, p.symN, p.symS, p.lam, p.lam_solve,
+                  p.yhat_solve, p.yhat, p.spec,
                   p.theta, p.dbuf[0], p.dbuf[1], p.psi, p.xh, p.yh, p.partial, p.partial_s, p.result, p.hist};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -184,8 +185,8 @@ static SolveArgs solve_args(const Plan& p, int mode_alpha_nn, double alpha) {
   SolveArgs sv;
   memset(&sv, 0, sizeof(sv));
   const Geometry& g = p.hr;
-  sv.lam = p.lam;
-  sv.yhat = p.yhat;
+  sv.lam = p.lam_solve;
+  sv.yhat = p.yhat_solve;
   sv.lr_out = p.yhat;
   sv.symM = p.symM; sv.symN = p.symN; sv.symS = p.symS;
   sv.twM = p.twM; sv.twN = p.twN; sv.twS = p.twS;
@@ -206,6 +207,7 @@ static int lr_spectrum(Plan& p, const void* y) {
   LAUNCH(SR3D_K_RFFT_FWD, launch_rfft_m_fwd(p, p.lr, y, p.yhat, p.twMl));
   LAUNCH(SR3D_K_FFTN_FWD, launch_fft_n(p, p.lr, p.yhat, p.twNl, false));
   LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.lr, p.yhat, p.twSl, S_FWD, false, nullptr));
+  LAUNCH(SR3D_K_OTHER, launch_perm_yhat(p, p.yhat, p.yhat_solve));
   return SR3D_OK;
 }
 
@@ -322,6 +324,8 @@ int sr3d_plan(sr3d_plan_t* out, const sr3d_desc* d) {
     TRY(dmalloc(p, &p.lam, (size_t)g.spec_elems() * csz));
     TRY(dmalloc(p, &p.spec, (size_t)g.spec_elems() * csz));
     TRY(dmalloc(p, &p.yhat, (size_t)l.spec_elems() * csz));
+    TRY(dmalloc(p, &p.lam_solve, (size_t)solve_lam_elems(g) * csz));
+    TRY(dmalloc(p, &p.yhat_solve, (size_t)solve_yhat_elems(g) * csz));
     TRY(dmalloc(p, &p.theta, (size_t)g.V() * p.esz));
     p.n_tv_blocks = tv_blocks(g);
     p.n_s_blocks = s_pass_blocks(g);
@@ -347,6 +351,7 @@ int sr3d_plan(sr3d_plan_t* out, const sr3d_desc* d) {
     if (e == cudaSuccess) e = launch_rfft_m_fwd(p, g, p.theta, p.lam, p.twM);
     if (e == cudaSuccess) e = launch_fft_n(p, g, p.lam, p.twN, false);
     if (e == cudaSuccess) e = launch_fft_s(p, g, p.lam, p.twS, S_FWD, false, nullptr);
+    if (e == cudaSuccess) e = launch_perm_lam(p, p.lam, p.lam_solve);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
     cudaFree(psf_dev);
     if (e != cudaSuccess) return fail(SR3D_ERR_CUDA, "plan setup: %s", cudaGetErrorString(e));
@@ -655,16 +660,16 @@ extern "C" int sr3d_tikhonov_noalloc(const sr3d_desc* d, const void* y, const vo
   const long long np = (long long)d->p_m * d->p_n * d->p_s;
   const Geometry& g = p.hr;
   const Geometry& l = p.lr;
-  const size_t sizes[12] = {(size_t)g.M * csz, (size_t)g.N * csz, (size_t)g.S * csz, (size_t)l.M * csz,
+  const size_t sizes[13] = {(size_t)g.M * csz, (size_t)g.N * csz, (size_t)g.S * csz, (size_t)l.M * csz,
                             (size_t)l.N * csz, (size_t)l.S * csz, (size_t)g.M * p.esz, (size_t)g.N * p.esz,
-                            (size_t)g.S * p.esz, (size_t)g.spec_elems() * csz, (size_t)g.spec_elems() * csz,
-                            (size_t)l.spec_elems() * csz};
+                            (size_t)g.S * p.esz, (size_t)solve_lam_elems(g) * csz, (size_t)g.spec_elems() * csz,
+                            (size_t)l.spec_elems() * csz, (size_t)solve_yhat_elems(g) * csz};
   size_t need = 0, off[14];
-  for (int i = 0; i < 12; ++i) {
+  for (int i = 0; i < 13; ++i) {
     off[i] = need;
     need += (sizes[i] + 255) & ~(size_t)255;
   }
-  off[12] = need;
+  off[13] = need;
   need += ((size_t)np * sizeof(double) + 255) & ~(size_t)255;
   if (need > (size_t)SR3D_NOALLOC_BYTES)
     return fail(SR3D_ERR_UNSUPPORTED_SIZE,
@@ -676,11 +681,16 @@ extern "C" int sr3d_tikhonov_noalloc(const sr3d_desc* d, const void* y, const vo
   p.twM = b + off[0]; p.twN = b + off[1]; p.twS = b + off[2];
   p.twMl = b + off[3]; p.twNl = b + off[4]; p.twSl = b + off[5];
   p.symM = b + off[6]; p.symN = b + off[7]; p.symS = b + off[8];
-  p.lam = b + off[9];
+  p.lam_solve = b + off[9];
   p.spec = b + off[10];
   p.yhat = b + off[11];
-  p.theta = p.spec;  // the wrapped PSF (real HR volume) only lives until Lambda is formed
-  double* psf_dev = (double*)(b + off[12]);
+  p.yhat_solve = b + off[12];
+  // scratch reuse without aliasing inside any kernel: the wrapped PSF (a real
+  // HR volume) sits in the solve-order region until Lambda is formed in the
+  // spec region; the permutation then overwrites the solve-order region
+  p.theta = p.lam_solve;
+  p.lam = p.spec;
+  double* psf_dev = (double*)(b + off[13]);
 
   CK(launch_twiddle(p, p.twM, g.M));
   CK(launch_twiddle(p, p.twN, g.N));
@@ -694,9 +704,11 @@ extern "C" int sr3d_tikhonov_noalloc(const sr3d_desc* d, const void* y, const vo
   CK(cudaMemcpyAsync(psf_dev, d->psf, (size_t)np * sizeof(double), cudaMemcpyHostToDevice, p.stream));
   CK(cudaMemsetAsync(p.theta, 0, (size_t)g.V() * p.esz, p.stream));  // the wrap fills only the PSF taps
   CK(launch_wrap_psf(p, p.theta, psf_dev, d->p_m, d->p_n, d->p_s));
+  // Lambda: wrapped PSF -> spectrum (spec region) -> solve order
   CK(launch_rfft_m_fwd(p, g, p.theta, p.lam, p.twM));
   CK(launch_fft_n(p, g, p.lam, p.twN, false));
   CK(launch_fft_s(p, g, p.lam, p.twS, S_FWD, false, nullptr));
+  CK(launch_perm_lam(p, p.lam, p.lam_solve));
   TRY(lr_spectrum(p, y));
   TRY(tikhonov_core(p, xbar, tau, x));
   CK(cudaStreamSynchronize(p.stream));

@@ -21,8 +21,8 @@ enum SMode {
 
 // Arguments of the per-aliasing-class solve inside the s pass.
 struct SolveArgs {
-  const void* lam;     // Lambda, HR spectral layout
-  const void* yhat;    // LR spectrum [Sl][Nl][Mlp]
+  const void* lam;     // Lambda in solve order (k_perm_lam)
+  const void* yhat;    // LR spectrum in solve order (k_perm_yhat)
   void* lr_out;        // S_FOLD output, LR spectral layout
   const void* symM;    // 4 sin^2(pi k / M) tables (element type T)
   const void* symN;
@@ -64,6 +64,8 @@ struct Plan {
   void* twMl = nullptr; void* twNl = nullptr; void* twSl = nullptr;  // LR twiddles
   void* symM = nullptr; void* symN = nullptr; void* symS = nullptr;
   void* lam = nullptr;    // HR spectral
+  void* lam_solve = nullptr;   // Lambda in the solve order of the s pass
+  void* yhat_solve = nullptr;  // LR spectrum in the same order
   void* yhat = nullptr;   // LR spectral
   void* spec = nullptr;   // HR spectral work
   void* theta = nullptr;  // HR real
@@ -95,6 +97,10 @@ cudaError_t launch_fft_n(const Plan& p, const Geometry& g, void* spec, const voi
 cudaError_t launch_fft_s(const Plan& p, const Geometry& g, void* spec, const void* tw, int mode, bool stats,
                          const SolveArgs* sv);
 long long s_pass_blocks(const Geometry& g);
+long long solve_lam_elems(const Geometry& g);
+long long solve_yhat_elems(const Geometry& g);
+cudaError_t launch_perm_lam(const Plan& p, const void* lam, void* out);
+cudaError_t launch_perm_yhat(const Plan& p, const void* yh, void* out);
 
 // ---- launchers (kernels_tv.cu) ----
 // mode 0: ADMM step (shrink + dual update); mode 1: initial Theta = L^T (L x - d)

@@ -170,7 +170,149 @@ __device__ __forceinline__ C box_factor(const C* __restrict__ tw, int n, int da,
 
 constexpr int DMAX = 8;  // largest supported d = dr*dc*ds
 
-template <typename T, int EMAX, int MODE, bool STATS, int NC>
+// Solve order of the per-class constants: for the s-pass CTA bc = (by, bx),
+// class c of the tile (c = gm + GMc * (gn + GNc * is)) and member q
+// (q = pm + dr * (pn + dc * ps)), Lambda sits at (bc * d + q) * ncls + c and
+// the LR spectrum at bc * ncls + c, so the solve's loads are contiguous
+// across a warp.  solve_layout gives the tile sizes shared by the kernels
+// and the permutations.
+struct SolveTile {
+  int GMc, GNc, ncls, Gm, gx;
+};
+__host__ __device__ __forceinline__ SolveTile solve_layout(int Ms, int TW, int G, int dr, int dc, int Sl) {
+  SolveTile t;
+  t.GMc = TW / dr;
+  t.GNc = G / dc;
+  t.ncls = t.GMc * t.GNc * Sl;
+  t.Gm = Ms / dr;
+  t.gx = (Ms + TW - 1) / TW;
+  return t;
+}
+
+// Per-aliasing-class solve of eq. (12) (Tikhonov, w = 1/tau) or of the
+// Gamma-weighted x-update of Algorithm 1 step 5a (ADMM, w_p = 1/(mu s_p)) on
+// a tile held in shared memory, and the fold of S_FOLD.  DR_/DC_/DS_ > 0 fix
+// the class shape at compile time; 0 takes it from sv.  Returns this
+// thread's share of sum_i |Y_i - (1/d) sum_p Lambda_p X_p|^2 (STATS).
+template <typename T, int MODE, bool STATS, int DR_, int DC_, int DS_>
+__device__ __forceinline__ double solve_tile(cplx<T>* sm, int TW, int G, int a0, int b0, int Ms, const SolveArgs& sv,
+                                             int tid, int nthr) {
+  using C = cplx<T>;
+  const int dr = DR_ > 0 ? DR_ : sv.dr, dc = DR_ > 0 ? DC_ : sv.dc, ds = DR_ > 0 ? DS_ : sv.ds;
+  const int d = dr * dc * ds;
+  const T dd = (T)d;
+  const SolveTile tl = solve_layout(Ms, TW, G, dr, dc, sv.Sl);
+  const int ncls = tl.ncls;
+  const long long bc = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+  const C* __restrict__ lamc = reinterpret_cast<const C*>(sv.lam) + bc * d * ncls;
+  const C* __restrict__ yhc = reinterpret_cast<const C*>(sv.yhat) + bc * ncls;
+  const T* __restrict__ symM = reinterpret_cast<const T*>(sv.symM);
+  const T* __restrict__ symN = reinterpret_cast<const T*>(sv.symN);
+  const T* __restrict__ symS = reinterpret_cast<const T*>(sv.symS);
+  const T alpha = (T)sv.alpha;
+  const T ialpha = (T)(1.0 / sv.alpha);
+  double acc = 0.0;
+  for (int c = tid; c < ncls; c += nthr) {
+    const int gm = c % tl.GMc;
+    const int rest = c / tl.GMc;
+    const int gn = rest % tl.GNc;
+    const int is = rest / tl.GNc;
+    const int g = a0 / dr + gm;
+    if (g >= tl.Gm) continue;
+    const int jl = b0 / dc + gn;
+    if (MODE == S_FOLD) {
+      C tsum = czero<C>();
+      for (int q = 0; q < d; ++q) {
+        const int pm = q % dr, pn = (q / dr) % dc, ps = q / (dr * dc);
+        const int si = ((is + ps * sv.Sl) * G + gn * dc + pn) * TW + gm * dr + pm;
+        tsum = tsum + cmul(__ldg(&lamc[(long long)q * ncls + c]), sm[si]);
+      }
+      reinterpret_cast<C*>(sv.lr_out)[((long long)is * sv.Nl + jl) * sv.Mlp + g] = tsum * (T)(1.0 / d);
+      continue;
+    }
+    const C Yc = __ldg(&yhc[c]);
+    const bool dc_cls = (MODE == S_ADMM) && g == 0 && jl == 0 && is == 0;
+    C av[DMAX], bv[DMAX];
+    T wv[DMAX];
+    int si[DMAX];
+    int qs = 0;
+    T best = (T)-1;
+#pragma unroll
+    for (int q = 0; q < DMAX; ++q) {
+      if (q < d) {
+        const int pm = q % dr, pn = (q / dr) % dc, ps = q / (dr * dc);
+        const int ks = is + ps * sv.Sl, kn = jl + pn * sv.Nl, km = g + pm * sv.Ml;
+        si[q] = (ks * G + gn * dc + pn) * TW + gm * dr + pm;
+        const C a_ = __ldg(&lamc[(long long)q * ncls + c]);
+        C B = cmulc(a_, Yc);  // conj(Lambda_p) Y: F H^H D^H y at this frequency
+        T w;
+        if (MODE == S_ADMM) {
+          B = B + sm[si[q]] * alpha;  // + mu F Theta
+          const T sy = __ldg(&symM[km]) + __ldg(&symN[kn]) + __ldg(&symS[ks]);
+          w = (dc_cls && q == 0) ? (T)0 : (T)1 / (alpha * sy);  // Gamma / mu
+        } else {
+          if (MODE == S_TIK_USER) B = B + sm[si[q]] * alpha;  // + tau F xbar
+          if (MODE == S_TIK_GEN && sv.nn_prior) {
+            const C bx = cmul(cmul(box_factor<C, T>(reinterpret_cast<const C*>(sv.twM), sv.M, dr, km),
+                                   box_factor<C, T>(reinterpret_cast<const C*>(sv.twN), sv.N, dc, kn)),
+                              box_factor<C, T>(reinterpret_cast<const C*>(sv.twS), sv.S, ds, ks));
+            B = B + cmul(Yc, bx) * alpha;  // + tau F xbar, xbar = nearest-neighbour y
+          }
+          w = ialpha;
+        }
+        const T key = (dc_cls && q == 0) ? Lim<T>::big : norm2(a_) * w;
+        if (key > best) { best = key; qs = q; }
+        av[q] = a_;
+        bv[q] = B;
+        wv[q] = w;
+      }
+    }
+    // Sherman-Morrison on the class block diag(1/w) + (1/d) conj(a) a^T with
+    // the dominant member p* = qs kept out of the sums (no cancellation).
+    T Sp = 0;
+    C Tp = czero<C>(), as = czero<C>(), bs = czero<C>();
+    T ws = 0;
+#pragma unroll
+    for (int q = 0; q < DMAX; ++q) {
+      if (q < d) {
+        if (q == qs) {
+          as = av[q]; bs = bv[q]; ws = wv[q];
+        } else {
+          Sp += norm2(av[q]) * wv[q];
+          Tp = Tp + cmul(av[q], bv[q]) * wv[q];
+        }
+      }
+    }
+    C Xs, ratio;
+    if (dc_cls) {
+      // zero frequency: Gamma singular, the class is solved exactly
+      const T inv = (T)1 / norm2(as);
+      Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * inv;
+      ratio = cmul(bs, as) * inv;  // B_* / conj(Lambda_*)
+    } else {
+      const T iD = (T)1 / (dd + Sp + norm2(as) * ws);
+      Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * (ws * iD);
+      ratio = (Tp + cmul(as, bs) * ws) * iD;
+    }
+    C tsum = czero<C>();
+#pragma unroll
+    for (int q = 0; q < DMAX; ++q) {
+      if (q < d) {
+        const C X = (q == qs) ? Xs : (bv[q] - cmulc(av[q], ratio)) * wv[q];
+        sm[si[q]] = conjc(X);  // conjugated: the inverse runs through the forward engine
+        if (STATS) tsum = tsum + cmul(av[q], X);
+      }
+    }
+    if (STATS) {
+      const C R = Yc - tsum * (T)(1.0 / d);
+      const double wgt = (g == 0 || 2 * g == sv.Ml) ? 1.0 : 2.0;
+      acc += wgt * (double)norm2(R);
+    }
+  }
+  return acc;
+}
+
+template <typename T, int EMAX, int MODE, bool STATS, int NC, int DR_, int DC_, int DS_>
 __global__ void __launch_bounds__(512) k_fft_s(cplx<T>* __restrict__ spec, LAxis a, int Ms, int Mp, int Nn, int TW, int G, SolveArgs sv,
                         const cplx<T>* __restrict__ twS) {
   using C = cplx<T>;
@@ -209,118 +351,7 @@ __global__ void __launch_bounds__(512) k_fft_s(cplx<T>* __restrict__ spec, LAxis
   }
 
   if (MODE >= S_TIK_GEN) {
-    const int d = sv.dr * sv.dc * sv.ds;
-    const T dd = (T)d;
-    const int GMc = TW / sv.dr, GNc = G / sv.dc;
-    const int Gm = Ms / sv.dr;
-    const int ncls = GMc * GNc * sv.Sl;
-    const C* __restrict__ lam = reinterpret_cast<const C*>(sv.lam);
-    const C* __restrict__ yh = reinterpret_cast<const C*>(sv.yhat);
-    const T* __restrict__ symM = reinterpret_cast<const T*>(sv.symM);
-    const T* __restrict__ symN = reinterpret_cast<const T*>(sv.symN);
-    const T* __restrict__ symS = reinterpret_cast<const T*>(sv.symS);
-    const T alpha = (T)sv.alpha;
-    const T ialpha = (T)(1.0 / sv.alpha);
-    double acc = 0.0;
-    for (int c = tid; c < ncls; c += nthr) {
-      const int gm = c % GMc;
-      const int rest = c / GMc;
-      const int gn = rest % GNc;
-      const int is = rest / GNc;
-      const int g = a0 / sv.dr + gm;
-      if (g >= Gm) continue;
-      const int jl = b0 / sv.dc + gn;
-      if (MODE == S_FOLD) {
-        C tsum = czero<C>();
-        for (int q = 0; q < d; ++q) {
-          const int pm = q % sv.dr, pn = (q / sv.dr) % sv.dc, ps = q / (sv.dr * sv.dc);
-          const int ks = is + ps * sv.Sl, lrow = gn * sv.dc + pn, lcol = gm * sv.dr + pm;
-          const C av = __ldg(&lam[(long long)ks * plane + (long long)(b0 + lrow) * Mp + a0 + lcol]);
-          tsum = tsum + cmul(av, sm[(ks * G + lrow) * TW + lcol]);
-        }
-        reinterpret_cast<C*>(sv.lr_out)[((long long)is * sv.Nl + jl) * sv.Mlp + g] = tsum * (T)(1.0 / d);
-        continue;
-      }
-      const C Yc = __ldg(&yh[((long long)is * sv.Nl + jl) * sv.Mlp + g]);
-      const bool dc_cls = (MODE == S_ADMM) && g == 0 && jl == 0 && is == 0;
-      C av[DMAX], bv[DMAX];
-      T wv[DMAX];
-      int si[DMAX];
-      int qs = 0;
-      T best = (T)-1;
-#pragma unroll
-      for (int q = 0; q < DMAX; ++q) {
-        if (q < d) {
-          const int pm = q % sv.dr, pn = (q / sv.dr) % sv.dc, ps = q / (sv.dr * sv.dc);
-          const int ks = is + ps * sv.Sl, kn = jl + pn * sv.Nl, km = g + pm * sv.Ml;
-          const int lrow = gn * sv.dc + pn, lcol = gm * sv.dr + pm;
-          si[q] = (ks * G + lrow) * TW + lcol;
-          const C a_ = __ldg(&lam[(long long)ks * plane + (long long)(b0 + lrow) * Mp + a0 + lcol]);
-          C B = cmulc(a_, Yc);  // conj(Lambda_p) Y: F H^H D^H y at this frequency
-          T w;
-          if (MODE == S_ADMM) {
-            B = B + sm[si[q]] * alpha;  // + mu F Theta
-            const T sy = __ldg(&symM[km]) + __ldg(&symN[kn]) + __ldg(&symS[ks]);
-            w = (dc_cls && q == 0) ? (T)0 : (T)1 / (alpha * sy);  // Gamma / mu
-          } else {
-            if (MODE == S_TIK_USER) B = B + sm[si[q]] * alpha;  // + tau F xbar
-            if (MODE == S_TIK_GEN && sv.nn_prior) {
-              const C bx = cmul(cmul(box_factor<C, T>(reinterpret_cast<const C*>(sv.twM), sv.M, sv.dr, km),
-                                     box_factor<C, T>(reinterpret_cast<const C*>(sv.twN), sv.N, sv.dc, kn)),
-                                box_factor<C, T>(reinterpret_cast<const C*>(sv.twS), sv.S, sv.ds, ks));
-              B = B + cmul(Yc, bx) * alpha;  // + tau F xbar, xbar = nearest-neighbour y
-            }
-            w = ialpha;
-          }
-          const T key = (dc_cls && q == 0) ? Lim<T>::big : norm2(a_) * w;
-          if (key > best) { best = key; qs = q; }
-          av[q] = a_;
-          bv[q] = B;
-          wv[q] = w;
-        }
-      }
-      // Sherman-Morrison on the class block diag(1/w) + (1/d) conj(a) a^T with
-      // the dominant member p* = qs kept out of the sums (no cancellation).
-      T Sp = 0;
-      C Tp = czero<C>(), as = czero<C>(), bs = czero<C>();
-      T ws = 0;
-#pragma unroll
-      for (int q = 0; q < DMAX; ++q) {
-        if (q < d) {
-          if (q == qs) {
-            as = av[q]; bs = bv[q]; ws = wv[q];
-          } else {
-            Sp += norm2(av[q]) * wv[q];
-            Tp = Tp + cmul(av[q], bv[q]) * wv[q];
-          }
-        }
-      }
-      C Xs, ratio;
-      if (dc_cls) {
-        // zero frequency: Gamma singular, the class is solved exactly
-        const T inv = (T)1 / norm2(as);
-        Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * inv;
-        ratio = cmul(bs, as) * inv;  // B_* / conj(Lambda_*)
-      } else {
-        const T iD = (T)1 / (dd + Sp + norm2(as) * ws);
-        Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * (ws * iD);
-        ratio = (Tp + cmul(as, bs) * ws) * iD;
-      }
-      C tsum = czero<C>();
-#pragma unroll
-      for (int q = 0; q < DMAX; ++q) {
-        if (q < d) {
-          const C X = (q == qs) ? Xs : (bv[q] - cmulc(av[q], ratio)) * wv[q];
-          sm[si[q]] = conjc(X);  // conjugated: the inverse runs through the forward engine
-          if (STATS) tsum = tsum + cmul(av[q], X);
-        }
-      }
-      if (STATS) {
-        const C R = Yc - tsum * (T)(1.0 / d);
-        const double wgt = (g == 0 || 2 * g == sv.Ml) ? 1.0 : 2.0;
-        acc += wgt * (double)norm2(R);
-      }
-    }
+    double acc = solve_tile<T, MODE, STATS, DR_, DC_, DS_>(sm, TW, G, a0, b0, Ms, sv, tid, nthr);
     if (STATS) {
       __shared__ double red[32];
       acc = warp_sum(acc);
@@ -458,7 +489,7 @@ static cudaError_t fft_n_e(const Plan& p, const Geometry& g, void* spec, const v
   return cudaGetLastError();
 }
 
-template <typename T, int EMAX, int MODE, bool STATS, int NC>
+template <typename T, int EMAX, int MODE, bool STATS, int NC, int DR_ = 0, int DC_ = 0, int DS_ = 0>
 static cudaError_t fft_s_k(const Plan& p, const Geometry& g, void* spec, const void* tw, const SolveArgs& sv) {
   const int tpl = g.S / g.fs.e;
   const int TW = g.tw_s, G = g.g_s;
@@ -467,8 +498,8 @@ static cudaError_t fft_s_k(const Plan& p, const Geometry& g, void* spec, const v
   dim3 grid((g.Ms + TW - 1) / TW, g.N / G);
   LAxis a = laxis(g.S, g.Sl, g.ds, g.fs);
   cudaError_t e;
-  if ((e = allow_smem(k_fft_s<T, EMAX, MODE, STATS, NC>, smem)) != cudaSuccess) return e;
-  k_fft_s<T, EMAX, MODE, STATS, NC><<<grid, TW * G * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, g.N, TW,
+  if ((e = allow_smem(k_fft_s<T, EMAX, MODE, STATS, NC, DR_, DC_, DS_>, smem)) != cudaSuccess) return e;
+  k_fft_s<T, EMAX, MODE, STATS, NC, DR_, DC_, DS_><<<grid, TW * G * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, g.N, TW,
                                                                           G, sv, (const cplx<T>*)tw);
   return cudaGetLastError();
 }
@@ -483,9 +514,19 @@ static cudaError_t fft_s_e(const Plan& p, const Geometry& g, void* spec, const v
     case S_TIK_USER: return fft_s_k<T, EMAX, S_TIK_USER, false, 0>(p, g, spec, tw, sv);
     case S_ADMM:
       if constexpr (sizeof(T) == 4 && EMAX == 16) {
-        if (ct_len<T>(g.S, g.fs) == 256)
+        if (ct_len<T>(g.S, g.fs) == 256) {
+          if (g.dr == 2 && g.dc == 2 && g.ds == 2)
+            return stats ? fft_s_k<T, EMAX, S_ADMM, true, 256, 2, 2, 2>(p, g, spec, tw, sv)
+                         : fft_s_k<T, EMAX, S_ADMM, false, 256, 2, 2, 2>(p, g, spec, tw, sv);
+          if (g.dr == 1 && g.dc == 1 && g.ds == 4)
+            return stats ? fft_s_k<T, EMAX, S_ADMM, true, 256, 1, 1, 4>(p, g, spec, tw, sv)
+                         : fft_s_k<T, EMAX, S_ADMM, false, 256, 1, 1, 4>(p, g, spec, tw, sv);
           return stats ? fft_s_k<T, EMAX, S_ADMM, true, 256>(p, g, spec, tw, sv)
                        : fft_s_k<T, EMAX, S_ADMM, false, 256>(p, g, spec, tw, sv);
+        }
+        if (g.dr == 2 && g.dc == 2 && g.ds == 1)
+          return stats ? fft_s_k<T, EMAX, S_ADMM, true, 0, 2, 2, 1>(p, g, spec, tw, sv)
+                       : fft_s_k<T, EMAX, S_ADMM, false, 0, 2, 2, 1>(p, g, spec, tw, sv);
       }
       return stats ? fft_s_k<T, EMAX, S_ADMM, true, 0>(p, g, spec, tw, sv)
                    : fft_s_k<T, EMAX, S_ADMM, false, 0>(p, g, spec, tw, sv);
@@ -529,6 +570,83 @@ cudaError_t launch_fft_s(const Plan& p, const Geometry& g, void* spec, const voi
               : fft_s_e<double, Emax<double>::p2>(p, g, spec, tw, mode, stats, *sv);
   return f3 ? fft_s_e<float, Emax<float>::p3>(p, g, spec, tw, mode, stats, *sv)
             : fft_s_e<float, Emax<float>::p2>(p, g, spec, tw, mode, stats, *sv);
+}
+
+
+// ---------------------------------------------------------------------------
+// solve-order permutations of Lambda (plan time) and of the LR spectrum
+// (once per solve); see solve_layout.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_perm_lam(const cplx<T>* __restrict__ lam, cplx<T>* __restrict__ out, int Ms, int Mp, int N,
+                           int TW, int G, int dr, int dc, int ds, int Sl, long long total) {
+  const SolveTile tl = solve_layout(Ms, TW, G, dr, dc, Sl);
+  const int d = dr * dc * ds;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % tl.ncls);
+    const long long rest = idx / tl.ncls;
+    const int q = (int)(rest % d);
+    const long long bc = rest / d;
+    const int a0 = (int)(bc % tl.gx) * TW, b0 = (int)(bc / tl.gx) * G;
+    const int gm = c % tl.GMc, gn = (c / tl.GMc) % tl.GNc, is = c / (tl.GMc * tl.GNc);
+    const int pm = q % dr, pn = (q / dr) % dc, ps = q / (dr * dc);
+    cplx<T> v = czero<cplx<T>>();
+    if (a0 / dr + gm < tl.Gm)
+      v = lam[((long long)(is + ps * Sl) * N + b0 + gn * dc + pn) * Mp + a0 + gm * dr + pm];
+    out[idx] = v;
+  }
+}
+
+template <typename T>
+__global__ void k_perm_yhat(const cplx<T>* __restrict__ yh, cplx<T>* __restrict__ out, int Ms, int TW, int G,
+                            int dr, int dc, int Sl, int Nl, int Mlp, long long total) {
+  const SolveTile tl = solve_layout(Ms, TW, G, dr, dc, Sl);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % tl.ncls);
+    const long long bc = idx / tl.ncls;
+    const int a0 = (int)(bc % tl.gx) * TW, b0 = (int)(bc / tl.gx) * G;
+    const int gm = c % tl.GMc, gn = (c / tl.GMc) % tl.GNc, is = c / (tl.GMc * tl.GNc);
+    const int g = a0 / dr + gm, jl = b0 / dc + gn;
+    out[idx] = g < tl.Gm ? yh[((long long)is * Nl + jl) * Mlp + g] : czero<cplx<T>>();
+  }
+}
+
+long long solve_lam_elems(const Geometry& g) {
+  const SolveTile tl = solve_layout(g.Ms, g.tw_s, g.g_s, g.dr, g.dc, g.Sl);
+  return (long long)tl.gx * (g.N / g.g_s) * (g.dr * g.dc * g.ds) * tl.ncls;
+}
+
+long long solve_yhat_elems(const Geometry& g) {
+  const SolveTile tl = solve_layout(g.Ms, g.tw_s, g.g_s, g.dr, g.dc, g.Sl);
+  return (long long)tl.gx * (g.N / g.g_s) * tl.ncls;
+}
+
+cudaError_t launch_perm_lam(const Plan& p, const void* lam, void* out) {
+  const Geometry& g = p.hr;
+  const long long total = solve_lam_elems(g);
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  if (p.dtype)
+    k_perm_lam<double><<<blocks, 256, 0, p.stream>>>((const double2*)lam, (double2*)out, g.Ms, g.Mp, g.N, g.tw_s,
+                                                     g.g_s, g.dr, g.dc, g.ds, g.Sl, total);
+  else
+    k_perm_lam<float><<<blocks, 256, 0, p.stream>>>((const float2*)lam, (float2*)out, g.Ms, g.Mp, g.N, g.tw_s,
+                                                    g.g_s, g.dr, g.dc, g.ds, g.Sl, total);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_perm_yhat(const Plan& p, const void* yh, void* out) {
+  const Geometry& g = p.hr;
+  const long long total = solve_yhat_elems(g);
+  const int blocks = (int)((total + 255) / 256 < 4096 ? (total + 255) / 256 : 4096);
+  if (p.dtype)
+    k_perm_yhat<double><<<blocks, 256, 0, p.stream>>>((const double2*)yh, (double2*)out, g.Ms, g.tw_s, g.g_s, g.dr,
+                                                      g.dc, g.Sl, g.Nl, p.lr.Mp, total);
+  else
+    k_perm_yhat<float><<<blocks, 256, 0, p.stream>>>((const float2*)yh, (float2*)out, g.Ms, g.tw_s, g.g_s, g.dr,
+                                                     g.dc, g.Sl, g.Nl, p.lr.Mp, total);
+  return cudaGetLastError();
 }
 
 long long s_pass_blocks(const Geometry& g) {
