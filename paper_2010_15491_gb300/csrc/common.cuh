@@ -56,14 +56,11 @@ struct MAxis {
   FftAxis f;  // transform of length H
 };
 
-// n (or s) axis: length N, aliasing group size dc, LR length Nl.  After the
-// forward n pass frequency k sits at slot (k % Nl)*dc + k / Nl.
+// n (or s) axis: length N, aliasing group size dc, LR length Nl.
 struct LAxis {
   int N, Nl, dc;
   FftAxis f;
 };
-
-__device__ __forceinline__ int nslot(int k, int Nl, int dc) { return (k % Nl) * dc + k / Nl; }
 
 // Location of m-frequency k (0 <= k < M) in the slot layout: the slot and
 // whether the stored value must be conjugated (the value at M - k).  Along a

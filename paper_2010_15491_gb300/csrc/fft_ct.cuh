@@ -23,10 +23,20 @@ template <int N> __host__ __device__ constexpr bool ct_supported() {
   return N == 128 || N == 256 || N == 512;
 }
 
+// Shared-memory position of line element i: with PAD one spare slot follows
+// every 16 elements, which spreads the first stage's stride-R stores over
+// the banks (used by the contiguous-line m pass).
+template <bool PAD> __device__ __forceinline__ int ct_pos(int i) { return PAD ? i + (i >> 4) : i; }
+template <bool PAD> __host__ __device__ constexpr int ct_line_pitch(int n) {
+  // padded length rounded to 4 (mod 16) complex, so that consecutive lines
+  // start 8 banks apart
+  return PAD ? ((n + n / 16 + 1 + 15) / 16) * 16 + 4 : n;
+}
+
 // Stage I of the length-N transform on one line.  FIRST: inputs from ld;
 // LAST: outputs to st; otherwise shared memory in place (barrier between
 // the loads and the stores, and after the stores).
-template <int N, int I, bool FIRST, bool LAST, class Ld, class St>
+template <int N, int I, bool FIRST, bool LAST, bool PAD, class Ld, class St>
 __device__ __forceinline__ void ct_stage(const Ld& ld, const St& st, float2* line, int es, int tl,
                                          const float2* __restrict__ tws, int twstep) {
   constexpr int R = ct_radix(N, I);
@@ -44,7 +54,7 @@ __device__ __forceinline__ void ct_stage(const Ld& ld, const St& st, float2* lin
     for (int r = 0; r < R; ++r) {
       float2 a;
       if constexpr (FIRST) a = ld(j + r * NR);
-      else a = line[(j + r * NR) * es];
+      else a = line[ct_pos<PAD>(j + r * NR) * es];
       if constexpr (NS > 1)
         if (r > 0) a = cmul(a, tws[jm * r * STEP * twstep]);
       v[u * R + r] = a;
@@ -61,7 +71,7 @@ __device__ __forceinline__ void ct_stage(const Ld& ld, const St& st, float2* lin
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       if constexpr (LAST) st(base + r * NS, v[u * R + r]);
-      else line[(base + r * NS) * es] = v[u * R + r];
+      else line[ct_pos<PAD>(base + r * NS) * es] = v[u * R + r];
     }
   }
   if constexpr (!LAST) __syncthreads();
@@ -75,36 +85,36 @@ struct CtNone {
 // Stages I.. of the length-N transform.  G_IN: stage 0 reads through ld
 // (global); G_OUT: the last stage writes through st (global); otherwise the
 // line lives in shared memory.
-template <int N, int I, bool G_IN, bool G_OUT, class Ld, class St>
+template <int N, int I, bool G_IN, bool G_OUT, bool PAD, class Ld, class St>
 __device__ __forceinline__ void ct_run(const Ld& ld, const St& st, float2* line, int es, int tl,
                                        const float2* __restrict__ tws, int twstep) {
   constexpr int NST = ct_nst(N);
   if constexpr (I < NST) {
-    ct_stage<N, I, G_IN && I == 0, G_OUT && I == NST - 1>(ld, st, line, es, tl, tws, twstep);
-    ct_run<N, I + 1, G_IN, G_OUT>(ld, st, line, es, tl, tws, twstep);
+    ct_stage<N, I, G_IN && I == 0, G_OUT && I == NST - 1, PAD>(ld, st, line, es, tl, tws, twstep);
+    ct_run<N, I + 1, G_IN, G_OUT, PAD>(ld, st, line, es, tl, tws, twstep);
   }
 }
 
 // global -> global.  Every load precedes the first barrier and every store
 // follows it, so ld and st may alias.
-template <int N, class Ld, class St>
+template <int N, bool PAD = false, class Ld, class St>
 __device__ __forceinline__ void ct_line_gg(const Ld& ld, const St& st, float2* line, int es, int tl,
                                            const float2* __restrict__ tws, int twstep) {
-  ct_run<N, 0, true, true>(ld, st, line, es, tl, tws, twstep);
+  ct_run<N, 0, true, true, PAD>(ld, st, line, es, tl, tws, twstep);
 }
 
 // global -> shared (natural order, after a barrier)
-template <int N, class Ld>
+template <int N, bool PAD = false, class Ld>
 __device__ __forceinline__ void ct_line_gs(const Ld& ld, float2* line, int es, int tl,
                                            const float2* __restrict__ tws, int twstep) {
-  ct_run<N, 0, true, false>(ld, CtNone{}, line, es, tl, tws, twstep);
+  ct_run<N, 0, true, false, PAD>(ld, CtNone{}, line, es, tl, tws, twstep);
 }
 
 // shared (complete, after a barrier) -> global
-template <int N, class St>
+template <int N, bool PAD = false, class St>
 __device__ __forceinline__ void ct_line_sg(float2* line, const St& st, int es, int tl,
                                            const float2* __restrict__ tws, int twstep) {
-  ct_run<N, 0, false, true>(CtNone{}, st, line, es, tl, tws, twstep);
+  ct_run<N, 0, false, true, PAD>(CtNone{}, st, line, es, tl, tws, twstep);
 }
 
 // Copies the n-entry twiddle table to shared memory (all threads; barrier).

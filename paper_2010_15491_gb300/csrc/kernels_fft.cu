@@ -3,12 +3,11 @@
 // Spectral layout of a real volume x[s][n][m] (sizes M, N, S): complex
 // spec[k_s][n-slot][m-slot] with
 //   m-slot g*dr + p  <->  m-frequency g + p*Ml, g in [0, Ml/2]   (Ml = M/dr)
-//   n-slot (k % Nl)*dc + k / Nl  <->  n-frequency k               (Nl = N/dc)
-//   k_s natural.
+//   n and s natural.
 // Every frequency either is stored or has its conjugate stored (the m axis
 // is real), and the d = dr*dc*ds members of each aliasing class of eq. (8)
-// sit in one dr x dc block of slots on ds planes, so the s pass can solve a
-// class from one shared-memory tile.
+// sit in dr adjacent m-slots of the dc rows j, j+Nl, ... on ds planes, so the
+// s pass can solve a class from one shared-memory tile.
 //
 // Per solve the passes are: real FFT along m (packed half-length complex
 // transform), strided FFT along n, FFT along s fused with the class solve
@@ -53,11 +52,12 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_fwd(const T* __restrict__ in,
       C* tws = sm + L * Hp;  // table of the M = 2H roots
       ct_load_twiddles(tws, twM, 2 * NC);
       tw = tws;
-      ct_line_gs<NC>(ld, sm + l * Hp, 1, tl, tws, 2);
+      ct_line_gs<NC, true>(ld, sm + l * Hp, 1, tl, tws, 2);
     } else {
       fft_line_gs<T, EMAX>(ld, sm + l * Hp, 1, a.f, tl, tpl, twM, 2);
     }
   }
+  auto pos = [](int i) { return NC > 0 ? ct_pos<true>(i) : i; };
   // split the packed transform: X[k] = E[k] + W^k O[k], E/O from Z[k], conj(Z[H-k])
   for (int i = threadIdx.x; i < L * a.Ms; i += blockDim.x) {
     const int l = i / a.Ms, slot = i - l * a.Ms;
@@ -67,8 +67,8 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_fwd(const T* __restrict__ in,
     int k = grp + p * a.Ml;
     const bool cj = k > H;
     if (cj) k = a.M - k;
-    const C zk = sm[l * Hp + (k == H ? 0 : k)];
-    const C zc = conjc(sm[l * Hp + (k == 0 ? 0 : H - k)]);
+    const C zk = sm[l * Hp + pos(k == H ? 0 : k)];
+    const C zc = conjc(sm[l * Hp + pos(k == 0 ? 0 : H - k)]);
     const C e = (zk + zc) * (T)0.5;
     const C o = mul_mi(zk - zc) * (T)0.5;
     const C X = e + cmul(NC > 0 ? tw[k] : __ldg(&twM[k]), o);
@@ -88,16 +88,30 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_inv(const cplx<T>* __restrict
   const int H = NC > 0 ? NC : a.H;
   const int tpl = NC > 0 ? NC / 16 : H / a.f.e;
   const C* tw = twM;
+  C* slots = sm + L * Hp + (NC > 0 ? 2 * NC : 0);  // NC > 0: the CTA's L slot rows, staged
   if constexpr (NC > 0) {
     C* tws = sm + L * Hp;
-    ct_load_twiddles(tws, twM, 2 * NC);
+    // the L rows of Mp complex are contiguous in global memory: 16-byte async copies
+    const long long line0s = (long long)blockIdx.x * L;
+    const long long nrows = (nlines - line0s) < L ? (nlines - line0s) : L;
+    const float* src = reinterpret_cast<const float*>(in + line0s * a.Mp);
+    float* dst = reinterpret_cast<float*>(slots);
+    const int n16 = (int)(nrows * a.Mp / 2);  // Mp even: whole 16-byte chunks
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) {
+      const unsigned dsh = (unsigned)__cvta_generic_to_shared(dst + 4 * i);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dsh), "l"(src + 4 * i) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    for (int i = threadIdx.x; i < 2 * NC; i += blockDim.x) tws[i] = __ldg(&twM[i]);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    __syncthreads();
     tw = tws;
   }
   const long long line0 = (long long)blockIdx.x * L;
   const int l = threadIdx.x / tpl, tl = threadIdx.x - l * tpl;
   const long long gl = line0 + l;
   const bool ok = gl < nlines;
-  const C* row = in + gl * a.Mp;
+  const C* row = NC > 0 ? slots + (long long)l * a.Mp : in + gl * a.Mp;
   // Z[k] = E'[k] + i O'[k] from X[k] and conj(X[H-k]); the inverse runs
   // through the forward engine on conj(Z)
   auto ld = [&](int k) -> C {
@@ -105,9 +119,9 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_inv(const cplx<T>* __restrict
     bool c1, c2;
     const int s1 = mslot_of(k, a.M, a.Ml, a.dr, c1);
     const int s2 = mslot_of(H - k, a.M, a.Ml, a.dr, c2);
-    C xk = __ldg(&row[s1]);
+    C xk = NC > 0 ? row[s1] : __ldg(&row[s1]);
     if (c1) xk = conjc(xk);
-    C xh = __ldg(&row[s2]);
+    C xh = NC > 0 ? row[s2] : __ldg(&row[s2]);
     if (!c2) xh = conjc(xh);  // conj(X[H-k])
     const C e = xk + xh;
     const C o = cmulc(NC > 0 ? tw[k] : __ldg(&twM[k]), xk - xh);  // W^-k (X[k] - conj(X[H-k]))
@@ -117,13 +131,12 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_inv(const cplx<T>* __restrict
   auto st = [&](int j, C r) {
     if (ok) outc[j] = mkc(r.x * scale, -r.y * scale);
   };
-  if constexpr (NC > 0) ct_line_gg<NC>(ld, st, sm + l * Hp, 1, tl, tw, 2);
+  if constexpr (NC > 0) ct_line_gg<NC, true>(ld, st, sm + l * Hp, 1, tl, tw, 2);
   else fft_line_gg<T, EMAX>(ld, st, sm + l * Hp, 1, a.f, tl, tpl, twM, 2);
 }
 
 // ---------------------------------------------------------------------------
-// n pass: tile of TW m-slots x all N rows of one s plane.  Forward reads n in
-// natural order and writes n-slots; inverse reads n-slots, writes natural n.
+// n pass: tile of TW m-slots x all N rows of one s plane.
 // ---------------------------------------------------------------------------
 template <typename T, int EMAX, bool INV, int NC>
 __global__ void __launch_bounds__(256, 2) k_fft_n(cplx<T>* __restrict__ spec, LAxis a, int Ms, int Mp, int TW,
@@ -140,11 +153,11 @@ __global__ void __launch_bounds__(256, 2) k_fft_n(cplx<T>* __restrict__ spec, LA
   C* col = base + t;
   auto ld = [&](int k) -> C {
     if (!ok) return czero<C>();
-    const C v = col[(long long)(INV ? nslot(k, a.Nl, a.dc) : k) * Mp];
+    const C v = col[(long long)k * Mp];
     return INV ? conjc(v) : v;
   };
   auto st = [&](int k, C v) {
-    if (ok) col[(long long)(INV ? k : nslot(k, a.Nl, a.dc)) * Mp] = INV ? conjc(v) : v;
+    if (ok) col[(long long)k * Mp] = INV ? conjc(v) : v;
   };
   if constexpr (NC > 0) {
     C* tws = sm + N * TW;
@@ -212,6 +225,7 @@ __device__ __forceinline__ double solve_tile(cplx<T>* sm, int TW, int G, int a0,
   const T alpha = (T)sv.alpha;
   const T ialpha = (T)(1.0 / sv.alpha);
   double acc = 0.0;
+#pragma unroll 1
   for (int c = tid; c < ncls; c += nthr) {
     const int gm = c % tl.GMc;
     const int rest = c / tl.GMc;
@@ -232,6 +246,74 @@ __device__ __forceinline__ double solve_tile(cplx<T>* sm, int TW, int G, int a0,
     }
     const C Yc = __ldg(&yhc[c]);
     const bool dc_cls = (MODE == S_ADMM) && g == 0 && jl == 0 && is == 0;
+    if constexpr (DR_ > 0 && MODE == S_ADMM) {
+      // compile-time class shape: Lambda in registers, B parked in the tile,
+      // the dr + dc + ds symbol values instead of d weights
+      constexpr int D = DR_ * DC_ * DS_;
+      T sMv[DR_], sNv[DC_], sSv[DS_];
+#pragma unroll
+      for (int i = 0; i < DR_; ++i) sMv[i] = __ldg(&symM[g + i * sv.Ml]);
+#pragma unroll
+      for (int i = 0; i < DC_; ++i) sNv[i] = __ldg(&symN[jl + i * sv.Nl]);
+#pragma unroll
+      for (int i = 0; i < DS_; ++i) sSv[i] = __ldg(&symS[is + i * sv.Sl]);
+      const int sbase = (is * G + gn * DC_) * TW + gm * DR_;
+      const int splane = sv.Sl * G * TW;
+      auto sidx = [&](int q) { return sbase + (q / (DR_ * DC_)) * splane + ((q / DR_) % DC_) * TW + q % DR_; };
+      auto wgt = [&](int q) -> T {
+        if (dc_cls && q == 0) return (T)0;
+        return (T)1 / (alpha * (sMv[q % DR_] + sNv[(q / DR_) % DC_] + sSv[q / (DR_ * DC_)]));
+      };
+      C av[D];
+      int qs = 0;
+      T best = (T)-1;
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const C a_ = __ldg(&lamc[(long long)q * ncls + c]);
+        av[q] = a_;
+        const int si = sidx(q);
+        sm[si] = cmulc(a_, Yc) + sm[si] * alpha;  // B = conj(Lambda) Y + mu F Theta
+        const T key = (dc_cls && q == 0) ? Lim<T>::big : norm2(a_) * wgt(q);
+        if (key > best) { best = key; qs = q; }
+      }
+      T Sp = 0, ws = 0;
+      C Tp = czero<C>(), as = czero<C>(), bs = czero<C>();
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const C B = sm[sidx(q)];
+        const T w = wgt(q);
+        if (q == qs) {
+          as = av[q]; bs = B; ws = w;
+        } else {
+          Sp += norm2(av[q]) * w;
+          Tp = Tp + cmul(av[q], B) * w;
+        }
+      }
+      C Xs, ratio;
+      if (dc_cls) {
+        const T inv = (T)1 / norm2(as);
+        Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * inv;
+        ratio = cmul(bs, as) * inv;
+      } else {
+        const T iD = (T)1 / (dd + Sp + norm2(as) * ws);
+        Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * (ws * iD);
+        ratio = (Tp + cmul(as, bs) * ws) * iD;
+      }
+      C tsum = czero<C>();
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        const int si = sidx(q);
+        const C X = (q == qs) ? Xs : (sm[si] - cmulc(av[q], ratio)) * wgt(q);
+        sm[si] = conjc(X);
+        if (STATS) tsum = tsum + cmul(av[q], X);
+      }
+      if (STATS) {
+        const C R = Yc - tsum * (T)(1.0 / D);
+        const double wg = (g == 0 || 2 * g == sv.Ml) ? 1.0 : 2.0;
+        acc += wg * (double)norm2(R);
+      }
+      continue;
+    }
     C av[DMAX], bv[DMAX];
     T wv[DMAX];
     int si[DMAX];
@@ -313,8 +395,8 @@ __device__ __forceinline__ double solve_tile(cplx<T>* sm, int TW, int G, int a0,
 }
 
 template <typename T, int EMAX, int MODE, bool STATS, int NC, int DR_, int DC_, int DS_>
-__global__ void __launch_bounds__(512) k_fft_s(cplx<T>* __restrict__ spec, LAxis a, int Ms, int Mp, int Nn, int TW, int G, SolveArgs sv,
-                        const cplx<T>* __restrict__ twS) {
+__global__ void __launch_bounds__(NC > 0 ? 256 : 512, NC > 0 ? 3 : 1) k_fft_s(cplx<T>* __restrict__ spec, LAxis a, int Ms, int Mp, int Nn, int TW, int G, SolveArgs sv,
+                        const cplx<T>* __restrict__ twS, int ndc, int nNl) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
@@ -324,11 +406,12 @@ __global__ void __launch_bounds__(512) k_fft_s(cplx<T>* __restrict__ spec, LAxis
   const int nthr = blockDim.x, tid = threadIdx.x;
   const int rowlen = G * TW;
   const long long plane = (long long)Nn * Mp;
-  C* gbase = spec + (long long)b0 * Mp + a0;
   const int t = tid % TW, gi = (tid / TW) % G, tl = tid / (TW * G), tpl = NC > 0 ? NC / 16 : S / a.f.e;
   (void)tpl;
   const bool ok = t < tv;
-  C* col = gbase + (long long)gi * Mp + t;
+  // tile row gi = gn * dc + pn holds n = b0 / dc + gn + pn * Nl (dc, Nl of the n axis)
+  const int nrow = b0 / ndc + gi / ndc + (gi % ndc) * nNl;
+  C* col = spec + (long long)nrow * Mp + a0 + t;
   C* line = sm + gi * TW + t;
   C* tws = sm + S * rowlen;
   if constexpr (NC > 0) ct_load_twiddles(tws, twS, NC);
@@ -413,7 +496,10 @@ static cudaError_t rfft_fwd_k(const Plan& p, const Geometry& g, const void* in, 
   int L, Hp, threads;
   size_t smem;
   m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
-  if (NC > 0) smem += (size_t)2 * NC * sizeof(cplx<T>);
+  if (NC > 0) {
+    Hp = ct_line_pitch<true>(NC);
+    smem = (size_t)(L * Hp + 2 * NC) * sizeof(cplx<T>);
+  }
   const long long nlines = (long long)g.S * g.N;
   const unsigned blocks = (unsigned)((nlines + L - 1) / L);
   MAxis a = maxis(g);
@@ -430,7 +516,10 @@ static cudaError_t rfft_inv_k(const Plan& p, const Geometry& g, const void* in, 
   int L, Hp, threads;
   size_t smem;
   m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
-  if (NC > 0) smem += (size_t)2 * NC * sizeof(cplx<T>);
+  if (NC > 0) {
+    Hp = ct_line_pitch<true>(NC);
+    smem = (size_t)(L * Hp + 2 * NC + L * g.Mp) * sizeof(cplx<T>);
+  }
   const long long nlines = (long long)g.S * g.N;
   const unsigned blocks = (unsigned)((nlines + L - 1) / L);
   MAxis a = maxis(g);
@@ -500,7 +589,7 @@ static cudaError_t fft_s_k(const Plan& p, const Geometry& g, void* spec, const v
   cudaError_t e;
   if ((e = allow_smem(k_fft_s<T, EMAX, MODE, STATS, NC, DR_, DC_, DS_>, smem)) != cudaSuccess) return e;
   k_fft_s<T, EMAX, MODE, STATS, NC, DR_, DC_, DS_><<<grid, TW * G * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, g.N, TW,
-                                                                          G, sv, (const cplx<T>*)tw);
+                                                                          G, sv, (const cplx<T>*)tw, g.dc, g.Nl);
   return cudaGetLastError();
 }
 
@@ -514,7 +603,7 @@ static cudaError_t fft_s_e(const Plan& p, const Geometry& g, void* spec, const v
     case S_TIK_USER: return fft_s_k<T, EMAX, S_TIK_USER, false, 0>(p, g, spec, tw, sv);
     case S_ADMM:
       if constexpr (sizeof(T) == 4 && EMAX == 16) {
-        if (ct_len<T>(g.S, g.fs) == 256) {
+        if (ct_len<T>(g.S, g.fs) == 256 && g.tw_s * g.g_s * (256 / 16) <= 256) {
           if (g.dr == 2 && g.dc == 2 && g.ds == 2)
             return stats ? fft_s_k<T, EMAX, S_ADMM, true, 256, 2, 2, 2>(p, g, spec, tw, sv)
                          : fft_s_k<T, EMAX, S_ADMM, false, 256, 2, 2, 2>(p, g, spec, tw, sv);
@@ -593,7 +682,7 @@ __global__ void k_perm_lam(const cplx<T>* __restrict__ lam, cplx<T>* __restrict_
     const int pm = q % dr, pn = (q / dr) % dc, ps = q / (dr * dc);
     cplx<T> v = czero<cplx<T>>();
     if (a0 / dr + gm < tl.Gm)
-      v = lam[((long long)(is + ps * Sl) * N + b0 + gn * dc + pn) * Mp + a0 + gm * dr + pm];
+      v = lam[((long long)(is + ps * Sl) * N + b0 / dc + gn + pn * (N / dc)) * Mp + a0 + gm * dr + pm];
     out[idx] = v;
   }
 }

@@ -644,7 +644,7 @@ __global__ void k_export_half(const cplx<T>* __restrict__ spec, cplx<T>* __restr
     const int slot = mslot_of(km, M, Ml, dr, cj);
     const int kn2 = cj ? (N - kn) % N : kn;
     const int ks2 = cj ? (S - ks) % S : ks;
-    const cplx<T> v = spec[((long long)ks2 * N + nslot(kn2, Nl, dc)) * Mp + slot];
+    const cplx<T> v = spec[((long long)ks2 * N + kn2) * Mp + slot];
     out[i] = cj ? conjc(v) : v;
   }
 }
