@@ -175,6 +175,7 @@ static void free_plan(Plan& p) {
                   p.theta, p.dbuf[0], p.dbuf[1], p.psi, p.xh, p.yh, p.partial, p.partial_s, p.result, p.hist};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  if (p.iter_graph) cudaGraphExecDestroy(p.iter_graph);
   if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
   for (int i = 0; i < 2 * p.prof_cap; ++i) cudaEventDestroy(p.prof_ev[i]);
   delete[] p.prof_ev;
@@ -240,6 +241,57 @@ static int xstep_core(Plan& p, const void* theta, double mu, void* x, bool stats
   SolveArgs sv = solve_args(p, 0, mu);
   LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_ADMM, stats, &sv));
   return hr_inverse_partial(p, x);
+}
+
+static int sync_plan(Plan& p);
+
+// One ADMM iteration without statistics: x-step from Theta, then the TV step
+// (u, d_in -> d_out, next Theta).
+static int admm_iteration(Plan& p, void* x, const void* din, void* dout, double thr, double rho);
+
+// Runs n >= 2 iterations (n even) through the cached two-iteration graph,
+// capturing it first when the buffers or parameters changed.
+static int admm_iterations_graph(Plan& p, void* x, void* d0, void* d1, double thr, double rho, int n) {
+  if (!p.iter_graph || p.ig_x != x || p.ig_d0 != d0 || p.ig_d1 != d1 || p.ig_thr != thr || p.ig_rho != rho) {
+    if (p.iter_graph) {
+      cudaGraphExecDestroy(p.iter_graph);
+      p.iter_graph = nullptr;
+    }
+    long long before[8];
+    for (int k = 0; k < 8; ++k) before[k] = p.launches[k];
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(p.stream, cudaStreamCaptureModeThreadLocal));
+    int rc = admm_iteration(p, x, d0, d1, thr, rho);
+    if (rc == SR3D_OK) rc = admm_iteration(p, x, d1, d0, thr, rho);
+    cudaError_t ec = cudaStreamEndCapture(p.stream, &graph);
+    if (rc != SR3D_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return fail(SR3D_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+    ec = cudaGraphInstantiate(&p.iter_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) {
+      p.iter_graph = nullptr;
+      return fail(SR3D_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+    }
+    for (int k = 0; k < 8; ++k) {
+      p.ig_launches[k] = p.launches[k] - before[k];
+      p.launches[k] = before[k];
+    }
+    p.ig_x = x; p.ig_d0 = d0; p.ig_d1 = d1; p.ig_thr = thr; p.ig_rho = rho;
+  }
+  for (int i = 0; i + 2 <= n; i += 2) {
+    CK(cudaGraphLaunch(p.iter_graph, p.stream));
+    for (int k = 0; k < 8; ++k) p.launches[k] += p.ig_launches[k];
+  }
+  return SR3D_OK;
+}
+
+static int admm_iteration(Plan& p, void* x, const void* din, void* dout, double thr, double rho) {
+  TRY(xstep_core(p, p.theta, rho, x, false));
+  LAUNCH(SR3D_K_TV, launch_tv(p, x, din, dout, p.theta, p.psi, thr, 0, false));
+  return SR3D_OK;
 }
 
 static int sync_plan(Plan& p) {
@@ -527,7 +579,25 @@ int sr3d_admm_tv(sr3d_plan_t plan, const void* y, void* x, void* d_dev, double l
   int evals = 0, it = 0;
   bool converged = false;
   double res[16] = {0};
-  for (int k = 1; k <= max_iters; ++k) {
+  if (!want_stats && !p.prof_on && p.stream != nullptr && max_iters >= 3) {
+    // fixed iterations: the first runs eagerly (every kernel is loaded and
+    // configured before any capture), then the two-iteration graph is
+    // replayed; an odd last iteration runs eagerly
+    auto eager = [&]() -> int {
+      TRY(admm_iteration(p, x, dcur, dnext, thr, rho));
+      void* t = dcur;
+      dcur = dnext;
+      dnext = t;
+      ++it;
+      return SR3D_OK;
+    };
+    TRY(eager());
+    const int pairs = (max_iters - it) / 2;
+    TRY(admm_iterations_graph(p, x, dcur, dnext, thr, rho, 2 * pairs));
+    it += 2 * pairs;
+    if (it < max_iters) TRY(eager());
+  }
+  for (int k = it + 1; k <= max_iters; ++k) {
     const bool eval_now = want_stats && ((every > 0 && k % every == 0) || k == max_iters);
     const bool stats_now = want_stats && (eval_now || (every > 0 && (k + 1) % every == 0) || k + 1 == max_iters);
     TRY(xstep_core(p, p.theta, rho, x, eval_now));

@@ -87,6 +87,14 @@ struct Plan {
   int* prof_kind = nullptr;
   double prof_ms[8] = {0};
   long long launches[8] = {0};
+  // CUDA graph of two ADMM iterations (x-step + TV step twice, dual buffers
+  // swapped), replayed by sr3d_admm_tv for iterations without statistics
+  cudaGraphExec_t iter_graph = nullptr;
+  const void* ig_x = nullptr;
+  const void* ig_d0 = nullptr;
+  const void* ig_d1 = nullptr;
+  double ig_thr = 0, ig_rho = 0;
+  long long ig_launches[8] = {0};
 };
 
 // ---- launchers (kernels_fft.cu) ----

@@ -228,3 +228,20 @@ def test_headline_size_against_oracle(lib, tag):
     plan.admm_tv(T(y, "f32"), xg, W.lam, W.mu, 2, tau_init=W.tau)
     assert rel_l2(H(xg), ref["x"], tag("admm2")) < TOL["f32"]
     plan.close()
+
+
+def test_graph_replay_across_calls(lib, tag):
+    """Fixed-iteration solves replay a captured two-iteration graph; a change of
+    buffers or parameters re-captures it.  Every call must still match the oracle."""
+    import torch
+    dims, dec = (128, 64, 32), (2, 2, 2)
+    psf, xt, y = make_problem(dims, dec, seed=24)
+    plan = lib.Plan(dims, dec, psf, "f32")
+    yd = T(y, "f32")
+    x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
+    for call, (lam, mu, iters) in enumerate([(1e-3, 1e-2, 7), (1e-3, 1e-2, 8), (3e-3, 2e-2, 9)]):
+        x = plan.empty_hr() if call != 1 else x  # call 1 reuses the buffer of call 0
+        plan.admm_tv(yd, x, lam, mu, iters, tau_init=1e-2)
+        ref = O.admm_tv(y, psf, dec, lam, mu, iters, x0)["x"]
+        assert rel_l2(H(x), ref, tag(f"call{call}")) < TOL["f32"]
+    plan.close()
