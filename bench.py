@@ -170,6 +170,22 @@ def run_reference(args, w, rank):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(v: float, world: int, device=None) -> float:
+    """The largest of one float per rank (the timing rule: max over ranks)."""
+    if world <= 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Units processed by all ranks (weak scaling: each rank does the same work) per second."""
+    return world * units_per_rank / seconds
+
+
 def run_ours(args, w, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -201,7 +217,7 @@ def run_ours(args, w, rank, world, local_rank):
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, "cuda")
     launches = sum(n for _, n in plan.profile_read().values())
     # the same steps again with CUDA events around every launch (on the plan's
     # stream): per-kernel average durations for the roofline
@@ -209,12 +225,8 @@ def run_ours(args, w, rank, world, local_rank):
     for _ in range(args.steps):
         step()
     prof = plan.profile_read()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     ms_step = ms / args.steps
-    value = world * w.voxels * w.iters * args.steps / (ms / 1e3)
+    value = whole_job_rate(w.voxels * w.iters * args.steps, world, ms / 1e3)
 
     # end to end through the public host-buffer entry point: pinned host y in,
     # x out, copies inside the timed region
@@ -227,12 +239,8 @@ def run_ours(args, w, rank, world, local_rank):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         plan.admm_tv_host(yh, xh, w.lam, w.mu, w.iters, tau_init=w.tau)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * w.voxels * w.iters * args.steps / e2e_s, "unit": UNIT,
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, "cuda")
+    e2e = {"value": whole_job_rate(w.voxels * w.iters * args.steps, world, e2e_s), "unit": UNIT,
            "h2d_bytes_per_step": yh.numel() * yh.element_size(),
            "d2h_bytes_per_step": xh.numel() * xh.element_size()}
 
