@@ -131,6 +131,18 @@ int sr3d_admm_tv_host(sr3d_plan_t plan, const void* y_host, void* x_host,
                       double lambda, double rho, int max_iters, double tol, double tau_init,
                       sr3d_stats* stats);
 
+/* Batched ADMM-TV over n volumes of uneven size and decimation (one plan
+ * per volume; plans distinct and on non-default streams): for volume i,
+ * sr3d_admm_tv(plans[i], y[i], x[i], NULL, lambda[i], rho[i], iters, 0,
+ * tau_init[i], NULL).  The iterations of all volumes run as one CUDA graph
+ * with one independent chain per volume, so small volumes execute
+ * concurrently; the graph is cached and replayed while plans, buffers and
+ * parameters repeat.  Serialised across host threads.  Not in the paper
+ * (a throughput mode for many volumes).  Errors: INVALID_ARG, SINGULAR,
+ * CUDA. */
+int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const* y, void* const* x,
+                         const double* lambda, const double* rho, const double* tau_init, int iters);
+
 /* Message of the last failure on the calling thread ("" if none). */
 const char* sr3d_last_error(void);
 

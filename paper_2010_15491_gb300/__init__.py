@@ -31,7 +31,7 @@ XBAR_NEAREST = ctypes.c_void_p(1)
 EXPORTED = [
     "sr3d_plan", "sr3d_destroy", "sr3d_forward", "sr3d_tikhonov", "sr3d_admm_tv", "sr3d_admm_tv_host",
     "sr3d_last_error", "sr3d_get_otf", "sr3d_fft3", "sr3d_xstep", "sr3d_tv_step", "sr3d_plan_info",
-    "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc",
+    "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc", "sr3d_admm_tv_batched",
 ]
 KINDS = ["tv", "rfft_m_fwd", "fft_n_fwd", "fft_s", "fft_n_inv", "rfft_m_inv", "other", "setup"]
 
@@ -87,6 +87,8 @@ def load() -> ctypes.CDLL:
         "sr3d_profile": (i, [vp, i]),
         "sr3d_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "sr3d_tikhonov_noalloc": (i, [ctypes.POINTER(Desc), vp, vp, d, vp]),
+        "sr3d_admm_tv_batched": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                     ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d), i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -302,3 +304,18 @@ def tikhonov_noalloc(dims, dec, psf, y, tau: float, x, xbar=None, dtype: str = "
     _check(L.sr3d_tikhonov_noalloc(ctypes.byref(desc), _ptr(y, td, (s // ds, n // dc, m // dr)), xb, float(tau),
                                    _ptr(x, td, (s, n, m))))
     return x
+
+
+def admm_tv_batched(plans, ys, xs, lams, rhos, taus, iters: int):
+    """sr3d_admm_tv_batched: ADMM-TV on many volumes (one plan each, each plan
+    created with its own stream), iterations of all volumes in one CUDA graph."""
+    n = len(plans)
+    if not (len(ys) == len(xs) == len(lams) == len(rhos) == len(taus) == n):
+        raise ValueError("one y, x, lambda, rho and tau per plan")
+    vp = ctypes.c_void_p
+    P = (vp * n)(*[p._h.value for p in plans])
+    Y = (vp * n)(*[p._lr(t) for p, t in zip(plans, ys)])
+    X = (vp * n)(*[p._hr(t) for p, t in zip(plans, xs)])
+    dd = ctypes.c_double * n
+    _check(load().sr3d_admm_tv_batched(n, P, Y, X, dd(*lams), dd(*rhos), dd(*taus), int(iters)))
+    return xs

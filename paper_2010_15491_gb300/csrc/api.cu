@@ -666,6 +666,158 @@ int sr3d_admm_tv_host(sr3d_plan_t plan, const void* y_host, void* x_host, double
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Batched solve of many volumes of uneven size and decimation.
+//
+// Every volume keeps its own plan and stream.  The per-volume set-up (LR
+// spectrum, Tikhonov start, initial Theta) is launched on the plans' streams;
+// the iterations run as one CUDA graph that forks from a capture stream into
+// one chain per volume (two ADMM iterations each) and joins back, replayed
+// iters/2 times.  Independent chains run concurrently, so many small volumes
+// fill the GPU together.  The graph is cached for repeated calls with the same
+// plans, buffers and parameters.
+// ---------------------------------------------------------------------------
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> key_ptr;
+  std::vector<double> key_val;
+  std::vector<cudaEvent_t> ev;  // fork/join events
+  cudaStream_t main = nullptr;
+  long long launches[8] = {0};
+};
+static std::mutex g_batch_mu;
+static BatchGraph g_batch;
+
+static int batch_events(size_t n) {
+  while (g_batch.ev.size() < n + 1) {
+    cudaEvent_t e;
+    CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    g_batch.ev.push_back(e);
+  }
+  if (!g_batch.main) CK(cudaStreamCreateWithFlags(&g_batch.main, cudaStreamNonBlocking));
+  return SR3D_OK;
+}
+
+extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const* y, void* const* x,
+                                    const double* lambda, const double* rho, const double* tau_init, int iters) {
+  if (n <= 0 || !plans || !y || !x || !lambda || !rho || !tau_init || iters < 0)
+    return fail(SR3D_ERR_INVALID_ARG, "NULL argument or non-positive count");
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !y[i] || !x[i]) return fail(SR3D_ERR_INVALID_ARG, "NULL plan or buffer %d", i);
+    if (!(rho[i] > 0) || !(lambda[i] >= 0)) return fail(SR3D_ERR_INVALID_ARG, "volume %d: need rho > 0, lambda >= 0", i);
+    if (plans[i]->p.psf_sum == 0.0) return fail(SR3D_ERR_SINGULAR, "volume %d: PSF taps sum to zero", i);
+    if (plans[i]->p.stream == nullptr) return fail(SR3D_ERR_INVALID_ARG, "volume %d: plan on the legacy stream", i);
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return fail(SR3D_ERR_INVALID_ARG, "plan %d repeated", i);
+  }
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  TRY(batch_events((size_t)n));
+  std::vector<void*> dcur(n), dnext(n);
+  // set-up on every plan's stream, after whatever the stream holds
+  for (int i = 0; i < n; ++i) {
+    Plan& p = plans[i]->p;
+    TRY(ensure_admm_buffers(p, false));
+    dcur[i] = p.dbuf[0];
+    dnext[i] = p.dbuf[1];
+    p.kind_override = SR3D_K_SETUP;
+    struct Reset { Plan& p; ~Reset() { p.kind_override = -1; } } reset{p};
+    TRY(lr_spectrum(p, y[i]));
+    if (tau_init[i] > 0) TRY(tikhonov_core(p, SR3D_XBAR_NEAREST, tau_init[i], x[i]));
+    CK(cudaMemsetAsync(dcur[i], 0, (size_t)3 * p.hr.V() * p.esz, p.stream));
+    LAUNCH(SR3D_K_TV, launch_tv(p, x[i], dcur[i], nullptr, p.theta, p.psi, lambda[i] / rho[i], 1, false));
+  }
+  auto eager_iteration = [&]() -> int {
+    for (int i = 0; i < n; ++i) {
+      Plan& p = plans[i]->p;
+      TRY(admm_iteration(p, x[i], dcur[i], dnext[i], lambda[i] / rho[i], rho[i]));
+      std::swap(dcur[i], dnext[i]);
+    }
+    return SR3D_OK;
+  };
+  int it = 0;
+  // the first iteration runs eagerly (kernels loaded before any capture)
+  if (iters > 0) {
+    TRY(eager_iteration());
+    it = 1;
+  }
+  bool profiling = false;
+  for (int i = 0; i < n; ++i) profiling |= plans[i]->p.prof_on;
+  const int pairs = profiling ? 0 : (iters - it) / 2;  // per-launch events are not captured
+  if (pairs > 0) {
+    std::vector<const void*> kp;
+    std::vector<double> kv;
+    for (int i = 0; i < n; ++i) {
+      kp.push_back(plans[i]);
+      kp.push_back(x[i]);
+      kp.push_back(dcur[i]);
+      kv.push_back(lambda[i]);
+      kv.push_back(rho[i]);
+    }
+    if (!g_batch.exec || kp != g_batch.key_ptr || kv != g_batch.key_val) {
+      if (g_batch.exec) {
+        cudaGraphExecDestroy(g_batch.exec);
+        g_batch.exec = nullptr;
+      }
+      std::vector<long long> before(8 * (size_t)n);
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 8; ++k) before[8 * i + k] = plans[i]->p.launches[k];
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(g_batch.main, cudaStreamCaptureModeThreadLocal));
+      int rc = SR3D_OK;
+      cudaError_t ec = cudaEventRecord(g_batch.ev[n], g_batch.main);
+      for (int i = 0; i < n && rc == SR3D_OK && ec == cudaSuccess; ++i) {
+        Plan& p = plans[i]->p;
+        ec = cudaStreamWaitEvent(p.stream, g_batch.ev[n], 0);
+        if (ec != cudaSuccess) break;
+        rc = admm_iteration(p, x[i], dcur[i], dnext[i], lambda[i] / rho[i], rho[i]);
+        if (rc == SR3D_OK) rc = admm_iteration(p, x[i], dnext[i], dcur[i], lambda[i] / rho[i], rho[i]);
+        if (rc == SR3D_OK) ec = cudaEventRecord(g_batch.ev[i], p.stream);
+        if (ec == cudaSuccess && rc == SR3D_OK) ec = cudaStreamWaitEvent(g_batch.main, g_batch.ev[i], 0);
+      }
+      cudaError_t ee = cudaStreamEndCapture(g_batch.main, &graph);
+      if (rc != SR3D_OK || ec != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != SR3D_OK) return rc;
+        return fail(SR3D_ERR_CUDA, "batched graph capture: %s",
+                    cudaGetErrorString(ec != cudaSuccess ? ec : ee));
+      }
+      ee = cudaGraphInstantiate(&g_batch.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ee != cudaSuccess) {
+        g_batch.exec = nullptr;
+        return fail(SR3D_ERR_CUDA, "batched graph instantiate: %s", cudaGetErrorString(ee));
+      }
+      for (int k = 0; k < 8; ++k) g_batch.launches[k] = 0;
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 8; ++k) {
+          g_batch.launches[k] += plans[i]->p.launches[k] - before[8 * i + k];
+          plans[i]->p.launches[k] = before[8 * i + k];
+        }
+      g_batch.key_ptr = kp;
+      g_batch.key_val = kv;
+    }
+    // the graph starts after every plan's queued work
+    for (int i = 0; i < n; ++i) {
+      CK(cudaEventRecord(g_batch.ev[i], plans[i]->p.stream));
+      CK(cudaStreamWaitEvent(g_batch.main, g_batch.ev[i], 0));
+    }
+    for (int r = 0; r < pairs; ++r) {
+      CK(cudaGraphLaunch(g_batch.exec, g_batch.main));
+      for (int k = 0; k < 8; ++k) plans[0]->p.launches[k] += g_batch.launches[k];
+    }
+    // later work on the plans' streams starts after the graph
+    CK(cudaEventRecord(g_batch.ev[n], g_batch.main));
+    for (int i = 0; i < n; ++i) CK(cudaStreamWaitEvent(plans[i]->p.stream, g_batch.ev[n], 0));
+    it += 2 * pairs;
+  }
+  while (it < iters) {
+    TRY(eager_iteration());
+    ++it;
+  }
+  for (int i = 0; i < n; ++i) TRY(sync_plan(plans[i]->p));
+  return SR3D_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Allocation-free Tikhonov solve.
 //
 // For callers that must not allocate device memory once they are running:
