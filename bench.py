@@ -195,6 +195,7 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.Stream()
     plan = sr3d.Plan(w.dims, w.dec, w.psf(), "f32", stream=stream)
+    plan.autotune()
     with torch.cuda.stream(stream):
         y = make_inputs(w, plan, torch)
         x = plan.empty_hr()
@@ -289,6 +290,7 @@ def run_batch(args, rank, world, local_rank):
     for w in ws:
         st = torch.cuda.Stream()
         p = sr3d.Plan(w.dims, w.dec, w.psf(), "f32", stream=st)
+        p.autotune()
         with torch.cuda.stream(st):
             ys.append(make_inputs(w, p, torch))
             xs.append(p.empty_hr())

@@ -168,6 +168,14 @@ int sr3d_xstep(sr3d_plan_t plan, const void* y_dev, const void* theta_dev, doubl
 int sr3d_tv_step(sr3d_plan_t plan, const void* x_dev, const void* d_in_dev, void* d_out_dev,
                  double lambda, double rho, void* theta_out_dev);
 
+/* Autotuner: times candidate tile schedules of the n pass, of the s pass with
+ * its class solve, and of the TV kernel (reps launches each) on the plan's
+ * own buffers, keeps the fastest and caches the choice per geometry (sizes,
+ * decimation, dtype) for the process; a later plan of the same geometry only
+ * applies the cached choice.  Results are unchanged (the schedules only
+ * split the same work differently).  Errors: INVALID_ARG, CUDA, OOM. */
+int sr3d_autotune(sr3d_plan_t plan, int reps);
+
 /* Per-kernel accounting.  Kernel kinds: SR3D_K_TV (fused u/d/Theta step),
  * SR3D_K_RFFT_FWD / SR3D_K_RFFT_INV (real FFT along m), SR3D_K_FFTN_FWD /
  * SR3D_K_FFTN_INV (FFT along n), SR3D_K_FFTS (FFT along s, with the class

@@ -31,7 +31,7 @@ XBAR_NEAREST = ctypes.c_void_p(1)
 EXPORTED = [
     "sr3d_plan", "sr3d_destroy", "sr3d_forward", "sr3d_tikhonov", "sr3d_admm_tv", "sr3d_admm_tv_host",
     "sr3d_last_error", "sr3d_get_otf", "sr3d_fft3", "sr3d_xstep", "sr3d_tv_step", "sr3d_plan_info",
-    "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc", "sr3d_admm_tv_batched",
+    "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc", "sr3d_admm_tv_batched", "sr3d_autotune",
 ]
 KINDS = ["tv", "rfft_m_fwd", "fft_n_fwd", "fft_s", "fft_n_inv", "rfft_m_inv", "other", "setup"]
 
@@ -87,6 +87,7 @@ def load() -> ctypes.CDLL:
         "sr3d_profile": (i, [vp, i]),
         "sr3d_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "sr3d_tikhonov_noalloc": (i, [ctypes.POINTER(Desc), vp, vp, d, vp]),
+        "sr3d_autotune": (i, [vp, i]),
         "sr3d_admm_tv_batched": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d), i]),
     }
@@ -170,6 +171,10 @@ class Plan:
         out = dict(zip(keys, list(sizes)))
         out["bytes"] = b.value
         return out
+
+    def autotune(self, reps: int = 3):
+        """Times candidate tile schedules and keeps the fastest (cached per geometry)."""
+        _check(load().sr3d_autotune(self._h, int(reps)))
 
     def profile(self, on: bool = True):
         """Resets the per-kernel accounting; with on=True also times every launch."""

@@ -7,7 +7,10 @@
 #include <string.h>
 
 #include <cmath>
+#include <functional>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -376,8 +379,10 @@ int sr3d_plan(sr3d_plan_t* out, const sr3d_desc* d) {
     TRY(dmalloc(p, &p.lam, (size_t)g.spec_elems() * csz));
     TRY(dmalloc(p, &p.spec, (size_t)g.spec_elems() * csz));
     TRY(dmalloc(p, &p.yhat, (size_t)l.spec_elems() * csz));
-    TRY(dmalloc(p, &p.lam_solve, (size_t)solve_lam_elems(g) * csz));
-    TRY(dmalloc(p, &p.yhat_solve, (size_t)solve_yhat_elems(g) * csz));
+    p.lam_solve_cap = solve_lam_elems(g);
+    p.yhat_solve_cap = solve_yhat_elems(g);
+    TRY(dmalloc(p, &p.lam_solve, (size_t)p.lam_solve_cap * csz));
+    TRY(dmalloc(p, &p.yhat_solve, (size_t)p.yhat_solve_cap * csz));
     TRY(dmalloc(p, &p.theta, (size_t)g.V() * p.esz));
     p.n_tv_blocks = tv_blocks(g);
     p.n_s_blocks = s_pass_blocks(g);
@@ -666,6 +671,150 @@ int sr3d_admm_tv_host(sr3d_plan_t plan, const void* y_host, void* x_host, double
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Autotuner: times candidate tile schedules of the n pass, the s pass (with
+// its class solve) and the TV kernel on the plan's own buffers, keeps the
+// fastest and caches the choice per geometry for the process.
+// ---------------------------------------------------------------------------
+using TuneKey = std::tuple<int, int, int, int, int, int, int>;
+struct TuneVal { int tw_n, tw_s, ts_tv; };
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneVal> g_tune;
+
+static int time_ms(Plan& p, int reps, float* ms, const std::function<int()>& f) {
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  int rc = f();  // warm-up (also loads the kernel)
+  if (rc == SR3D_OK && cudaEventRecord(a, p.stream) == cudaSuccess) {
+    for (int i = 0; i < reps && rc == SR3D_OK; ++i) rc = f();
+    cudaEventRecord(b, p.stream);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(ms, a, b);
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return rc;
+}
+
+static int realloc_partials(Plan& p) {
+  const long long ns = s_pass_blocks(p.hr);
+  if (ns > p.n_s_blocks) {
+    cudaFree(p.partial_s);
+    p.partial_s = nullptr;
+    TRY(dmalloc(p, (void**)&p.partial_s, (size_t)ns * sizeof(double)));
+    p.n_s_blocks = ns;
+  }
+  return SR3D_OK;
+}
+
+extern "C" int sr3d_autotune(sr3d_plan_t plan, int reps) {
+  if (!plan) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  Geometry& g = p.hr;
+  const size_t csz = 2 * p.esz;
+  const TuneKey key{g.M, g.N, g.S, g.dr, g.dc, g.ds, p.dtype};
+  TuneVal best{g.tw_n, g.tw_s, g.ts_tv};
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      best = it->second;
+      cached = true;
+    }
+  }
+  if (reps < 1) reps = 3;
+  const bool prof = p.prof_on;
+  p.prof_on = false;
+  struct Restore { Plan& p; bool on; ~Restore() { p.prof_on = on; } } restore{p, prof};
+  if (!cached) {
+    TRY(ensure_admm_buffers(p, false));
+    CK(cudaMemsetAsync(p.spec, 0, (size_t)g.spec_elems() * csz, p.stream));
+    CK(cudaMemsetAsync(p.yhat_solve, 0, (size_t)solve_yhat_elems(g) * csz, p.stream));
+    CK(cudaMemsetAsync(p.dbuf[0], 0, (size_t)3 * g.V() * p.esz, p.stream));
+    CK(cudaMemsetAsync(p.theta, 0, (size_t)g.V() * p.esz, p.stream));
+    // n pass tile width
+    {
+      const int tpl = g.N / g.fn.e;
+      const int cap = (g.Ms + 1) & ~1;
+      float bt = 1e30f;
+      for (int tw : {g.tw_n / 2, g.tw_n, g.tw_n * 2, g.tw_n * 4}) {
+        if (tw < 1 || tw > 64 || tw > cap || tw * tpl > 256 || (size_t)tw * g.N * csz > 96 * 1024) continue;
+        if (tw > 1 && tw % 2) continue;
+        g.tw_n = tw;
+        float ms = 0;
+        TRY(time_ms(p, reps, &ms, [&]() -> int {
+          CK(launch_fft_n(p, g, p.spec, p.twN, false));
+          CK(launch_fft_n(p, g, p.spec, p.twN, true));
+          return SR3D_OK;
+        }));
+        if (ms < bt) { bt = ms; best.tw_n = tw; }
+      }
+      g.tw_n = best.tw_n;
+    }
+    // s pass (ADMM class solve) tile width; Lambda is re-permuted per candidate
+    {
+      const int tpl = g.S / g.fs.e;
+      const int cap = ((g.Ms + 2 * g.dr - 1) / (2 * g.dr)) * (2 * g.dr);
+      float bt = 1e30f;
+      const int tw0 = g.tw_s;
+      for (int tw : {tw0 / 2, tw0, tw0 * 2}) {
+        tw = (tw / g.dr) * g.dr;
+        if (tw < g.dr || tw > cap || (long long)tw * g.g_s * tpl > 512 || (size_t)tw * g.g_s * g.S * csz > 160 * 1024)
+          continue;
+        Geometry gc = g;
+        gc.tw_s = tw;
+        if (solve_lam_elems(gc) > p.lam_solve_cap || solve_yhat_elems(gc) > p.yhat_solve_cap) continue;
+        g.tw_s = tw;
+        TRY(realloc_partials(p));
+        CK(launch_perm_lam(p, p.lam, p.lam_solve));
+        SolveArgs sv = solve_args(p, 0, 1e-2);
+        float ms = 0;
+        TRY(time_ms(p, reps, &ms, [&]() -> int {
+          CK(launch_fft_s(p, g, p.spec, p.twS, S_ADMM, false, &sv));
+          return SR3D_OK;
+        }));
+        if (ms < bt) { bt = ms; best.tw_s = tw; }
+      }
+      g.tw_s = best.tw_s;
+    }
+    // TV planes per CTA
+    {
+      float bt = 1e30f;
+      for (int ts : {4, 8, 16, 32}) {
+        if (ts > g.S) continue;
+        g.ts_tv = ts;
+        float ms = 0;
+        TRY(time_ms(p, reps, &ms, [&]() -> int {
+          CK(launch_tv(p, p.theta, p.dbuf[0], p.dbuf[1], p.spec, nullptr, 1.0, 0, false));
+          return SR3D_OK;
+        }));
+        if (ms < bt) { bt = ms; best.ts_tv = ts; }
+      }
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  g.tw_n = best.tw_n;
+  g.tw_s = best.tw_s;
+  g.ts_tv = best.ts_tv;
+  {
+    Geometry gc = g;
+    if (solve_lam_elems(gc) > p.lam_solve_cap || solve_yhat_elems(gc) > p.yhat_solve_cap)
+      g.tw_s = make_geom(g.M, g.N, g.S, g.dr, g.dc, g.ds, csz).tw_s;  // cached choice does not fit: default
+  }
+  ++p.version;
+  TRY(realloc_partials(p));
+  CK(launch_perm_lam(p, p.lam, p.lam_solve));
+  if (p.iter_graph) {
+    cudaGraphExecDestroy(p.iter_graph);
+    p.iter_graph = nullptr;
+  }
+  TRY(sync_plan(p));
+  return SR3D_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Batched solve of many volumes of uneven size and decimation.
 //
 // Every volume keeps its own plan and stream.  The per-volume set-up (LR
@@ -751,6 +900,7 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
       kp.push_back(dcur[i]);
       kv.push_back(lambda[i]);
       kv.push_back(rho[i]);
+      kv.push_back((double)plans[i]->p.version);
     }
     if (!g_batch.exec || kp != g_batch.key_ptr || kv != g_batch.key_val) {
       if (g_batch.exec) {
@@ -904,6 +1054,8 @@ extern "C" int sr3d_tikhonov_noalloc(const sr3d_desc* d, const void* y, const vo
   p.twMl = b + off[3]; p.twNl = b + off[4]; p.twSl = b + off[5];
   p.symM = b + off[6]; p.symN = b + off[7]; p.symS = b + off[8];
   p.lam_solve = b + off[9];
+  p.lam_solve_cap = solve_lam_elems(g);
+  p.yhat_solve_cap = solve_yhat_elems(g);
   p.spec = b + off[10];
   p.yhat = b + off[11];
   p.yhat_solve = b + off[12];

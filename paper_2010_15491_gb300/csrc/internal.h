@@ -48,6 +48,7 @@ struct Geometry {
   int tw_s;           // s-pass tile width (multiple of dr)
   int g_s;            // s-pass tile height in n slots (multiple of dc)
   int tw_n;           // n-pass tile width
+  int ts_tv;          // TV kernel: s planes per CTA (0 = default rule)
   long long V() const { return (long long)M * N * S; }
   long long spec_elems() const { return (long long)S * N * Mp; }
 };
@@ -66,6 +67,8 @@ struct Plan {
   void* lam = nullptr;    // HR spectral
   void* lam_solve = nullptr;   // Lambda in the solve order of the s pass
   void* yhat_solve = nullptr;  // LR spectrum in the same order
+  long long lam_solve_cap = 0, yhat_solve_cap = 0;  // allocated elements
+  int version = 0;             // bumped whenever the tile schedule changes
   void* yhat = nullptr;   // LR spectral
   void* spec = nullptr;   // HR spectral work
   void* theta = nullptr;  // HR real
@@ -115,6 +118,7 @@ cudaError_t launch_perm_yhat(const Plan& p, const void* yh, void* out);
 cudaError_t launch_tv(const Plan& p, const void* x, const void* din, void* dout, void* theta, void* psi,
                       double thr, int mode, bool stats);
 long long tv_blocks(const Geometry& g);
+int tv_default_ts(const Geometry& g);
 cudaError_t launch_finalize(const Plan& p, int hist_index, double lam_tv, double mu, double inv_nl,
                             bool with_data);
 cudaError_t launch_twiddle(const Plan& p, void* tw, int n);

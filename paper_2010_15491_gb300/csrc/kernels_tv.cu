@@ -469,17 +469,20 @@ static size_t tv4_smem(bool stats) {
 
 static bool tv_vec4(const Plan& p) { return p.dtype == 0 && p.hr.M % V4M == 0 && p.hr.N % TN == 0; }
 
-static int tv_ts(const Geometry& g) {
-  // planes per CTA: aim for a few CTAs per SM-slot while keeping the
-  // one-plane priming overhead small
+int tv_default_ts(const Geometry& g) {
+  // planes per CTA: a few CTAs per SM while keeping the one-plane priming
+  // overhead small
   if (g.S >= 256) return 16;
   if (g.S >= 64) return 8;
   return 4;
 }
 
+static int tv_ts(const Geometry& g) { return g.ts_tv > 0 ? g.ts_tv : tv_default_ts(g); }
+
 long long tv_blocks(const Geometry& g) {
-  // an upper bound covering both variants (the vectorised one has 4x fewer m tiles)
-  const int ts = tv_ts(g);
+  // an upper bound covering both variants (the vectorised one has 4x fewer m
+  // tiles) and every planes-per-CTA choice of at least 4
+  const int ts = 4;
   return (long long)((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN) * ((g.S + ts - 1) / ts);
 }
 

@@ -48,3 +48,22 @@ def test_batched_rejects_repeated_plans(lib):
     with pytest.raises(lib.Sr3dError):
         lib.admm_tv_batched([p, p], [yd, yd], [p.empty_hr(), p.empty_hr()], [1e-3] * 2, [1e-2] * 2, [1e-2] * 2, 4)
     p.close()
+
+
+def test_autotuned_plans_keep_parity(lib):
+    import torch
+    dims, dec = (128, 64, 32), (2, 2, 2)
+    psf, xt, y = make_problem(dims, dec, seed=60)
+    x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
+    ref = O.admm_tv(y, psf, dec, 1e-3, 1e-2, 6, x0)["x"]
+    yd = torch.tensor(y, dtype=torch.float32, device="cuda")
+    for _ in range(2):  # the second plan applies the cached schedule
+        p = lib.Plan(dims, dec, psf, "f32", stream=torch.cuda.Stream())
+        p.autotune(2)
+        x = p.empty_hr()
+        p.admm_tv(yd, x, 1e-3, 1e-2, 6, tau_init=1e-2)
+        assert rel_l2(x.cpu().numpy(), ref) < 1e-5
+        xs = [p.empty_hr()]
+        lib.admm_tv_batched([p], [yd], xs, [1e-3], [1e-2], [1e-2], 6)
+        assert torch.equal(xs[0], x)
+        p.close()
