@@ -220,6 +220,76 @@ int sr3d_profile_read(sr3d_plan_t plan, double ms[SR3D_NKINDS], long long launch
 int sr3d_tikhonov_noalloc(const sr3d_desc* desc, const void* y_dev, const void* xbar_dev, double tau,
                           void* x_dev);
 
+/* ---------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper, whose ADMM-TV of
+ * Algorithm 1 starts from the Tikhonov solution of Eq. 12 and which argues
+ * against learned super-resolution).  A 3D U-Net refines the Tikhonov
+ * estimate into the ADMM starting point x0; sr3d_dual_init gives the dual
+ * that is consistent with that x0.
+ *
+ * Network (channels C1 = 16, C2 = 32, C3 = 64; 3x3x3 convolutions with zero
+ * padding and bias, each followed by ReLU; volumes [s][n][m]):
+ *   e1 = conv(conv(x))               full size, C1
+ *   e2 = conv(conv(maxpool(e1)))     half size, C2   (2x2x2 max pooling)
+ *   e3 = conv(conv(maxpool(e2)))     quarter size, C3
+ *   d2 = conv(conv([up(e3), e2]))    half size, C2   (nearest 2x upsampling,
+ *   d1 = conv(conv([up(d2), e1]))    full size, C1    channel concatenation)
+ *   out = sum_c w_h[c] d1[c] + b_h + x                (1x1x1 residual head)
+ * Parameters are one flat FP32 vector of sr3d_unet_param_count() values: for
+ * each of the ten 3x3x3 layers in the order above W[co][tap][ci] (tap =
+ * (ks*3 + kn)*3 + km for the offset (ks-1, kn-1, km-1) in (s, n, m)) followed
+ * by b[co]; then w_h[C1] and b_h.  Weights and activations are BF16 on the
+ * tensor cores with FP32 accumulation; master weights and the Adam state are
+ * FP32.  Sizes m, n, s must be positive multiples of 4.
+ * ------------------------------------------------------------------------- */
+typedef struct sr3d_unet_s* sr3d_unet_t;
+
+/* number of FP32 parameters of the network above (353,281) */
+long long sr3d_unet_param_count(void);
+
+/* Creates a network with all parameters zero (the identity map: out = x) on
+ * `stream` (NULL = legacy default stream).  Activation buffers are
+ * allocated on first use of a size and kept until the size changes.  The
+ * handle is freed by sr3d_unet_destroy; a network is used by one host thread
+ * at a time. */
+int sr3d_unet_create(sr3d_unet_t* out, void* stream);
+int sr3d_unet_destroy(sr3d_unet_t net);
+
+/* Copy the flat parameter vector from / to host memory (n must equal
+ * sr3d_unet_param_count()); setting parameters also clears the Adam state. */
+int sr3d_unet_set_params(sr3d_unet_t net, const float* params_host, long long n);
+int sr3d_unet_get_params(sr3d_unet_t net, float* params_host, long long n);
+
+/* out_dev = network(x_dev); both FP32 device arrays of m*n*s values in the
+ * [s][n][m] layout (they may not alias).  Synchronises the stream. */
+int sr3d_unet_forward(sr3d_unet_t net, int m, int n, int s, const float* x_dev, float* out_dev);
+
+/* One training step on the pair (x_dev, target_dev) (FP32 device arrays as in
+ * sr3d_unet_forward): loss = mean((network(x) - target)^2) is written to
+ * *loss (if not NULL); the gradient of the loss with respect to the flat
+ * parameters is copied to grad_host (if not NULL, FP32, param_count values);
+ * with update != 0 the parameters then take one Adam step (beta1 0.9,
+ * beta2 0.999, eps 1e-8, bias-corrected) of learning rate lr. */
+int sr3d_unet_train_step(sr3d_unet_t net, int m, int n, int s, const float* x_dev, const float* target_dev,
+                         double lr, double* loss, float* grad_host, int update);
+
+/* Copies an activation of the last forward pass (sr3d_unet_forward or
+ * sr3d_unet_train_step) to host memory, for inspection and layer-by-layer
+ * tests: which = 0 x, 1 e1a, 2 e1, 3 maxpool(e1), 4 e2a, 5 e2,
+ * 6 maxpool(e2), 7 e3a, 8 e3, 9 d2a, 10 d2, 11 d1a, 12 d1 (BF16,
+ * [voxel][channel] at the level's size, the first conv of each level named
+ * with an "a"), 13 the output (FP32 [voxel]).  bytes must equal the
+ * activation's size. */
+int sr3d_unet_read(sr3d_unet_t net, int which, void* host, long long bytes);
+
+/* KKT-consistent initial dual for sr3d_admm_tv started at x (no counterpart in
+ * the paper, which starts from d = 0): with g = Lx (periodic forward
+ * differences, Section 3.2) and t = lambda / rho,
+ *   d_j = t g_j / max(||g_j||, t)   (j = voxel, ||.|| over the 3 directions),
+ * written as d_dev[3][V] in the plan's dtype; x_dev is an HR volume of the
+ * plan.  Pass d_dev to sr3d_admm_tv together with x_dev as x0. */
+int sr3d_dual_init(sr3d_plan_t plan, const void* x_dev, double lambda, double rho, void* d_dev);
+
 /* Plan facts for callers and tests: sizes[0..8] = m_h, n_h, s_h, m_l, n_l,
  * s_l, m-slots, m-pitch, dtype; bytes = device memory the plan holds. */
 int sr3d_plan_info(sr3d_plan_t plan, int sizes[9], long long* bytes);

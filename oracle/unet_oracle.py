@@ -21,10 +21,25 @@ forward pass and gradients can be checked:
 
 Parameters are one flat vector: for each of the ten 3x3x3 layers in the order
 above W (co, tap, ci) then b (co); then w_h (C1) and b_h.
+
+Max pooling decides an integer (the argmax) from floating-point values.  A
+network that stores its activations in a lower precision takes that decision
+on the stored values, so forward() and grad() accept `quant`, a rounding
+applied to every stored activation (bf16_round for BF16 storage); the
+arithmetic stays FP64 and quant=None is the exact network.
 """
 from __future__ import annotations
 
 import numpy as np
+
+def bf16_round(a: np.ndarray) -> np.ndarray:
+    """Round to the nearest BF16 value (ties to even) through FP32: the FP32
+    bit pattern keeps its upper 16 bits after adding 0x7FFF plus the lowest
+    kept bit (finite inputs)."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
 
 TAPS = [(ks - 1, kn - 1, km - 1) for ks in range(3) for kn in range(3) for km in range(3)]
 
@@ -104,11 +119,13 @@ def unpack(theta: np.ndarray, c=(16, 32, 64)):
     return layers, wh, bh
 
 
-def forward(theta: np.ndarray, x: np.ndarray, c=(16, 32, 64), keep=False):
-    """x: (s, n, m) -> out (s, n, m); keep=True also returns the activations."""
+def forward(theta: np.ndarray, x: np.ndarray, c=(16, 32, 64), keep=False, quant=None):
+    """x: (s, n, m) -> out (s, n, m); keep=True also returns the activations.
+    quant (optional) rounds every stored activation (see the module notes)."""
     L, wh, bh = unpack(theta, c)
-    relu = lambda z: np.maximum(z, 0.0)  # noqa: E731
-    a = {"x": x[..., None]}
+    q = (lambda z: z) if quant is None else quant  # noqa: E731
+    relu = lambda z: q(np.maximum(z, 0.0))  # noqa: E731
+    a = {"x": q(x)[..., None]}
     a["e1a"] = relu(conv3(a["x"], *L[0]))
     a["e1"] = relu(conv3(a["e1a"], *L[1]))
     a["p1"], a["i1"] = maxpool(a["e1"])
@@ -131,9 +148,10 @@ def loss(theta, x, target, c=(16, 32, 64)) -> float:
     return float(((forward(theta, x, c) - target) ** 2).mean())
 
 
-def grad(theta, x, target, c=(16, 32, 64)):
-    """Loss and its gradient with respect to the flat parameter vector."""
-    out, a = forward(theta, x, c, keep=True)
+def grad(theta, x, target, c=(16, 32, 64), quant=None):
+    """Loss and its gradient with respect to the flat parameter vector (the
+    activations rounded by quant, if given, as in forward)."""
+    out, a = forward(theta, x, c, keep=True, quant=quant)
     L, wh, bh = unpack(theta, c)
     r = out - target
     lval = float((r ** 2).mean())

@@ -32,6 +32,8 @@ EXPORTED = [
     "sr3d_plan", "sr3d_destroy", "sr3d_forward", "sr3d_tikhonov", "sr3d_admm_tv", "sr3d_admm_tv_host",
     "sr3d_last_error", "sr3d_get_otf", "sr3d_fft3", "sr3d_xstep", "sr3d_tv_step", "sr3d_plan_info",
     "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc", "sr3d_admm_tv_batched", "sr3d_autotune",
+    "sr3d_dual_init", "sr3d_unet_param_count", "sr3d_unet_create", "sr3d_unet_destroy", "sr3d_unet_set_params",
+    "sr3d_unet_get_params", "sr3d_unet_forward", "sr3d_unet_train_step", "sr3d_unet_read",
 ]
 KINDS = ["tv", "rfft_m_fwd", "fft_n_fwd", "fft_s", "fft_n_inv", "rfft_m_inv", "other", "setup"]
 
@@ -90,6 +92,15 @@ def load() -> ctypes.CDLL:
         "sr3d_autotune": (i, [vp, i]),
         "sr3d_admm_tv_batched": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d), i]),
+        "sr3d_dual_init": (i, [vp, vp, d, d, vp]),
+        "sr3d_unet_param_count": (ctypes.c_longlong, []),
+        "sr3d_unet_create": (i, [ctypes.POINTER(vp), vp]),
+        "sr3d_unet_destroy": (i, [vp]),
+        "sr3d_unet_set_params": (i, [vp, vp, ctypes.c_longlong]),
+        "sr3d_unet_get_params": (i, [vp, vp, ctypes.c_longlong]),
+        "sr3d_unet_forward": (i, [vp, i, i, i, vp, vp]),
+        "sr3d_unet_train_step": (i, [vp, i, i, i, vp, vp, d, ctypes.POINTER(d), vp, i]),
+        "sr3d_unet_read": (i, [vp, i, vp, ctypes.c_longlong]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -253,6 +264,13 @@ class Plan:
                                    _ptr(d_out, self.tdtype, shp), float(lam), float(rho), self._hr(theta)))
         return d_out, theta
 
+    def dual_init(self, x, lam: float, rho: float, d=None):
+        """KKT-consistent initial dual for ADMM started at x (sr3d_dual_init)."""
+        d = self._torch.empty((3,) + self.hr_shape, dtype=self.tdtype, device=x.device) if d is None else d
+        _check(load().sr3d_dual_init(self._h, self._hr(x), float(lam), float(rho),
+                                     _ptr(d, self.tdtype, (3,) + self.hr_shape)))
+        return d
+
     def close(self):
         if getattr(self, "_h", None):
             load().sr3d_destroy(self._h)
@@ -324,3 +342,79 @@ def admm_tv_batched(plans, ys, xs, lams, rhos, taus, iters: int):
     dd = ctypes.c_double * n
     _check(load().sr3d_admm_tv_batched(n, P, Y, X, dd(*lams), dd(*rhos), dd(*taus), int(iters)))
     return xs
+
+
+class UNet:
+    """The learned warm-start network of the library (sr3d_unet_*): a 3D U-Net
+    with channels 16 / 32 / 64 on BF16 tensor-core kernels.  Volumes are FP32
+    CUDA tensors of shape (s, n, m), each size a multiple of 4.  A new network
+    has all parameters zero (the identity map)."""
+
+    def __init__(self, stream=None):
+        import torch
+        self._torch = torch
+        L = load()
+        self.n_params = int(L.sr3d_unet_param_count())
+        handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        self._h = ctypes.c_void_p()
+        _check(L.sr3d_unet_create(ctypes.byref(self._h), ctypes.c_void_p(handle) if handle else None))
+
+    def _vol(self, t):
+        if t.dim() != 3:
+            raise ValueError("expected an (s, n, m) volume")
+        return _ptr(t, self._torch.float32)
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(theta, dtype=np.float32)
+        if a.size != self.n_params:
+            raise ValueError(f"expected {self.n_params} parameters")
+        _check(load().sr3d_unet_set_params(self._h, a.ctypes.data, a.size))
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.n_params, dtype=np.float32)
+        _check(load().sr3d_unet_get_params(self._h, a.ctypes.data, a.size))
+        return a
+
+    def forward(self, x, out=None):
+        out = self._torch.empty_like(x) if out is None else out
+        s, n, m = x.shape
+        _check(load().sr3d_unet_forward(self._h, m, n, s, self._vol(x), self._vol(out)))
+        return out
+
+    def train_step(self, x, target, lr: float = 1e-3, update: bool = True, want_grad: bool = False):
+        """One step; returns (loss, gradient or None)."""
+        s, n, m = x.shape
+        if tuple(target.shape) != tuple(x.shape):
+            raise ValueError("target must have the shape of x")
+        loss = ctypes.c_double()
+        g = np.empty(self.n_params, dtype=np.float32) if want_grad else None
+        _check(load().sr3d_unet_train_step(self._h, m, n, s, self._vol(x), self._vol(target), float(lr),
+                                           ctypes.byref(loss), g.ctypes.data if g is not None else None,
+                                           int(bool(update))))
+        return loss.value, g
+
+    ACTIVATIONS = ["x", "e1a", "e1", "p1", "e2a", "e2", "p2", "e3a", "e3", "d2a", "d2", "d1a", "d1", "out"]
+
+    def read(self, name: str, shape) -> np.ndarray:
+        """An activation of the last forward pass (sr3d_unet_read) as float32
+        of shape (s, n, m, channels) at its level ((s, n, m) for x and out)."""
+        which = self.ACTIVATIONS.index(name)
+        count = int(np.prod(shape))
+        if which == 13:
+            a = np.empty(count, dtype=np.float32)
+            _check(load().sr3d_unet_read(self._h, which, a.ctypes.data, a.nbytes))
+            return a.reshape(shape)
+        raw = np.empty(count, dtype=np.uint16)
+        _check(load().sr3d_unet_read(self._h, which, raw.ctypes.data, raw.nbytes))
+        return (raw.astype(np.uint32) << 16).view(np.float32).reshape(shape)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sr3d_unet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

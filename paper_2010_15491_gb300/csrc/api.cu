@@ -35,6 +35,8 @@ static int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+int sr3d::record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 #define CK(call)                                                                                  \
   do {                                                                                            \
     cudaError_t e_ = (call);                                                                      \
@@ -476,6 +478,14 @@ int sr3d_plan_info(sr3d_plan_t plan, int sizes[9], long long* bytes) {
   for (int i = 0; i < 9; ++i) sizes[i] = v[i];
   if (bytes) *bytes = p.bytes;
   return SR3D_OK;
+}
+
+int sr3d_dual_init(sr3d_plan_t plan, const void* x, double lambda, double rho, void* d) {
+  if (!plan || !x || !d) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  if (!(rho > 0) || !(lambda > 0)) return fail(SR3D_ERR_INVALID_ARG, "need rho > 0 and lambda > 0");
+  Plan& p = plan->p;
+  LAUNCH(SR3D_K_OTHER, launch_dual_init(p, x, lambda / rho, d));
+  return sync_plan(p);
 }
 
 int sr3d_forward(sr3d_plan_t plan, const void* x, void* y) {

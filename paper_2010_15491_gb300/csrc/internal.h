@@ -126,4 +126,9 @@ cudaError_t launch_symbol(const Plan& p, void* sym, int n);
 cudaError_t launch_wrap_psf(const Plan& p, void* out, const double* psf_dev, int pm, int pn, int ps);
 cudaError_t launch_export_half(const Plan& p, const void* spec, void* out);
 
+// KKT-consistent initial dual from x (unet.cu)
+cudaError_t launch_dual_init(const Plan& p, const void* x, double thr, void* d);
+// sets the calling thread's last-error text (api.cu) and returns code
+int record_error(int code, const char* msg);
+
 }  // namespace sr3d

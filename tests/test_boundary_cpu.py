@@ -15,7 +15,7 @@ HEADER = os.path.join(ROOT, "include", "sr3d.h")
 
 def declared_symbols():
     txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(sr3d_\w+)\s*\(", txt, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|long long|const char\*)\s+(sr3d_\w+)\s*\(", txt, flags=re.M)))
 
 
 @pytest.fixture(scope="module")

@@ -85,3 +85,31 @@ def test_dual_from_x_lies_in_the_ball_and_is_aligned():
     g = O.grad(x)
     gn = np.sqrt((g ** 2).sum(axis=0))
     assert np.allclose(d * gn[None], g * nrm[None])  # parallel to Lx
+
+
+def test_bf16_round_is_round_to_nearest_even():
+    import torch
+    rng = np.random.default_rng(7)
+    a = np.concatenate([rng.standard_normal(10000) * 10.0 ** rng.integers(-20, 20, 10000),
+                        [0.0, -0.0, 1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 65504.0]])
+    a32 = a.astype(np.float32)
+    ref = torch.tensor(a32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(U.bf16_round(a32), ref)
+    # halfway cases go to the even neighbour
+    assert U.bf16_round(np.array([1.0 + 2.0 ** -8]))[0] == 1.0
+    assert U.bf16_round(np.array([1.0 + 3 * 2.0 ** -8]))[0] == 1.0 + 2.0 ** -6
+
+
+def test_quantised_network_rounds_only_the_stored_activations():
+    c = (4, 4, 4)
+    rng = np.random.default_rng(8)
+    theta = rng.standard_normal(U.param_count(c)) * 0.3
+    x = rng.standard_normal((8, 8, 8))
+    exact = U.forward(theta, x, c)
+    _, a = U.forward(theta, x, c, keep=True, quant=U.bf16_round)
+    for k in ("e1a", "e1", "e2", "e3", "d2", "d1"):
+        assert np.array_equal(U.bf16_round(a[k]), a[k]), k
+    out = U.forward(theta, x, c, quant=U.bf16_round)
+    # 2^-9 relative per rounding through ten layers
+    assert np.linalg.norm(out - exact) <= 5e-2 * np.linalg.norm(exact - x)
+    assert np.array_equal(U.forward(theta, x, c, quant=None), exact)
