@@ -174,6 +174,167 @@ __global__ void __launch_bounds__(128) k_conv_fwd(ConvIn in, const bf16* __restr
 }
 
 // ---------------------------------------------------------------------------
+// halo-tiled convolution for 16-multiple channel counts (forward and data
+// gradient).  A CTA computes a 16 (m) x 4 (n) x 2*MT (s) brick of output
+// voxels, 8 warps each owning MT rows of 16 voxels along m.  The input brick
+// plus its one-voxel halo is copied once into shared memory (one padded row of
+// CIN channels per voxel); the 27 taps then read their shifted A rows straight
+// from it with ldmatrix (each lane addresses its own voxel row, so the im2col
+// is implicit), while the next tap's weight slice streams in with cp.async.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cpz16(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 16 : 0;  // 0 source bytes: the 16 bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_commit_() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait_() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <int CIN, int COUT, int MT>
+struct Conv3Cfg {
+  static constexpr int TM = 16, TN = 4, TS = 2 * MT;
+  static constexpr int HM = TM + 2, HN = TN + 2, HS = TS + 2;
+  static constexpr int HV = HM * HN * HS;
+  static constexpr int CH = CIN / 8;           // 16-byte chunks per voxel row
+  static constexpr int VST = CIN * 2 + 16;     // padded row: an odd number of chunks, conflict-free ldmatrix
+  static constexpr int HALO = HV * VST;
+  static constexpr int WBYTES = COUT * VST;    // one tap's weights, rows n (out), CIN wide
+  static constexpr int SMEM = HALO + 2 * WBYTES;
+};
+
+// address of channels [c, c+8) of the (concatenated, possibly upsampled) input at an in-range voxel
+__device__ __forceinline__ const bf16* chunk_ptr(const ConvIn& in, int s, int n, int m, int c) {
+  if (c < in.c0) {
+    long long idx;
+    if (in.up0) idx = ((long long)(s >> 1) * (in.N >> 1) + (n >> 1)) * (in.M >> 1) + (m >> 1);
+    else idx = ((long long)s * in.N + n) * in.M + m;
+    return in.src0 + idx * in.c0 + c;
+  }
+  return in.src1 + (((long long)s * in.N + n) * in.M + m) * in.c1 + (c - in.c0);
+}
+
+template <int CIN, int COUT, int MT>
+__device__ __forceinline__ void conv3_load_w(unsigned char* dst, const bf16* __restrict__ wt, int tap) {
+  using C = Conv3Cfg<CIN, COUT, MT>;
+  const bf16* src = wt + (long long)tap * COUT * CIN;
+  for (int i = threadIdx.x; i < COUT * C::CH; i += 256) {
+    const int n = i / C::CH, c = i - n * C::CH;
+    cpz16(dst + n * C::VST + c * 16, src + n * CIN + c * 8, true);
+  }
+}
+
+// wt: [27][COUT][CIN] BF16 (tap-major slices, rows = output channel)
+template <int CIN, int COUT, int MT>
+__global__ void __launch_bounds__(256) k_conv3(ConvIn in, const bf16* __restrict__ wt, const float* __restrict__ bias,
+                                               int relu, bf16* __restrict__ out) {
+  using C = Conv3Cfg<CIN, COUT, MT>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char* halo = smem;
+  unsigned char* wbuf = smem + C::HALO;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int tilesM = (in.M + C::TM - 1) / C::TM, tilesN = (in.N + C::TN - 1) / C::TN;
+  int b = blockIdx.x;
+  const int m0 = (b % tilesM) * C::TM;
+  b /= tilesM;
+  const int n0 = (b % tilesN) * C::TN;
+  const int s0 = (b / tilesN) * C::TS;
+
+  for (int i = threadIdx.x; i < C::HV * C::CH; i += 256) {
+    const int hv = i / C::CH, c = i - hv * C::CH;
+    const int hm = hv % C::HM, r = hv / C::HM;
+    const int m = m0 + hm - 1, n = n0 + r % C::HN - 1, s = s0 + r / C::HN - 1;
+    const bool ok = m >= 0 && m < in.M && n >= 0 && n < in.N && s >= 0 && s < in.S;
+    cpz16(halo + hv * C::VST + c * 16, ok ? chunk_ptr(in, s, n, m, c * 8) : in.src0, ok);
+  }
+  conv3_load_w<CIN, COUT, MT>(wbuf, wt, 0);
+  cp_commit_();
+
+  float acc[MT][COUT / 8][4];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < COUT / 8; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+  const int lr = (lane & 7) + 8 * ((lane >> 3) & 1), lc = 8 * (lane >> 4);  // A: voxel row, channel block
+  const int bn = (lane & 7) + 8 * (lane >> 4), bk = 8 * ((lane >> 3) & 1);  // B: out-channel row, k block
+#pragma unroll 1
+  for (int tap = 0; tap < 27; ++tap) {
+    if (tap + 1 < 27) conv3_load_w<CIN, COUT, MT>(wbuf + ((tap + 1) & 1) * C::WBYTES, wt, tap + 1);
+    cp_commit_();
+    cp_wait_<1>();
+    __syncthreads();
+    const unsigned char* wb = wbuf + (tap & 1) * C::WBYTES;
+    const int dm = tap % 3, dn = (tap / 3) % 3, ds = tap / 9;  // halo offsets (0..2)
+    int arow[MT];
+#pragma unroll
+    for (int i = 0; i < MT; ++i) {
+      const int r = warp * MT + i;  // row of 16 voxels: n = r % 4, s = r / 4 within the brick
+      arow[i] = (((r >> 2) + ds) * C::HN + (r & 3) + dn) * C::HM + lr + dm;
+    }
+#pragma unroll
+    for (int kk = 0; kk < CIN / 16; ++kk) {
+      uint32_t bfr[COUT / 16][4];
+#pragma unroll
+      for (int np = 0; np < COUT / 16; ++np)
+        ldsm_x4(bfr[np], reinterpret_cast<const bf16*>(wb + (np * 16 + bn) * C::VST + (kk * 16 + bk) * 2));
+#pragma unroll
+      for (int i = 0; i < MT; ++i) {
+        uint32_t a[4];
+        ldsm_x4(a, reinterpret_cast<const bf16*>(halo + arow[i] * C::VST + (kk * 16 + lc) * 2));
+#pragma unroll
+        for (int np = 0; np < COUT / 16; ++np) {
+          mma16816(acc[i][2 * np], a, bfr[np][0], bfr[np][1]);
+          mma16816(acc[i][2 * np + 1], a, bfr[np][2], bfr[np][3]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < MT; ++i) {
+    const int r = warp * MT + i;
+    const int n = n0 + (r & 3), s = s0 + (r >> 2);
+    if (n >= in.N || s >= in.S) continue;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int m = m0 + g + 8 * half;
+      if (m >= in.M) continue;
+      bf16* o = out + (((long long)s * in.N + n) * in.M + m) * COUT;
+#pragma unroll
+      for (int nt = 0; nt < COUT / 8; ++nt) {
+        const int co = nt * 8 + 2 * t;
+        float x0 = acc[i][nt][2 * half], x1 = acc[i][nt][2 * half + 1];
+        if (bias) {
+          x0 += bias[co];
+          x1 += bias[co + 1];
+        }
+        if (relu) {
+          x0 = fmaxf(x0, 0.f);
+          x1 = fmaxf(x1, 0.f);
+        }
+        *reinterpret_cast<__nv_bfloat162*>(o + co) = __floats2bfloat162_rn(x0, x1);
+      }
+    }
+  }
+}
+
+// tap-major weight slices for k_conv3: forward wt[tap][co][ci] = W[co][tap][ci];
+// data gradient wtb[tap][ci][co] = W[co][26 - tap][ci]
+__global__ void k_pack_w3(const float* __restrict__ W, int Cout, int Cin, bf16* __restrict__ wt, bf16* __restrict__ wtb) {
+  const int total = 27 * Cout * Cin;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int ci = i % Cin, r = i / Cin, co = r % Cout, tap = r / Cout;
+    wt[i] = __float2bfloat16(W[((long long)co * 27 + tap) * Cin + ci]);
+    const int cb = i % Cout, rb = i / Cout, cib = rb % Cin, tb = rb / Cin;
+    wtb[i] = __float2bfloat16(W[((long long)cb * 27 + (26 - tb)) * Cin + cib]);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // weight gradient: dw[co][k] += sum_v g[v][co] A[v][k] for the k-chunk
 // blockIdx.x, over the 16-voxel tiles blockIdx.y*4 + warp (+ stride).
 // ---------------------------------------------------------------------------
@@ -465,8 +626,9 @@ struct sr3d_unet_s {
   long long step = 0;
   long long off_w[10], off_b[10], off_h;
   int kpad[10];
-  bf16* wf[10] = {};    // packed forward weights
-  bf16* wb[10] = {};    // packed data-gradient weights
+  bf16* wf0 = nullptr;  // first layer (one input channel): [co][Kpad] im2col weights
+  bf16* wt[10] = {};    // layers 1..9: tap-major forward slices [27][co][ci]
+  bf16* wtb[10] = {};   // layers 1..9: tap-major data-gradient slices [27][ci][co]
   float* dw = nullptr;  // weight-gradient scratch [Cout][Kpad]
   size_t dw_cap = 0;
   double* loss = nullptr;
@@ -524,24 +686,42 @@ static int ensure_size(sr3d_unet_s* u, int M, int N, int S) {
   return SR3D_OK;
 }
 
-template <int COUT>
-static cudaError_t conv_fwd_c(cudaStream_t st, const ConvIn& in, const bf16* w, int Kpad, int Cin,
-                              const float* bias, int relu, bf16* out, long long V) {
+// first layer: one input channel, im2col k = tap (27 taps padded to 32)
+static cudaError_t conv_first(cudaStream_t st, const ConvIn& in, const bf16* w, int Kpad, const float* bias,
+                              bf16* out, long long V) {
   const unsigned blocks = (unsigned)((V + 127) / 128);
-  if (Cin == 1) k_conv_fwd<COUT, true><<<blocks, 128, 0, st>>>(in, w, Kpad, Cin, bias, relu, out, V);
-  else k_conv_fwd<COUT, false><<<blocks, 128, 0, st>>>(in, w, Kpad, Cin, bias, relu, out, V);
+  k_conv_fwd<16, true><<<blocks, 128, 0, st>>>(in, w, Kpad, 1, bias, 1, out, V);
   return cudaGetLastError();
 }
 
-static cudaError_t conv_fwd(cudaStream_t st, int Cout, const ConvIn& in, const bf16* w, int Kpad, int Cin,
-                            const float* bias, int relu, bf16* out, long long V) {
-  switch (Cout) {
-    case 16: return conv_fwd_c<16>(st, in, w, Kpad, Cin, bias, relu, out, V);
-    case 32: return conv_fwd_c<32>(st, in, w, Kpad, Cin, bias, relu, out, V);
-    case 48: return conv_fwd_c<48>(st, in, w, Kpad, Cin, bias, relu, out, V);
-    case 64: return conv_fwd_c<64>(st, in, w, Kpad, Cin, bias, relu, out, V);
-    case 96: return conv_fwd_c<96>(st, in, w, Kpad, Cin, bias, relu, out, V);
-  }
+template <int CIN, int COUT, int MT>
+static cudaError_t conv3_t(cudaStream_t st, const ConvIn& in, const bf16* wt, const float* bias, int relu, bf16* out) {
+  using C = Conv3Cfg<CIN, COUT, MT>;
+  cudaError_t e = cudaFuncSetAttribute(k_conv3<CIN, COUT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (long long)((in.M + C::TM - 1) / C::TM) * ((in.N + C::TN - 1) / C::TN) *
+                           ((in.S + C::TS - 1) / C::TS);
+  k_conv3<CIN, COUT, MT><<<(unsigned)blocks, 256, C::SMEM, st>>>(in, wt, bias, relu, out);
+  return cudaGetLastError();
+}
+
+// 3x3x3 convolution with cin = in.c0 + in.c1 input channels (a multiple of 16)
+static cudaError_t conv3(cudaStream_t st, int cin, int cout, const ConvIn& in, const bf16* wt, const float* bias,
+                         int relu, bf16* out) {
+#define SR3D_CONV3(CI, CO, MT_) \
+  if (cin == CI && cout == CO) return conv3_t<CI, CO, MT_>(st, in, wt, bias, relu, out);
+  SR3D_CONV3(16, 16, 2)
+  SR3D_CONV3(16, 32, 2)
+  SR3D_CONV3(32, 32, 2)
+  SR3D_CONV3(32, 64, 2)
+  SR3D_CONV3(64, 64, 2)
+  SR3D_CONV3(96, 32, 1)
+  SR3D_CONV3(48, 16, 2)
+  SR3D_CONV3(16, 48, 2)
+  SR3D_CONV3(32, 96, 2)
+  SR3D_CONV3(64, 32, 2)
+  SR3D_CONV3(32, 16, 2)
+#undef SR3D_CONV3
   return cudaErrorInvalidValue;
 }
 
@@ -575,9 +755,11 @@ static ConvIn cin(const bf16* a, int ca, int up, const bf16* b, int cb, int M, i
 }
 
 static int pack_weights(sr3d_unet_s* u) {
-  for (int l = 0; l < 10; ++l) {
+  k_pack_w<<<64, 256, 0, u->stream>>>(u->p + u->off_w[0], kLayers[0].cout, 1, u->kpad[0], u->wf0, nullptr);
+  UCK(cudaGetLastError());
+  for (int l = 1; l < 10; ++l) {
     const LayerShape& L = kLayers[l];
-    k_pack_w<<<64, 256, 0, u->stream>>>(u->p + u->off_w[l], L.cout, L.cin, u->kpad[l], u->wf[l], l > 0 ? u->wb[l] : nullptr);
+    k_pack_w3<<<128, 256, 0, u->stream>>>(u->p + u->off_w[l], L.cout, L.cin, u->wt[l], u->wtb[l]);
     UCK(cudaGetLastError());
   }
   return SR3D_OK;
@@ -591,18 +773,18 @@ static int unet_forward(sr3d_unet_s* u, const float* x) {
   auto bias = [&](int l) { return b + u->off_b[l]; };
   k_to_bf16<<<grid_for(V), 256, 0, st>>>(x, u->xb, V);
   UCK(cudaGetLastError());
-  UCK(conv_fwd(st, C1, cin(u->xb, 1, 0, nullptr, 0, M, N, S), u->wf[0], u->kpad[0], 1, bias(0), 1, u->e1a, V));
-  UCK(conv_fwd(st, C1, cin(u->e1a, C1, 0, nullptr, 0, M, N, S), u->wf[1], u->kpad[1], C1, bias(1), 1, u->e1, V));
+  UCK(conv_first(st, cin(u->xb, 1, 0, nullptr, 0, M, N, S), u->wf0, u->kpad[0], bias(0), u->e1a, V));
+  UCK(conv3(st, C1, C1, cin(u->e1a, C1, 0, nullptr, 0, M, N, S), u->wt[1], bias(1), 1, u->e1));
   k_maxpool<<<grid_for(V2 * C1), 256, 0, st>>>(u->e1, u->p1, u->i1, M, N, S, C1);
-  UCK(conv_fwd(st, C2, cin(u->p1, C1, 0, nullptr, 0, M / 2, N / 2, S / 2), u->wf[2], u->kpad[2], C1, bias(2), 1, u->e2a, V2));
-  UCK(conv_fwd(st, C2, cin(u->e2a, C2, 0, nullptr, 0, M / 2, N / 2, S / 2), u->wf[3], u->kpad[3], C2, bias(3), 1, u->e2, V2));
+  UCK(conv3(st, C1, C2, cin(u->p1, C1, 0, nullptr, 0, M / 2, N / 2, S / 2), u->wt[2], bias(2), 1, u->e2a));
+  UCK(conv3(st, C2, C2, cin(u->e2a, C2, 0, nullptr, 0, M / 2, N / 2, S / 2), u->wt[3], bias(3), 1, u->e2));
   k_maxpool<<<grid_for(V4 * C2), 256, 0, st>>>(u->e2, u->p2, u->i2, M / 2, N / 2, S / 2, C2);
-  UCK(conv_fwd(st, C3, cin(u->p2, C2, 0, nullptr, 0, M / 4, N / 4, S / 4), u->wf[4], u->kpad[4], C2, bias(4), 1, u->e3a, V4));
-  UCK(conv_fwd(st, C3, cin(u->e3a, C3, 0, nullptr, 0, M / 4, N / 4, S / 4), u->wf[5], u->kpad[5], C3, bias(5), 1, u->e3, V4));
-  UCK(conv_fwd(st, C2, cin(u->e3, C3, 1, u->e2, C2, M / 2, N / 2, S / 2), u->wf[6], u->kpad[6], C3 + C2, bias(6), 1, u->d2a, V2));
-  UCK(conv_fwd(st, C2, cin(u->d2a, C2, 0, nullptr, 0, M / 2, N / 2, S / 2), u->wf[7], u->kpad[7], C2, bias(7), 1, u->d2, V2));
-  UCK(conv_fwd(st, C1, cin(u->d2, C2, 1, u->e1, C1, M, N, S), u->wf[8], u->kpad[8], C2 + C1, bias(8), 1, u->d1a, V));
-  UCK(conv_fwd(st, C1, cin(u->d1a, C1, 0, nullptr, 0, M, N, S), u->wf[9], u->kpad[9], C1, bias(9), 1, u->d1, V));
+  UCK(conv3(st, C2, C3, cin(u->p2, C2, 0, nullptr, 0, M / 4, N / 4, S / 4), u->wt[4], bias(4), 1, u->e3a));
+  UCK(conv3(st, C3, C3, cin(u->e3a, C3, 0, nullptr, 0, M / 4, N / 4, S / 4), u->wt[5], bias(5), 1, u->e3));
+  UCK(conv3(st, C3 + C2, C2, cin(u->e3, C3, 1, u->e2, C2, M / 2, N / 2, S / 2), u->wt[6], bias(6), 1, u->d2a));
+  UCK(conv3(st, C2, C2, cin(u->d2a, C2, 0, nullptr, 0, M / 2, N / 2, S / 2), u->wt[7], bias(7), 1, u->d2));
+  UCK(conv3(st, C2 + C1, C1, cin(u->d2, C2, 1, u->e1, C1, M, N, S), u->wt[8], bias(8), 1, u->d1a));
+  UCK(conv3(st, C1, C1, cin(u->d1a, C1, 0, nullptr, 0, M, N, S), u->wt[9], bias(9), 1, u->d1));
   k_head_fwd<C1><<<grid_for(V), 256, 0, st>>>(u->d1, b + u->off_h, x, u->out, V);
   UCK(cudaGetLastError());
   return SR3D_OK;
@@ -622,7 +804,7 @@ static int layer_back(sr3d_unet_s* u, int l, const ConvIn& in, bf16* gy, const b
   UCK(cudaGetLastError());
   if (gx) {
     const ConvIn gi = cin(gy, L.cout, 0, nullptr, 0, in.M, in.N, in.S);
-    UCK(conv_fwd(st, L.cin, gi, u->wb[l], 27 * L.cout, L.cout, nullptr, 0, gx, V));
+    UCK(conv3(st, L.cout, L.cin, gi, u->wtb[l], nullptr, 0, gx));
   }
   return SR3D_OK;
 }
@@ -698,9 +880,11 @@ int sr3d_unet_create(sr3d_unet_t* out, void* stream) {
   if (e == cudaSuccess) e = cudaMalloc(&u->m2, u->np * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&u->loss, sizeof(double));
   size_t dwmax = 0;
+  if (e == cudaSuccess) e = cudaMalloc(&u->wf0, (size_t)kLayers[0].cout * u->kpad[0] * sizeof(bf16));
   for (int l = 0; l < 10 && e == cudaSuccess; ++l) {
-    e = cudaMalloc(&u->wf[l], (size_t)kLayers[l].cout * u->kpad[l] * sizeof(bf16));
-    if (e == cudaSuccess && l > 0) e = cudaMalloc(&u->wb[l], (size_t)kLayers[l].cin * 27 * kLayers[l].cout * sizeof(bf16));
+    const size_t nw = (size_t)27 * kLayers[l].cout * kLayers[l].cin;
+    if (l > 0) e = cudaMalloc(&u->wt[l], nw * sizeof(bf16));
+    if (e == cudaSuccess && l > 0) e = cudaMalloc(&u->wtb[l], nw * sizeof(bf16));
     const size_t dws = (size_t)kLayers[l].cout * u->kpad[l];
     if (dws > dwmax) dwmax = dws;
   }
@@ -724,9 +908,10 @@ int sr3d_unet_destroy(sr3d_unet_t u) {
   void* ps[] = {u->p, u->g, u->m1, u->m2, u->loss, u->dw};
   for (void* b : ps)
     if (b) cudaFree(b);
+  if (u->wf0) cudaFree(u->wf0);
   for (int l = 0; l < 10; ++l) {
-    if (u->wf[l]) cudaFree(u->wf[l]);
-    if (u->wb[l]) cudaFree(u->wb[l]);
+    if (u->wt[l]) cudaFree(u->wt[l]);
+    if (u->wtb[l]) cudaFree(u->wtb[l]);
   }
   delete u;
   return SR3D_OK;
