@@ -181,6 +181,10 @@ static void free_plan(Plan& p) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p.iter_graph) cudaGraphExecDestroy(p.iter_graph);
+  for (auto& g : p.eval_graph)
+    if (g) cudaGraphExecDestroy(g);
+  if (p.hcount) cudaFree(p.hcount);
+  if (p.res_host) cudaFreeHost(p.res_host);
   if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
   for (int i = 0; i < 2 * p.prof_cap; ++i) cudaEventDestroy(p.prof_ev[i]);
   delete[] p.prof_ev;
@@ -296,6 +300,77 @@ static int admm_iterations_graph(Plan& p, void* x, void* d0, void* d1, double th
 static int admm_iteration(Plan& p, void* x, const void* din, void* dout, double thr, double rho) {
   TRY(xstep_core(p, p.theta, rho, x, false));
   LAUNCH(SR3D_K_TV, launch_tv(p, x, din, dout, p.theta, p.psi, thr, 0, false));
+  return SR3D_OK;
+}
+
+static void drop_eval_graphs(Plan& p) {
+  for (auto& g : p.eval_graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// One evaluation block: iterations 1..every, statistics kernels in the last
+// two (the dual residual needs L^T u of the iteration before), the finalize
+// (objective history indexed on the device) and the copy of its results to
+// pinned host memory.  d0 -> d1 -> d0 ... through the block.
+static int admm_eval_block(Plan& p, void* x, void* d0, void* d1, double thr, double rho, double lambda,
+                           int every) {
+  void* a = d0;
+  void* b = d1;
+  for (int j = 1; j <= every; ++j) {
+    const bool eval_now = j == every;
+    const bool stats_now = eval_now || j + 1 == every;
+    TRY(xstep_core(p, p.theta, rho, x, eval_now));
+    LAUNCH(SR3D_K_TV, launch_tv(p, x, a, b, p.theta, p.psi, thr, 0, stats_now));
+    void* t = a;
+    a = b;
+    b = t;
+  }
+  LAUNCH(SR3D_K_OTHER, launch_finalize(p, -2, lambda, rho, 1.0 / (double)p.lr.V(), true));
+  CK(cudaMemcpyAsync(p.res_host, p.result, 11 * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+  return SR3D_OK;
+}
+
+// Replays the evaluation block whose dual buffers start as (d0, d1),
+// capturing it first when buffers or parameters changed.  par selects the
+// cached graph (0: first buffer order seen, 1: the swapped order).
+static int admm_eval_block_graph(Plan& p, void* x, void* d0, void* d1, double thr, double rho, double lambda,
+                                 int every, int par) {
+  if (p.eg_x != x || p.eg_thr != thr || p.eg_rho != rho || p.eg_lam != lambda || p.eg_every != every ||
+      p.eg_hist != p.hist || p.eg_partial != p.partial || p.eg_d[par] != d0 || p.eg_d[1 - par] != d1) {
+    drop_eval_graphs(p);
+    p.eg_x = x; p.eg_thr = thr; p.eg_rho = rho; p.eg_lam = lambda; p.eg_every = every;
+    p.eg_hist = p.hist; p.eg_partial = p.partial;
+    p.eg_d[par] = d0; p.eg_d[1 - par] = d1;
+  }
+  cudaGraphExec_t& ge = p.eval_graph[par];
+  if (!ge) {
+    long long before[8];
+    for (int k = 0; k < 8; ++k) before[k] = p.launches[k];
+    cudaGraph_t graph = nullptr;
+    CK(cudaStreamBeginCapture(p.stream, cudaStreamCaptureModeThreadLocal));
+    const int rc = admm_eval_block(p, x, d0, d1, thr, rho, lambda, every);
+    cudaError_t ec = cudaStreamEndCapture(p.stream, &graph);
+    if (rc != SR3D_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ec != cudaSuccess) return fail(SR3D_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+    ec = cudaGraphInstantiate(&ge, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ec != cudaSuccess) {
+      ge = nullptr;
+      return fail(SR3D_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+    }
+    for (int k = 0; k < 8; ++k) {
+      p.eg_launches[par][k] = p.launches[k] - before[k];
+      p.launches[k] = before[k];
+    }
+  }
+  CK(cudaGraphLaunch(ge, p.stream));
+  for (int k = 0; k < 8; ++k) p.launches[k] += p.eg_launches[par][k];
   return SR3D_OK;
 }
 
@@ -612,7 +687,39 @@ int sr3d_admm_tv(sr3d_plan_t plan, const void* y, void* x, void* d_dev, double l
     it += 2 * pairs;
     if (it < max_iters) TRY(eager());
   }
+  // with statistics: after the first evaluation (all kernels loaded), whole
+  // evaluation blocks run as replayed graphs; tol > 0 waits for each block's
+  // residuals, otherwise the blocks are queued back to back
+  const bool block_graphs = want_stats && every >= 1 && !p.prof_on && p.stream != nullptr;
+  if (block_graphs) {
+    if (!p.hcount) TRY(dmalloc(p, (void**)&p.hcount, sizeof(int)));
+    if (!p.res_host) CK(cudaHostAlloc((void**)&p.res_host, 16 * sizeof(double), cudaHostAllocDefault));
+  }
+  void* const d_first = dcur;
   for (int k = it + 1; k <= max_iters; ++k) {
+    if (block_graphs && evals > 0 && (k - 1) % every == 0 && k - 1 + every <= max_iters) {
+      CK(cudaMemcpyAsync(p.hcount, &evals, sizeof(int), cudaMemcpyHostToDevice, p.stream));
+      const int par = dcur == d_first ? 0 : 1;
+      TRY(admm_eval_block_graph(p, x, dcur, dnext, thr, rho, lambda, every, par));
+      if (every & 1) {
+        void* t = dcur;
+        dcur = dnext;
+        dnext = t;
+      }
+      ++evals;
+      it = k - 1 + every;
+      k = it;
+      if (tol > 0) {
+        TRY(sync_plan(p));
+        memcpy(res, p.res_host, 11 * sizeof(double));
+        if (res[10] != 0.0) return fail(SR3D_ERR_NUMERIC, "NaN/Inf in the objective or residuals at iteration %d", it);
+        if (res[8] < tol && res[9] < tol) {
+          converged = true;
+          break;
+        }
+      }
+      continue;
+    }
     const bool eval_now = want_stats && ((every > 0 && k % every == 0) || k == max_iters);
     const bool stats_now = want_stats && (eval_now || (every > 0 && (k + 1) % every == 0) || k + 1 == max_iters);
     TRY(xstep_core(p, p.theta, rho, x, eval_now));
@@ -820,6 +927,7 @@ extern "C" int sr3d_autotune(sr3d_plan_t plan, int reps) {
     cudaGraphExecDestroy(p.iter_graph);
     p.iter_graph = nullptr;
   }
+  drop_eval_graphs(p);
   TRY(sync_plan(p));
   return SR3D_OK;
 }

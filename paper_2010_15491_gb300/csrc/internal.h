@@ -98,6 +98,20 @@ struct Plan {
   const void* ig_d1 = nullptr;
   double ig_thr = 0, ig_rho = 0;
   long long ig_launches[8] = {0};
+  // CUDA graphs of one evaluation block of sr3d_admm_tv with statistics:
+  // every-1 iterations, the iteration that evaluates (statistics kernels in
+  // the last two), the finalize and the copy of its results to pinned host
+  // memory.  One graph per dual-buffer parity at the start of the block.
+  cudaGraphExec_t eval_graph[2] = {nullptr, nullptr};
+  const void* eg_x = nullptr;
+  const void* eg_d[2] = {nullptr, nullptr};
+  const void* eg_hist = nullptr;
+  const void* eg_partial = nullptr;
+  double eg_thr = 0, eg_rho = 0, eg_lam = 0;
+  int eg_every = 0;
+  long long eg_launches[2][8] = {};
+  int* hcount = nullptr;       // device: objective-history entries written by graph replays
+  double* res_host = nullptr;  // pinned host copy of the finalize results
 };
 
 // ---- launchers (kernels_fft.cu) ----

@@ -222,8 +222,11 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
 // consecutive m voxels (float4 loads and stores).  Warp 0 also evaluates the
 // -n halo row of the rho region, warp 1 the -m halo column; x halo rows come
 // through warps 0 and 7, halo columns through warp 1.  Same algebra, modes
-// and statistics as k_tv.  Shared rows are padded so that m0 sits at column
-// 4 (16-byte aligned); column 3 is m0-1 and column 132 is m0+128.
+// and statistics as k_tv; the statistics of a thread's four voxels are summed
+// in FP32 (sqrtf for ||g||) and those four-term sums accumulated in FP64
+// (FP64 arithmetic is slow on this GPU; a four-term FP32 sum is exact to a
+// few ulps).  Shared rows are padded so that m0 sits at column 4 (16-byte
+// aligned); column 3 is m0-1 and column 132 is m0+128.
 // ---------------------------------------------------------------------------
 constexpr int V4M = 128;
 constexpr int V4W = 136;  // padded row length (floats)
@@ -344,6 +347,7 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
       const float4 dv1 = lds4(dd + 1 * RP + xr * V4W + mc);
       const float4 dv2 = lds4(dd + 2 * RP + xr * V4W + mc);
       float e0v[4], e1v[4], e2v[4];
+      float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;  // the quad's partial sums (FP32, 4 terms)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         const float xv = f4(a, i);
@@ -353,14 +357,19 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
         float u0, u1, u2;
         voxel(xr, mc + i, g0, g1, g2, f4(dv0, i), f4(dv1, i), f4(dv2, i), u0, u1, u2, e0v[i], e1v[i], e2v[i]);
         if (STATS && interior && own_plane) {
-          const double gg = (double)g0 * g0 + (double)g1 * g1 + (double)g2 * g2;
-          q[0] += sqrt(gg);
-          const double p0 = (double)e0v[i] - f4(dv0, i), p1 = (double)e1v[i] - f4(dv1, i),
-                       p2 = (double)e2v[i] - f4(dv2, i);
-          q[1] += p0 * p0 + p1 * p1 + p2 * p2;
-          q[2] += gg;
-          q[3] += (double)u0 * u0 + (double)u1 * u1 + (double)u2 * u2;
+          const float gg = g0 * g0 + g1 * g1 + g2 * g2;
+          f0 += sqrtf(gg);
+          const float p0 = e0v[i] - f4(dv0, i), p1 = e1v[i] - f4(dv1, i), p2 = e2v[i] - f4(dv2, i);
+          f1 += p0 * p0 + p1 * p1 + p2 * p2;
+          f2 += gg;
+          f3 += u0 * u0 + u1 * u1 + u2 * u2;
         }
+      }
+      if (STATS && interior && own_plane) {
+        q[0] += f0;
+        q[1] += f1;
+        q[2] += f2;
+        q[3] += f3;
       }
       if (MODE == 0 && interior && own_plane) {
         const long long gi = pl + o_in;
@@ -414,6 +423,7 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
         if (STATS) {
           const float ul = rs[0 * RP + row - 1], el = rs[3 * RP + row - 1];
           float pv[4];
+          float f5 = 0.f;
 #pragma unroll
           for (int i = 0; i < 4; ++i) {
             const float lu = i == 0 ? ul : f4(u_0, i - 1);
@@ -421,15 +431,18 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
             const float psi_v = (lu - f4(u_0, i)) + (f4(uup1, i) - f4(u_1, i)) + (f4(u2prev, i) - f4(u_2, i));
             const float ltd = (le - f4(e_0, i)) + (f4(eup1, i) - f4(e_1, i)) + (f4(e2prev, i) - f4(e_2, i));
             pv[i] = psi_v;
-            q[5] += (double)ltd * ltd;
+            f5 += ltd * ltd;
           }
+          q[5] += f5;
           if (MODE == 0) {
             const float4 old = ld4(psi + gi);
+            float f4s = 0.f;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-              const double dl = (double)pv[i] - (double)f4(old, i);
-              q[4] += dl * dl;
+              const float dl = pv[i] - f4(old, i);
+              f4s += dl * dl;
             }
+            q[4] += f4s;
           }
           st4(psi + gi, make_float4(pv[0], pv[1], pv[2], pv[3]));
         }
@@ -545,7 +558,8 @@ cudaError_t launch_tv(const Plan& p, const void* x, const void* din, void* dout,
 // ---------------------------------------------------------------------------
 __global__ void k_finalize(const double* __restrict__ ptv, long long ntv, const double* __restrict__ ps,
                            long long ns, double lam_tv, double mu, double inv_nl, int with_data,
-                           double* __restrict__ out, double* __restrict__ hist, int hidx) {
+                           double* __restrict__ out, double* __restrict__ hist, int hidx, int* __restrict__ hcount,
+                           int hcap) {
   __shared__ double red[NQ + 1][256];
   const int tid = threadIdx.x;
   double acc[NQ + 1] = {0, 0, 0, 0, 0, 0, 0};
@@ -583,7 +597,13 @@ __global__ void k_finalize(const double* __restrict__ ptv, long long ntv, const 
     bool bad = false;
     for (int k = 0; k < 10; ++k) bad |= !isfinite(out[k]);
     out[10] = bad ? 1.0 : 0.0;
-    if (hidx >= 0 && hist) hist[hidx] = obj;
+    if (hidx == -2 && hcount) {  // index kept on the device (graph replays)
+      const int i = *hcount;
+      if (i < hcap && hist) hist[i] = obj;
+      *hcount = i + 1;
+    } else if (hidx >= 0 && hist) {
+      hist[hidx] = obj;
+    }
   }
 }
 
@@ -598,7 +618,7 @@ static long long tv_launch_blocks(const Plan& p) {
 cudaError_t launch_finalize(const Plan& p, int hist_index, double lam_tv, double mu, double inv_nl,
                             bool with_data) {
   k_finalize<<<1, 256, 0, p.stream>>>(p.partial, tv_launch_blocks(p), p.partial_s, p.n_s_blocks, lam_tv, mu, inv_nl,
-                                      with_data ? 1 : 0, p.result, p.hist, hist_index);
+                                      with_data ? 1 : 0, p.result, p.hist, hist_index, p.hcount, p.hist_cap);
   return cudaGetLastError();
 }
 

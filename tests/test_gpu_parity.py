@@ -245,3 +245,40 @@ def test_graph_replay_across_calls(lib, tag):
         ref = O.admm_tv(y, psf, dec, lam, mu, iters, x0)["x"]
         assert rel_l2(H(x), ref, tag(f"call{call}")) < TOL["f32"]
     plan.close()
+
+
+@pytest.mark.parametrize("every,dtype", [(4, "f32"), (3, "f32"), (1, "f64"), (5, "f64")])
+def test_statistics_blocks_replayed_as_graphs_match_eager(lib, every, dtype):
+    """With statistics, whole evaluation blocks are replayed as CUDA graphs
+    (odd blocks alternate the dual buffers); profiling forces every launch to
+    run eagerly.  Both give the same iterates, dual, residuals and objective
+    history bit for bit, with and without a tolerance stop."""
+    import torch
+    dims, dec = (128, 32, 16), (2, 2, 1)
+    psf, xt, y = make_problem(dims, dec, seed=31)
+    plan = lib.Plan(dims, dec, psf, dtype)
+    yd = T(y, dtype)
+    runs = []
+    for prof in (False, True):
+        plan.profile(prof)
+        x = plan.empty_hr()
+        d = torch.zeros((3,) + plan.hr_shape, dtype=plan.tdtype, device="cuda")
+        st = plan.admm_tv(yd, x, 2e-3, 1e-2, 23, d=d, tau_init=1e-2, eval_every=every, hist_len=64)
+        x2 = plan.empty_hr()
+        st2 = plan.admm_tv(yd, x2, 2e-3, 1e-2, 400, tol=3e-3, tau_init=1e-2, eval_every=every, hist_len=64)
+        runs.append((x, d, st, x2, st2))
+    plan.profile(False)
+    (xa, da, sa, xa2, sa2), (xb, db, sb, xb2, sb2) = runs
+    assert torch.equal(xa, xb) and torch.equal(da, db) and torch.equal(xa2, xb2)
+    for k in ("iters", "evals", "objective", "primal_rel", "dual_rel", "objective_hist"):
+        assert sa[k] == sb[k], k
+        assert sa2[k] == sb2[k], k
+    assert sa["evals"] == 23 // every + (1 if 23 % every else 0)
+    assert sa2["converged"] and sa2["iters"] % every == 0
+    # the history equals the oracle's objective at the evaluated iterations
+    x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
+    ref = O.admm_tv(y, psf, dec, 2e-3, 1e-2, 23, x0, record=True)
+    its = [k for k in range(1, 24) if k % every == 0 or k == 23]
+    tol = 1e-5 if dtype == "f32" else 1e-10
+    assert np.allclose(sa["objective_hist"], [ref["hist"]["objective"][k - 1] for k in its], rtol=tol)
+    plan.close()
