@@ -31,23 +31,24 @@ import numpy as np
 from . import Plan, UNet
 
 
-def warm_start(plan: Plan, net: UNet, y, lam: float, rho: float, tau: float):
-    """x0 = UNet(Tikhonov(y)) and the dual consistent with it; returns (x0, d0)."""
+def warm_start(plan: Plan, net: UNet, y, lam: float, rho: float, tau: float, dual: bool = True):
+    """x0 = UNet(Tikhonov(y)) and the dual consistent with it (None with
+    dual=False: ADMM then starts from d0 = 0); returns (x0, d0)."""
     x_tik = plan.tikhonov(y, tau, xbar="nearest")
     x0 = net.forward(x_tik)
-    d0 = plan.dual_init(x0, lam, rho)
+    d0 = plan.dual_init(x0, lam, rho) if dual else None
     return x0, d0
 
 
 def solve(plan: Plan, y, lam: float, rho: float, tau: float, tol: float, max_iters: int,
-          eval_every: int = 5, net: Optional[UNet] = None):
-    """ADMM-TV to tolerance, cold (Tikhonov start, d0 = 0) or warm (net given).
-    Returns (x, statistics)."""
+          eval_every: int = 5, net: Optional[UNet] = None, dual: bool = True):
+    """ADMM-TV to tolerance, cold (Tikhonov start, d0 = 0) or warm (net given;
+    dual=False keeps d0 = 0).  Returns (x, statistics)."""
     if net is None:
         x = plan.empty_hr()
         st = plan.admm_tv(y, x, lam, rho, max_iters, tol=tol, tau_init=tau, eval_every=eval_every)
     else:
-        x, d = warm_start(plan, net, y, lam, rho, tau)
+        x, d = warm_start(plan, net, y, lam, rho, tau, dual)
         st = plan.admm_tv(y, x, lam, rho, max_iters, d=d, tol=tol, eval_every=eval_every)
     return x, st
 
