@@ -41,6 +41,30 @@ UNIT = "voxel·iters/s"
 # half spectrum = 4 B/voxel); they sum to 80 B per voxel-iteration
 ALG_BYTES = {"tv": 32, "rfft_m_fwd": 8, "fft_n_fwd": 8, "fft_s": 16, "fft_n_inv": 8, "rfft_m_inv": 8}
 STEP_BYTES = 80
+# DRAM bytes per launch (dram__bytes_read + dram__bytes_write) of each loop
+# kernel from one ncu capture of this workload (profiles/admm_tv_256_kernels_ncu.md),
+# valid while the kernel's sources hash to the recorded value
+NCU_TRAFFIC = {
+    "tv": (516.4e6, ("kernels_tv.cu", "common.cuh"), "c8cf7651b7dee524"),
+    "rfft_m_fwd": (87.7e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "d71d6d29773ae8aa"),
+    "fft_n_fwd": (80.4e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "d71d6d29773ae8aa"),
+    "fft_s": (185.3e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "d71d6d29773ae8aa"),
+    "fft_n_inv": (80.5e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "d71d6d29773ae8aa"),
+    "rfft_m_inv": (89.7e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "d71d6d29773ae8aa"),
+}
+
+
+def ncu_traffic(kind):
+    """Recorded DRAM bytes per launch of a loop kernel, or None if its sources changed."""
+    import hashlib
+    if kind not in NCU_TRAFFIC:
+        return None
+    nbytes, files, digest = NCU_TRAFFIC[kind]
+    m = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2010_15491_gb300", "csrc", f), "rb") as fh:
+            m.update(fh.read())
+    return nbytes if m.hexdigest()[:16] == digest else None
 
 
 def workload_desc(w):
@@ -123,7 +147,7 @@ def make_inputs(w, plan, torch):
     return y
 
 
-def cpu_baseline(w, y_host, iters=2):
+def cpu_baseline(w, y_host, iters=5):
     """The FP64 oracle as it stands, timed on this host for `iters` ADMM-TV iterations."""
     import oracle as O
     psf = w.psf()
@@ -260,7 +284,7 @@ def run_ours(args, w, rank, world, local_rank):
     per_launch_s = timed[dom]["ms_per_launch"] / 1e3
     achieved = ALG_BYTES[dom] * w.voxels / per_launch_s / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(dom),
                 "alg_bytes_per_launch": ALG_BYTES[dom] * w.voxels,
                 "step_frac": value / world * STEP_BYTES / (peak * 1e9)}
     if rank != 0:
