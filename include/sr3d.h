@@ -290,6 +290,19 @@ int sr3d_unet_read(sr3d_unet_t net, int which, void* host, long long bytes);
  * plan.  Pass d_dev to sr3d_admm_tv together with x_dev as x0. */
 int sr3d_dual_init(sr3d_plan_t plan, const void* x_dev, double lambda, double rho, void* d_dev);
 
+/* Separable-PSF fast path.  When the PSF is an outer product of three 1-D
+ * factors (a Gaussian, for instance, as in the experiments of Sec. IV), the
+ * eigenvalues of eq. 2 factor as Lambda(k_m, k_n, k_s) = L_m(k_m) L_n(k_n)
+ * L_s(k_s), the 1-D DFTs of the wrapped factors.  sr3d_plan detects this (every
+ * tap equal to the product of the PSF's marginal sums over the total squared,
+ * to 1e-14 of the largest tap) and computes the three 1-D tables in FP64; the
+ * class solve of eq. 12 then forms Lambda from them instead of reading the
+ * stored 3-D Lambda (4 bytes less HBM traffic per voxel in FP32).  use = 1
+ * enables the path (the default), 0 disables it, -1 only queries; *active (if
+ * not NULL) receives 1 when the path is in use.  Results agree with the stored
+ * Lambda to rounding. */
+int sr3d_separable(sr3d_plan_t plan, int use, int* active);
+
 /* Plan facts for callers and tests: sizes[0..8] = m_h, n_h, s_h, m_l, n_l,
  * s_l, m-slots, m-pitch, dtype; bytes = device memory the plan holds. */
 int sr3d_plan_info(sr3d_plan_t plan, int sizes[9], long long* bytes);

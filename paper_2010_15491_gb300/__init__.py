@@ -32,6 +32,7 @@ EXPORTED = [
     "sr3d_plan", "sr3d_destroy", "sr3d_forward", "sr3d_tikhonov", "sr3d_admm_tv", "sr3d_admm_tv_host",
     "sr3d_last_error", "sr3d_get_otf", "sr3d_fft3", "sr3d_xstep", "sr3d_tv_step", "sr3d_plan_info",
     "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc", "sr3d_admm_tv_batched", "sr3d_autotune",
+    "sr3d_separable",
     "sr3d_dual_init", "sr3d_unet_param_count", "sr3d_unet_create", "sr3d_unet_destroy", "sr3d_unet_set_params",
     "sr3d_unet_get_params", "sr3d_unet_forward", "sr3d_unet_train_step", "sr3d_unet_read",
 ]
@@ -93,6 +94,7 @@ def load() -> ctypes.CDLL:
         "sr3d_admm_tv_batched": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d), i]),
         "sr3d_dual_init": (i, [vp, vp, d, d, vp]),
+        "sr3d_separable": (i, [vp, i, ctypes.POINTER(i)]),
         "sr3d_unet_param_count": (ctypes.c_longlong, []),
         "sr3d_unet_create": (i, [ctypes.POINTER(vp), vp]),
         "sr3d_unet_destroy": (i, [vp]),
@@ -182,6 +184,13 @@ class Plan:
         out = dict(zip(keys, list(sizes)))
         out["bytes"] = b.value
         return out
+
+    def separable(self, use: Optional[bool] = None) -> bool:
+        """Separable-PSF fast path (sr3d_separable): enable / disable it, or
+        only query with use=None; returns whether it is in use."""
+        act = ctypes.c_int()
+        _check(load().sr3d_separable(self._h, -1 if use is None else int(bool(use)), ctypes.byref(act)))
+        return bool(act.value)
 
     def autotune(self, reps: int = 3):
         """Times candidate tile schedules and keeps the fastest (cached per geometry)."""

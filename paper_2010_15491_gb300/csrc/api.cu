@@ -12,6 +12,7 @@
 #include <mutex>
 #include <tuple>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "internal.h"
@@ -177,7 +178,8 @@ static int dmalloc(Plan& p, void** ptr, size_t bytes) {
 static void free_plan(Plan& p) {
   void* bufs[] = {p.twM, p.twN, p.twS, p.twMl, p.twNl, p.twSl, p.symM, p.symN, p.symS, p.lam, p.lam_solve,
                   p.yhat_solve, p.yhat, p.spec,
-                  p.theta, p.dbuf[0], p.dbuf[1], p.psi, p.xh, p.yh, p.partial, p.partial_s, p.result, p.hist};
+                  p.theta, p.dbuf[0], p.dbuf[1], p.psi, p.xh, p.yh, p.partial, p.partial_s, p.result, p.hist,
+                  p.lamM1, p.lamN1, p.lamS1};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p.iter_graph) cudaGraphExecDestroy(p.iter_graph);
@@ -189,6 +191,38 @@ static void free_plan(Plan& p) {
   for (int i = 0; i < 2 * p.prof_cap; ++i) cudaEventDestroy(p.prof_ev[i]);
   delete[] p.prof_ev;
   delete[] p.prof_kind;
+}
+
+// Is the PSF an outer product f_s x f_n x f_m?  With T the sum of its taps,
+// the factors are its marginal sums and psf = f_s f_n f_m / T^2 exactly when
+// it is separable; accepted if every tap agrees to rounding (1e-14 of the
+// largest).  fm absorbs the 1 / T^2.
+static bool separable_factors(const double* psf, int pm, int pn, int ps, std::vector<double>& fm,
+                              std::vector<double>& fn, std::vector<double>& fs) {
+  fm.assign(pm, 0.0);
+  fn.assign(pn, 0.0);
+  fs.assign(ps, 0.0);
+  double tot = 0.0, big = 0.0;
+  for (int a = 0; a < ps; ++a)
+    for (int b = 0; b < pn; ++b)
+      for (int c = 0; c < pm; ++c) {
+        const double v = psf[((long long)a * pn + b) * pm + c];
+        fs[a] += v;
+        fn[b] += v;
+        fm[c] += v;
+        tot += v;
+        big = std::max(big, std::fabs(v));
+      }
+  if (tot == 0.0 || big == 0.0) return false;
+  const double it2 = 1.0 / (tot * tot);
+  for (int a = 0; a < ps; ++a)
+    for (int b = 0; b < pn; ++b)
+      for (int c = 0; c < pm; ++c) {
+        const double v = psf[((long long)a * pn + b) * pm + c];
+        if (std::fabs(v - fs[a] * fn[b] * fm[c] * it2) > 1e-14 * big) return false;
+      }
+  for (double& v : fm) v *= it2;
+  return true;
 }
 
 static SolveArgs solve_args(const Plan& p, int mode_alpha_nn, double alpha) {
@@ -207,6 +241,8 @@ static SolveArgs solve_args(const Plan& p, int mode_alpha_nn, double alpha) {
   sv.dr = g.dr; sv.dc = g.dc; sv.ds = g.ds;
   sv.Mlp = p.lr.Mp;
   sv.partial = p.partial_s;
+  sv.lamM = p.lamM1; sv.lamN = p.lamN1; sv.lamS = p.lamS1;
+  sv.sep = (p.sep_avail && p.sep_on) ? 1 : 0;
   return sv;
 }
 
@@ -489,6 +525,27 @@ int sr3d_plan(sr3d_plan_t* out, const sr3d_desc* d) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
     cudaFree(psf_dev);
     if (e != cudaSuccess) return fail(SR3D_ERR_CUDA, "plan setup: %s", cudaGetErrorString(e));
+    // separable PSF: the 1-D factor DFTs, whose products the class solve uses
+    std::vector<double> fm, fn, fs;
+    if (separable_factors(d->psf, d->p_m, d->p_n, d->p_s, fm, fn, fs)) {
+      TRY(dmalloc(p, &p.lamM1, (size_t)g.M * csz));
+      TRY(dmalloc(p, &p.lamN1, (size_t)g.N * csz));
+      TRY(dmalloc(p, &p.lamS1, (size_t)g.S * csz));
+      double* fdev = nullptr;
+      const size_t nf = fm.size() + fn.size() + fs.size();
+      CK(cudaMalloc(&fdev, nf * sizeof(double)));
+      std::vector<double> all(fm);
+      all.insert(all.end(), fn.begin(), fn.end());
+      all.insert(all.end(), fs.begin(), fs.end());
+      e = cudaMemcpyAsync(fdev, all.data(), nf * sizeof(double), cudaMemcpyHostToDevice, p.stream);
+      if (e == cudaSuccess) e = launch_dft_factor(p, p.lamM1, fdev, d->p_m, g.M);
+      if (e == cudaSuccess) e = launch_dft_factor(p, p.lamN1, fdev + fm.size(), d->p_n, g.N);
+      if (e == cudaSuccess) e = launch_dft_factor(p, p.lamS1, fdev + fm.size() + fn.size(), d->p_s, g.S);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
+      cudaFree(fdev);
+      if (e != cudaSuccess) return fail(SR3D_ERR_CUDA, "plan setup (separable PSF): %s", cudaGetErrorString(e));
+      p.sep_avail = true;
+    }
     return SR3D_OK;
   };
   rc = body();
@@ -561,6 +618,23 @@ int sr3d_dual_init(sr3d_plan_t plan, const void* x, double lambda, double rho, v
   Plan& p = plan->p;
   LAUNCH(SR3D_K_OTHER, launch_dual_init(p, x, lambda / rho, d));
   return sync_plan(p);
+}
+
+int sr3d_separable(sr3d_plan_t plan, int use, int* active) {
+  if (!plan) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  if (use >= 0 && (use != 0) != p.sep_on) {
+    TRY(sync_plan(p));
+    p.sep_on = use != 0;
+    if (p.iter_graph) {  // captured launches carry the old solve arguments
+      cudaGraphExecDestroy(p.iter_graph);
+      p.iter_graph = nullptr;
+    }
+    drop_eval_graphs(p);
+    ++p.version;
+  }
+  if (active) *active = (p.sep_avail && p.sep_on) ? 1 : 0;
+  return SR3D_OK;
 }
 
 int sr3d_forward(sr3d_plan_t plan, const void* x, void* y) {

@@ -37,6 +37,12 @@ struct SolveArgs {
   int dr, dc, ds;
   int Mlp;
   double* partial;     // per-CTA data-term partial sums (S_ADMM with statistics)
+  // separable PSF: Lambda(km, kn, ks) = lamM[km] lamN[kn] lamS[ks] (complex T);
+  // sep != 0 makes the class solve use these tables instead of `lam`
+  const void* lamM;
+  const void* lamN;
+  const void* lamS;
+  int sep;
 };
 
 struct Geometry {
@@ -58,6 +64,9 @@ struct Plan {
   size_t esz;    // element size
   Geometry hr, lr;
   double psf_sum;
+  bool sep_avail = false;  // the PSF is an outer product of three 1-D factors
+  bool sep_on = true;      // use the 1-D Lambda tables in the class solve when available
+  void* lamM1 = nullptr; void* lamN1 = nullptr; void* lamS1 = nullptr;  // 1-D factor DFTs (complex)
   cudaStream_t stream;
   bool own_stream;
   // device buffers
@@ -140,6 +149,7 @@ cudaError_t launch_symbol(const Plan& p, void* sym, int n);
 cudaError_t launch_wrap_psf(const Plan& p, void* out, const double* psf_dev, int pm, int pn, int ps);
 cudaError_t launch_export_half(const Plan& p, const void* spec, void* out);
 
+cudaError_t launch_dft_factor(const Plan& p, void* out, const double* f_dev, int pf, int n);
 // KKT-consistent initial dual from x (unet.cu)
 cudaError_t launch_dual_init(const Plan& p, const void* x, double thr, void* d);
 // sets the calling thread's last-error text (api.cu) and returns code

@@ -222,6 +222,10 @@ __device__ __forceinline__ double solve_tile(cplx<T>* sm, int TW, int G, int a0,
   const T* __restrict__ symM = reinterpret_cast<const T*>(sv.symM);
   const T* __restrict__ symN = reinterpret_cast<const T*>(sv.symN);
   const T* __restrict__ symS = reinterpret_cast<const T*>(sv.symS);
+  // separable PSF: Lambda of a member is the product of three 1-D factor DFTs
+  const C* __restrict__ lamM = reinterpret_cast<const C*>(sv.lamM);
+  const C* __restrict__ lamN = reinterpret_cast<const C*>(sv.lamN);
+  const C* __restrict__ lamS = reinterpret_cast<const C*>(sv.lamS);
   const T alpha = (T)sv.alpha;
   const T ialpha = (T)(1.0 / sv.alpha);
   double acc = 0.0;
@@ -239,7 +243,10 @@ __device__ __forceinline__ double solve_tile(cplx<T>* sm, int TW, int G, int a0,
       for (int q = 0; q < d; ++q) {
         const int pm = q % dr, pn = (q / dr) % dc, ps = q / (dr * dc);
         const int si = ((is + ps * sv.Sl) * G + gn * dc + pn) * TW + gm * dr + pm;
-        tsum = tsum + cmul(__ldg(&lamc[(long long)q * ncls + c]), sm[si]);
+        const C a_ = sv.sep ? cmul(cmul(__ldg(&lamM[g + pm * sv.Ml]), __ldg(&lamN[jl + pn * sv.Nl])),
+                                   __ldg(&lamS[is + ps * sv.Sl]))
+                            : __ldg(&lamc[(long long)q * ncls + c]);
+        tsum = tsum + cmul(a_, sm[si]);
       }
       reinterpret_cast<C*>(sv.lr_out)[((long long)is * sv.Nl + jl) * sv.Mlp + g] = tsum * (T)(1.0 / d);
       continue;
@@ -264,12 +271,23 @@ __device__ __forceinline__ double solve_tile(cplx<T>* sm, int TW, int G, int a0,
         if (dc_cls && q == 0) return (T)0;
         return (T)1 / (alpha * (sMv[q % DR_] + sNv[(q / DR_) % DC_] + sSv[q / (DR_ * DC_)]));
       };
+      C lmn[DR_ * DC_], lsv[DS_];
+      if (sv.sep) {
+#pragma unroll
+        for (int i = 0; i < DS_; ++i) lsv[i] = __ldg(&lamS[is + i * sv.Sl]);
+#pragma unroll
+        for (int j = 0; j < DC_; ++j) {
+          const C ln = __ldg(&lamN[jl + j * sv.Nl]);
+#pragma unroll
+          for (int i = 0; i < DR_; ++i) lmn[i + DR_ * j] = cmul(__ldg(&lamM[g + i * sv.Ml]), ln);
+        }
+      }
       C av[D];
       int qs = 0;
       T best = (T)-1;
 #pragma unroll
       for (int q = 0; q < D; ++q) {
-        const C a_ = __ldg(&lamc[(long long)q * ncls + c]);
+        const C a_ = sv.sep ? cmul(lmn[q % (DR_ * DC_)], lsv[q / (DR_ * DC_)]) : __ldg(&lamc[(long long)q * ncls + c]);
         av[q] = a_;
         const int si = sidx(q);
         sm[si] = cmulc(a_, Yc) + sm[si] * alpha;  // B = conj(Lambda) Y + mu F Theta
@@ -325,7 +343,8 @@ __device__ __forceinline__ double solve_tile(cplx<T>* sm, int TW, int G, int a0,
         const int pm = q % dr, pn = (q / dr) % dc, ps = q / (dr * dc);
         const int ks = is + ps * sv.Sl, kn = jl + pn * sv.Nl, km = g + pm * sv.Ml;
         si[q] = (ks * G + gn * dc + pn) * TW + gm * dr + pm;
-        const C a_ = __ldg(&lamc[(long long)q * ncls + c]);
+        const C a_ = sv.sep ? cmul(cmul(__ldg(&lamM[km]), __ldg(&lamN[kn])), __ldg(&lamS[ks]))
+                            : __ldg(&lamc[(long long)q * ncls + c]);
         C B = cmulc(a_, Yc);  // conj(Lambda_p) Y: F H^H D^H y at this frequency
         T w;
         if (MODE == S_ADMM) {

@@ -653,6 +653,25 @@ __global__ void k_wrap_psf(T* out, const double* __restrict__ psf, int pm, int p
   out[((long long)s * N + n) * M + m] = (T)psf[i];
 }
 
+// 1-D DFT of one factor f (length pf, centre tap pf/2 wrapped to the origin)
+// of a separable PSF: out[k] = sum_j f[j] exp(-2 pi i k ((j - pf/2) mod n) / n),
+// in FP64 with the exact integer phase (k * j') mod n
+template <typename T>
+__global__ void k_dft_factor(cplx<T>* __restrict__ out, const double* __restrict__ f, int pf, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double re = 0.0, im = 0.0;
+  for (int j = 0; j < pf; ++j) {
+    const long long jw = ((j - pf / 2) % n + n) % n;
+    const long long w = (jw * k) % n;
+    double sn, cs;
+    sincospi(-2.0 * (double)w / (double)n, &sn, &cs);
+    re += f[j] * cs;
+    im += f[j] * sn;
+  }
+  out[k] = mkc((T)re, (T)im);
+}
+
 template <typename T>
 __global__ void k_export_half(const cplx<T>* __restrict__ spec, cplx<T>* __restrict__ out, int M, int N, int S,
                               int Ml, int Nl, int dr, int dc, int Mp) {
@@ -692,6 +711,13 @@ cudaError_t launch_wrap_psf(const Plan& p, void* out, const double* psf_dev, int
   const Geometry& g = p.hr;
   if (p.dtype) k_wrap_psf<double><<<b, 256, 0, p.stream>>>((double*)out, psf_dev, pm, pn, ps, g.M, g.N, g.S);
   else k_wrap_psf<float><<<b, 256, 0, p.stream>>>((float*)out, psf_dev, pm, pn, ps, g.M, g.N, g.S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dft_factor(const Plan& p, void* out, const double* f_dev, int pf, int n) {
+  const int b = (n + 255) / 256;
+  if (p.dtype) k_dft_factor<double><<<b, 256, 0, p.stream>>>((cplx<double>*)out, f_dev, pf, n);
+  else k_dft_factor<float><<<b, 256, 0, p.stream>>>((cplx<float>*)out, f_dev, pf, n);
   return cudaGetLastError();
 }
 
