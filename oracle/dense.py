@@ -90,16 +90,28 @@ def admm_xstep_dense(y, psf, dec, mu, rho, shape):
     return np.linalg.solve(M, rhs).reshape(shape), M, rhs
 
 
-def tv_objective_dense(x, y, A, L, lam_tv):
+def tikhonov_grad_dense(y, psf, dec, tau):
+    """Solve (H^T D^T D H + tau L^T L) x = H^T D^T y (Tikhonov on the gradient)."""
+    dr, dc, ds = dec
+    shape = (y.shape[0] * ds, y.shape[1] * dc, y.shape[2] * dr)
+    A = decimation_matrix(shape, dec) @ blur_matrix(psf, shape)
+    L = grad_matrix(shape)
+    M = A.T @ A + tau * (L.T @ L)
+    return np.linalg.solve(M, A.T @ y.ravel()).reshape(shape), M
+
+
+def tv_objective_dense(x, y, A, L, lam_tv, aniso=False):
     g = (L @ x.ravel()).reshape(3, -1)
     r = y.ravel() - A @ x.ravel()
-    return 0.5 * float(r @ r) + lam_tv * float(np.sqrt((g ** 2).sum(axis=0)).sum())
+    tv = np.abs(g).sum() if aniso else np.sqrt((g ** 2).sum(axis=0)).sum()
+    return 0.5 * float(r @ r) + lam_tv * float(tv)
 
 
-def chambolle_pock_tv(y, psf, dec, lam_tv, shape, iters=20000, x0=None):
+def chambolle_pock_tv(y, psf, dec, lam_tv, shape, iters=20000, x0=None, aniso=False):
     """Independent solver for min_x 1/2||y - DHx||^2 + lambda sum_j ||(Lx)_j||:
     primal-dual hybrid gradient (Chambolle & Pock 2011) with K = [DH; L], G = 0,
-    F(z1, z2) = 1/2||z1 - y||^2 + lambda ||z2||_{2,1}; every prox is closed form."""
+    F(z1, z2) = 1/2||z1 - y||^2 + lambda ||z2||_{2,1}; every prox is closed form.
+    aniso=True: lambda ||z2||_1 (the dual projection clips each component)."""
     A = decimation_matrix(shape, dec) @ blur_matrix(psf, shape)
     L = grad_matrix(shape)
     K = np.vstack([A, L])
@@ -115,13 +127,16 @@ def chambolle_pock_tv(y, psf, dec, lam_tv, shape, iters=20000, x0=None):
         p = p + sig * (K @ xb)
         p[:nl] = (p[:nl] - sig * yv) / (1.0 + sig)
         q = p[nl:].reshape(3, nh)
-        nrm = np.sqrt((q ** 2).sum(axis=0))
-        q /= np.maximum(1.0, nrm / lam_tv)[None]
+        if aniso:
+            q = np.clip(q, -lam_tv, lam_tv)
+        else:
+            nrm = np.sqrt((q ** 2).sum(axis=0))
+            q /= np.maximum(1.0, nrm / lam_tv)[None]
         p[nl:] = q.ravel()
         xn = x - tau * (K.T @ p)
         xb = 2.0 * xn - x
         x = xn
-    return x.reshape(shape), tv_objective_dense(x, y, A, L, lam_tv)
+    return x.reshape(shape), tv_objective_dense(x, y, A, L, lam_tv, aniso)
 
 
 # ---------------------------------------------------------------------------

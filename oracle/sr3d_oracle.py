@@ -39,7 +39,8 @@ import numpy as np
 __all__ = [
     "otf", "blur", "decimate", "zero_fill", "forward", "nearest_neighbour",
     "fold", "replicate", "tikhonov", "grad", "grad_adj", "laplacian_symbol",
-    "shrink", "admm_xstep", "admm_tv", "objective", "augmented_lagrangian",
+    "shrink", "shrink_aniso", "tv_term", "admm_xstep", "admm_tv", "objective", "augmented_lagrangian",
+    "tikhonov_grad",
     "psnr",
 ]
 
@@ -50,6 +51,12 @@ def _lr_shape(shape, dec):
     if m % dr or n % dc or s % ds:
         raise ValueError("HR sizes must be multiples of the decimation factors")
     return (s // ds, n // dc, m // dr)
+
+
+def _hr_shape(lr_shape, dec):
+    s, n, m = lr_shape
+    dr, dc, ds = dec
+    return (s * ds, n * dc, m * dr)
 
 
 # ---------------------------------------------------------------------------
@@ -189,6 +196,21 @@ def shrink(nu: np.ndarray, t: float) -> np.ndarray:
     return nu * scale[None]
 
 
+def shrink_aniso(nu: np.ndarray, t: float) -> np.ndarray:
+    """Anisotropic soft threshold: the prox of t * sum_a |nu_a| (the u-step of
+    Algorithm 1 step 5b when phi is the anisotropic TV sum_j sum_a |(D_a x)_j|,
+    one of the other regularisers the conclusion of the paper points to):
+    each component shrinks towards 0 by t, u_a = 0 where |nu_a| <= t."""
+    return np.sign(nu) * np.maximum(np.abs(nu) - t, 0.0)
+
+
+def tv_term(g: np.ndarray, aniso: bool = False) -> float:
+    """sum_j ||g_j||_2 (isotropic TV) or sum_j sum_a |g_a,j| (anisotropic)."""
+    if aniso:
+        return float(np.abs(g).sum())
+    return float(np.sqrt((g ** 2).sum(axis=0)).sum())
+
+
 def dc_class_indices(shape, dec):
     """HR frequencies aliased onto the LR zero frequency (eq. 8), member (0,0,0) first."""
     sl, nl, ml = _lr_shape(shape, dec)
@@ -226,11 +248,19 @@ def admm_xstep(y: np.ndarray, lam: np.ndarray, theta: np.ndarray, mu: float, dec
     return np.real(np.fft.ifftn(X))
 
 
-def objective(x: np.ndarray, y: np.ndarray, psf: np.ndarray, dec, lam_tv: float) -> float:
-    """1/2 ||y - DHx||^2 + lambda sum_j ||(Lx)_j||_2 (eq. 3 with the isotropic TV)."""
+def objective(x: np.ndarray, y: np.ndarray, psf: np.ndarray, dec, lam_tv: float, aniso: bool = False) -> float:
+    """1/2 ||y - DHx||^2 + lambda phi(Lx) (eq. 3), phi the isotropic TV (or the
+    anisotropic one with aniso=True)."""
     r = y - forward(x, psf, dec)
-    g = grad(x)
-    return 0.5 * float((r ** 2).sum()) + lam_tv * float(np.sqrt((g ** 2).sum(axis=0)).sum())
+    return 0.5 * float((r ** 2).sum()) + lam_tv * tv_term(grad(x), aniso)
+
+
+def tikhonov_grad(y: np.ndarray, psf: np.ndarray, dec, tau: float) -> np.ndarray:
+    """Minimiser of 1/2 ||y - DHx||^2 + tau/2 ||Lx||^2 (Tikhonov on the
+    gradient, another regulariser for the same Fourier-domain solve): its
+    normal equations (H^T D^T D H + tau L^T L) x = H^T D^T y are those of the
+    ADMM x-subproblem of Algorithm 1 step 5a with u - d = 0 and mu = tau."""
+    return admm_xstep(y, otf(psf, _hr_shape(y.shape, dec)), np.zeros(_hr_shape(y.shape, dec)), tau, dec)
 
 
 def augmented_lagrangian(x, u, dvar, y, psf, dec, lam_tv, mu) -> float:
@@ -242,14 +272,15 @@ def augmented_lagrangian(x, u, dvar, y, psf, dec, lam_tv, mu) -> float:
 
 
 def admm_tv(y: np.ndarray, psf: np.ndarray, dec, lam_tv: float, mu: float, iters: int,
-            x0: np.ndarray, d0=None, u0=None, record: bool = False, callback=None) -> dict:
+            x0: np.ndarray, d0=None, u0=None, record: bool = False, callback=None, aniso: bool = False) -> dict:
     """Algorithm 1 (3D-FSR-l2-TV) for `iters` iterations from x0.
 
     u0 defaults to L x0 and d0 to zero.  Returns x, u, d after the last
     iteration and, with record=True, per-iteration history: objective,
     primal residual ||Lx - u||, dual residual mu ||L^T (u - u_prev)||, and the
     norms ||Lx||, ||u||, mu ||L^T d|| used by relative stopping tests.
-    `callback(i, x, u, d)` is called after every iteration.
+    `callback(i, x, u, d)` is called after every iteration.  aniso=True
+    uses the anisotropic TV (shrink_aniso in the u-step, its objective).
     """
     if mu <= 0:
         raise ValueError("mu must be positive")
@@ -266,11 +297,11 @@ def admm_tv(y: np.ndarray, psf: np.ndarray, dec, lam_tv: float, mu: float, iters
         # step 5b: u from the isotropic soft threshold of nu = Lx + d
         g = grad(x)
         u_prev = u
-        u = shrink(g + dvar, lam_tv / mu)
+        u = (shrink_aniso if aniso else shrink)(g + dvar, lam_tv / mu)
         # step 5c: d = d + (Lx - u)
         dvar = dvar + (g - u)
         if record:
-            hist["objective"].append(objective(x, y, psf, dec, lam_tv))
+            hist["objective"].append(objective(x, y, psf, dec, lam_tv, aniso))
             hist["primal"].append(float(np.sqrt(((g - u) ** 2).sum())))
             hist["dual"].append(mu * float(np.sqrt((grad_adj(u - u_prev) ** 2).sum())))
             hist["norm_Lx"].append(float(np.sqrt((g ** 2).sum())))

@@ -297,3 +297,52 @@ def test_data_term_by_parseval_over_aliasing_classes():
     R = np.fft.fftn(y) - O.fold(lam * np.fft.fftn(x), dec) / np.prod(dec)
     # fold of an unnormalised HR DFT, /d, is the LR DFT of the decimated volume
     assert np.isclose(direct, (np.abs(R) ** 2).sum() / y.size)
+
+
+# ---------------------------------------------------------------------------
+# other regularisers through the same x-step
+# ---------------------------------------------------------------------------
+
+def test_shrink_aniso_is_the_prox_of_the_l1_norm():
+    """u = shrink_aniso(nu, t) satisfies 0 in u - nu + t d|u| componentwise,
+    and differs from the isotropic shrink unless one component is nonzero."""
+    rng = np.random.default_rng(21)
+    nu = rng.standard_normal((3, 50))
+    t = 0.4
+    u = O.shrink_aniso(nu, t)
+    nz = u != 0
+    assert np.allclose((u - nu + t * np.sign(u))[nz], 0.0)
+    assert np.all(np.abs(nu[~nz]) <= t)
+    one = np.zeros((3, 4))
+    one[1] = [-2.0, -0.1, 0.3, 5.0]
+    assert np.allclose(O.shrink_aniso(one, t), O.shrink(one, t))
+    assert not np.allclose(u, O.shrink(nu, t))
+
+
+def test_admm_aniso_reaches_the_primal_dual_optimum():
+    shape, dec = (4, 4, 8), (2, 2, 2)
+    psf, y, _ = _small_problem(22, shape, dec)
+    lam_tv = 0.005  # small enough that the solution is not constant
+    x0 = O.tikhonov(y, psf, dec, 0.1, O.nearest_neighbour(y, dec))
+    r = O.admm_tv(y, psf, dec, lam_tv, 0.05, 3000, x0, aniso=True)
+    assert (np.abs(O.grad(r["x"])) > 1e-6).sum() > 10
+    f_admm = O.objective(r["x"], y, psf, dec, lam_tv, aniso=True)
+    _, f_cp = D.chambolle_pock_tv(y, psf, dec, lam_tv, shape, iters=40000, aniso=True)
+    assert abs(f_admm - f_cp) <= 1e-6 * f_cp
+    # and it is a different problem from the isotropic one
+    f_iso = O.objective(O.admm_tv(y, psf, dec, lam_tv, 0.05, 3000, x0)["x"], y, psf, dec, lam_tv, aniso=True)
+    assert f_iso > f_admm * (1 + 1e-2)
+
+
+def test_tikhonov_grad_equals_dense_normal_equations():
+    rng = np.random.default_rng(23)
+    for shape, dec in [((4, 6, 8), (2, 3, 2)), ((6, 4, 4), (1, 2, 2))]:
+        psf = rand_psf(rng, (3, 3, 3))  # asymmetric: complex Lambda
+        lr = (shape[0] // dec[2], shape[1] // dec[1], shape[2] // dec[0])
+        y = rng.standard_normal(lr)
+        x = O.tikhonov_grad(y, psf, dec, 0.07)
+        xd, M = D.tikhonov_grad_dense(y, psf, dec, 0.07)
+        assert np.allclose(x, xd, atol=1e-10)
+        # the residual of the dense system, not only agreement
+        A = D.decimation_matrix(shape, dec) @ D.blur_matrix(psf, shape)
+        assert np.linalg.norm(M @ x.ravel() - A.T @ y.ravel()) <= 1e-10 * np.linalg.norm(A.T @ y.ravel())
