@@ -12,11 +12,13 @@ working set (x, two dual buffers, Theta, Lambda, spectrum: ~0.65 GB) is far
 larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload headline|batch|warmstart]
+                  [--workload headline|batch|warmstart|regularisers]
 
 --workload batch: 64 volumes of uneven size and decimation solved together;
 --workload warmstart: wall-clock to tolerance at 256^3, cold start against
-the learned U-Net warm start (parameters in paper_2010_15491_gb300/weights/).
+the learned U-Net warm start (parameters in paper_2010_15491_gb300/weights/);
+--workload regularisers: the 256^3 solve with the anisotropic TV and the
+Tikhonov-on-gradient solve, separable-PSF path on and off.
 
 One JSON line on stdout (rank 0).  Under torchrun with N > 1 every rank solves
 its own replica (the single-volume path does not shard: replicas only).
@@ -356,6 +358,60 @@ def run_batch(args, rank, world, local_rank):
         p.close()
 
 
+def run_regularisers(args, rank, world, local_rank):
+    """--workload regularisers: the 256^3 headline solve with the anisotropic
+    TV (same metric, voxel*iterations/s), and the one-shot Tikhonov-on-gradient
+    solve at 256^3 (ms per solve, LR spectrum included); separable-PSF path
+    on and off for both."""
+    import torch
+    from paper_2010_15491_gb300.build import build
+    import paper_2010_15491_gb300 as sr3d
+    from synth import HEADLINE_256 as w
+    build()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream()
+    plan = sr3d.Plan(w.dims, w.dec, w.psf(), "f32", stream=stream)
+    plan.autotune()
+    with torch.cuda.stream(stream):
+        y = make_inputs(w, plan, torch)
+        x = plan.empty_hr()
+    out = {}
+    for sep in (True, False):
+        plan.separable(sep)
+        for kind in ("isotropic", "anisotropic"):
+            plan.set_tv(kind)
+            for _ in range(max(args.warmup, 1)):
+                plan.admm_tv(y, x, w.lam, w.mu, w.iters, tau_init=w.tau)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            for _ in range(args.steps):
+                plan.admm_tv(y, x, w.lam, w.mu, w.iters, tau_init=w.tau)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            out[f"admm_{kind}_sep{int(sep)}"] = w.voxels * w.iters * args.steps / (ev0.elapsed_time(ev1) / 1e3)
+        plan.set_tv("isotropic")
+        for _ in range(3):
+            plan.tikhonov_grad(y, 1e-2, x)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(10):
+            plan.tikhonov_grad(y, 1e-2, x)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        out[f"tikhonov_grad_ms_sep{int(sep)}"] = ev0.elapsed_time(ev1) / 10
+    plan.separable(True)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "ADMM-TV voxel·iters/s at 256³, anisotropic TV", "value": out["admm_anisotropic_sep1"],
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_desc(w) + "; anisotropic TV, and Tikhonov on the gradient (tau 1e-2)"},
+            "detail": out}), flush=True)
+    plan.close()
+
+
 WEIGHTS = os.path.join(ROOT, "paper_2010_15491_gb300", "weights", "unet_warmstart.npy")
 # forward multiply-adds per HR voxel of the warm-start U-Net: ten 3x3x3 layers
 # at full, 1/8 and 1/64 voxel density, plus the 1x1x1 head
@@ -453,7 +509,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["headline", "batch", "warmstart"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "batch", "warmstart", "regularisers"], default="headline")
     args = ap.parse_args()
     from synth import HEADLINE_256 as w
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -472,6 +528,9 @@ def main():
     elif args.workload == "warmstart":
         if rank == 0:
             run_warmstart(args, rank, world, local_rank)
+    elif args.workload == "regularisers":
+        if rank == 0:
+            run_regularisers(args, rank, world, local_rank)
     else:
         run_ours(args, w, rank, world, local_rank)
     if world > 1:

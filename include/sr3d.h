@@ -290,6 +290,29 @@ int sr3d_unet_read(sr3d_unet_t net, int which, void* host, long long bytes);
  * plan.  Pass d_dev to sr3d_admm_tv together with x_dev as x0. */
 int sr3d_dual_init(sr3d_plan_t plan, const void* x_dev, double lambda, double rho, void* d_dev);
 
+/* Other regularisers through the same Fourier-domain x-update (the
+ * conclusion of the paper points to regularisation functions other than
+ * Tikhonov and TV).
+ *
+ * sr3d_set_tv selects the TV of sr3d_admm_tv (and of the batched solve) on
+ * this plan: SR3D_TV_ISOTROPIC (default, sum_j ||(Lx)_j||_2, Algorithm 1) or
+ * SR3D_TV_ANISOTROPIC (sum_j sum_a |(D_a x)_j|): the u-step of step 5b then
+ * shrinks each component separately, u_a = sign(nu_a) max(|nu_a| - lambda/rho,
+ * 0); the x-update of step 5a and the dual step are unchanged; the statistics
+ * report the matching TV term.  Errors: INVALID_ARG. */
+#define SR3D_TV_ISOTROPIC 0
+#define SR3D_TV_ANISOTROPIC 1
+int sr3d_set_tv(sr3d_plan_t plan, int kind);
+
+/* Tikhonov on the gradient: x_dev = argmin 1/2 ||y - DHx||^2 + tau/2 ||Lx||^2
+ * (L the periodic forward differences of Sec. III-B).  Its normal equations
+ * (H^T D^T D H + tau L^T L) x = H^T D^T y are those of the x-update of
+ * Algorithm 1 step 5a with u - d = 0 and mu = tau, so it is one class solve of
+ * eq. 12 with weights 1/(tau s_p) (the zero-frequency class solved exactly)
+ * and one inverse 3D FFT.  Errors: INVALID_ARG (tau <= 0, NULL arrays),
+ * SINGULAR (PSF taps sum to zero), CUDA. */
+int sr3d_tikhonov_grad(sr3d_plan_t plan, const void* y_dev, double tau, void* x_dev);
+
 /* Separable-PSF fast path.  When the PSF is an outer product of three 1-D
  * factors (a Gaussian, for instance, as in the experiments of Sec. IV), the
  * eigenvalues of eq. 2 factor as Lambda(k_m, k_n, k_s) = L_m(k_m) L_n(k_n)

@@ -32,7 +32,7 @@ EXPORTED = [
     "sr3d_plan", "sr3d_destroy", "sr3d_forward", "sr3d_tikhonov", "sr3d_admm_tv", "sr3d_admm_tv_host",
     "sr3d_last_error", "sr3d_get_otf", "sr3d_fft3", "sr3d_xstep", "sr3d_tv_step", "sr3d_plan_info",
     "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc", "sr3d_admm_tv_batched", "sr3d_autotune",
-    "sr3d_separable",
+    "sr3d_separable", "sr3d_set_tv", "sr3d_tikhonov_grad",
     "sr3d_dual_init", "sr3d_unet_param_count", "sr3d_unet_create", "sr3d_unet_destroy", "sr3d_unet_set_params",
     "sr3d_unet_get_params", "sr3d_unet_forward", "sr3d_unet_train_step", "sr3d_unet_read",
 ]
@@ -95,6 +95,8 @@ def load() -> ctypes.CDLL:
                                      ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d), i]),
         "sr3d_dual_init": (i, [vp, vp, d, d, vp]),
         "sr3d_separable": (i, [vp, i, ctypes.POINTER(i)]),
+        "sr3d_set_tv": (i, [vp, i]),
+        "sr3d_tikhonov_grad": (i, [vp, vp, d, vp]),
         "sr3d_unet_param_count": (ctypes.c_longlong, []),
         "sr3d_unet_create": (i, [ctypes.POINTER(vp), vp]),
         "sr3d_unet_destroy": (i, [vp]),
@@ -184,6 +186,16 @@ class Plan:
         out = dict(zip(keys, list(sizes)))
         out["bytes"] = b.value
         return out
+
+    def set_tv(self, kind: str):
+        """TV of admm_tv on this plan: "isotropic" (default) or "anisotropic" (sr3d_set_tv)."""
+        _check(load().sr3d_set_tv(self._h, {"isotropic": 0, "anisotropic": 1}[kind]))
+
+    def tikhonov_grad(self, y, tau: float, x=None):
+        """argmin 1/2 ||y - DHx||^2 + tau/2 ||Lx||^2 (sr3d_tikhonov_grad)."""
+        x = self.empty_hr() if x is None else x
+        _check(load().sr3d_tikhonov_grad(self._h, self._lr(y), float(tau), self._hr(x)))
+        return x
 
     def separable(self, use: Optional[bool] = None) -> bool:
         """Separable-PSF fast path (sr3d_separable): enable / disable it, or

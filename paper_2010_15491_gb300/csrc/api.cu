@@ -620,6 +620,39 @@ int sr3d_dual_init(sr3d_plan_t plan, const void* x, double lambda, double rho, v
   return sync_plan(p);
 }
 
+int sr3d_set_tv(sr3d_plan_t plan, int kind) {
+  if (!plan) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  if (kind != SR3D_TV_ISOTROPIC && kind != SR3D_TV_ANISOTROPIC)
+    return fail(SR3D_ERR_INVALID_ARG, "kind must be SR3D_TV_ISOTROPIC or SR3D_TV_ANISOTROPIC");
+  Plan& p = plan->p;
+  const bool aniso = kind == SR3D_TV_ANISOTROPIC;
+  if (aniso != p.tv_aniso) {
+    TRY(sync_plan(p));
+    p.tv_aniso = aniso;
+    if (p.iter_graph) {  // captured launches hold the other TV kernel
+      cudaGraphExecDestroy(p.iter_graph);
+      p.iter_graph = nullptr;
+    }
+    drop_eval_graphs(p);
+    ++p.version;
+  }
+  return SR3D_OK;
+}
+
+int sr3d_tikhonov_grad(sr3d_plan_t plan, const void* y, double tau, void* x) {
+  if (!plan || !y || !x) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  if (!(tau > 0) || !std::isfinite(tau)) return fail(SR3D_ERR_INVALID_ARG, "tau must be positive");
+  Plan& p = plan->p;
+  if (p.psf_sum == 0.0) return fail(SR3D_ERR_SINGULAR, "PSF taps sum to zero: the zero-frequency class is singular");
+  TRY(lr_spectrum(p, y));
+  // the ADMM x-step with Theta = 0 and mu = tau: a zero spectrum for F Theta
+  CK(cudaMemsetAsync(p.spec, 0, (size_t)p.hr.spec_elems() * 2 * p.esz, p.stream));
+  SolveArgs sv = solve_args(p, 0, tau);
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_ADMM, false, &sv));
+  TRY(hr_inverse_partial(p, x));
+  return sync_plan(p);
+}
+
 int sr3d_separable(sr3d_plan_t plan, int use, int* active) {
   if (!plan) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
   Plan& p = plan->p;

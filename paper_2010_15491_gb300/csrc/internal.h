@@ -64,6 +64,7 @@ struct Plan {
   size_t esz;    // element size
   Geometry hr, lr;
   double psf_sum;
+  bool tv_aniso = false;   // u-step and TV term of the anisotropic TV (sr3d_set_tv)
   bool sep_avail = false;  // the PSF is an outer product of three 1-D factors
   bool sep_on = true;      // use the 1-D Lambda tables in the class solve when available
   void* lamM1 = nullptr; void* lamN1 = nullptr; void* lamS1 = nullptr;  // 1-D factor DFTs (complex)

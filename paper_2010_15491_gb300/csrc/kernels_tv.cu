@@ -22,7 +22,9 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // nu = g + d, u = shrink(nu, thr), d' = nu - u and rho = u - d'; then
 // Theta = L^T rho on the tile, using rho of the previous plane (kept in a
 // register) for the s component.
-// MODE 0: ADMM step.  MODE 1: initial Theta with u = Lx and d unchanged.
+// MODE 0: ADMM step (isotropic shrink).  MODE 1: initial Theta with u = Lx
+// and d unchanged.  MODE 2: ADMM step of the anisotropic TV (componentwise
+// shrink: d' = clamp(nu, -thr, thr), u = nu - d'; TV term sum_a |g_a|).
 // STATS: per-CTA FP64 sums of ||g||, ||d'-d||^2, ||g||^2, ||u||^2,
 // (L^T u - psi)^2, (L^T d')^2; psi (= L^T u of the previous iteration) is
 // read and overwritten in place.
@@ -125,6 +127,10 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
       if (MODE == 1) {
         u0 = g0; u1 = g1; u2 = g2;
         e0 = dv[0]; e1 = dv[1]; e2 = dv[2];
+      } else if (MODE == 2) {  // anisotropic: d' = clamp(nu, -thr, thr), u = nu - d'
+        const T v0 = g0 + dv[0], v1 = g1 + dv[1], v2 = g2 + dv[2];
+        e0 = fmin(fmax(v0, -thr), thr); e1 = fmin(fmax(v1, -thr), thr); e2 = fmin(fmax(v2, -thr), thr);
+        u0 = v0 - e0; u1 = v1 - e1; u2 = v2 - e2;
       } else {
         const T v0 = g0 + dv[0], v1 = g1 + dv[1], v2 = g2 + dv[2];
         const T nrm = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
@@ -139,12 +145,12 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
         rs[0][i] = u0 - e0; rs[1][i] = u1 - e1; rs[2][i] = u2 - e2;
       }
       if (interior && own_plane) {
-        if (MODE == 0) {
+        if (MODE != 1) {
           dout[gi] = e0; dout[V + gi] = e1; dout[2 * V + gi] = e2;
         }
         if (STATS) {
           const double gg = (double)g0 * g0 + (double)g1 * g1 + (double)g2 * g2;
-          q[0] += sqrt(gg);
+          q[0] += MODE == 2 ? fabs((double)g0) + fabs((double)g1) + fabs((double)g2) : sqrt(gg);
           const double p0 = (double)e0 - dv[0], p1 = (double)e1 - dv[1], p2 = (double)e2 - dv[2];
           q[1] += p0 * p0 + p1 * p1 + p2 * p2;
           q[2] += gg;
@@ -174,7 +180,7 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
           const T psi_v = (rs[0][left] - rs[0][own]) + (rs[1][down] - rs[1][own]) + (u2prev - u2c);
           const T ltd = (rs[3][left] - rs[3][own]) + (rs[4][down] - rs[4][own]) + (d2prev - d2c);
           th = psi_v - ltd;
-          if (MODE == 0) {
+          if (MODE != 1) {
             const double dl = (double)psi_v - (double)psi[gi];
             q[4] += dl * dl;
           }
@@ -322,6 +328,10 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
       if (MODE == 1) {
         u0 = g0; u1 = g1; u2 = g2;
         e0 = d0; e1 = d1; e2 = d2;
+      } else if (MODE == 2) {  // anisotropic: d' = clamp(nu, -thr, thr), u = nu - d'
+        const float v0 = g0 + d0, v1 = g1 + d1, v2 = g2 + d2;
+        e0 = fminf(fmaxf(v0, -thr), thr); e1 = fminf(fmaxf(v1, -thr), thr); e2 = fminf(fmaxf(v2, -thr), thr);
+        u0 = v0 - e0; u1 = v1 - e1; u2 = v2 - e2;
       } else {
         const float v0 = g0 + d0, v1 = g1 + d1, v2 = g2 + d2;
         const float nrm = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
@@ -358,7 +368,7 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
         voxel(xr, mc + i, g0, g1, g2, f4(dv0, i), f4(dv1, i), f4(dv2, i), u0, u1, u2, e0v[i], e1v[i], e2v[i]);
         if (STATS && interior && own_plane) {
           const float gg = g0 * g0 + g1 * g1 + g2 * g2;
-          f0 += sqrtf(gg);
+          f0 += MODE == 2 ? fabsf(g0) + fabsf(g1) + fabsf(g2) : sqrtf(gg);
           const float p0 = e0v[i] - f4(dv0, i), p1 = e1v[i] - f4(dv1, i), p2 = e2v[i] - f4(dv2, i);
           f1 += p0 * p0 + p1 * p1 + p2 * p2;
           f2 += gg;
@@ -371,7 +381,7 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
         q[2] += f2;
         q[3] += f3;
       }
-      if (MODE == 0 && interior && own_plane) {
+      if (MODE != 1 && interior && own_plane) {
         const long long gi = pl + o_in;
         st4(dout + gi, make_float4(e0v[0], e0v[1], e0v[2], e0v[3]));
         st4(dout + V + gi, make_float4(e1v[0], e1v[1], e1v[2], e1v[3]));
@@ -434,7 +444,7 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
             f5 += ltd * ltd;
           }
           q[5] += f5;
-          if (MODE == 0) {
+          if (MODE != 1) {
             const float4 old = ld4(psi + gi);
             float f4s = 0.f;
 #pragma unroll
@@ -532,14 +542,20 @@ static cudaError_t tv4_k(const Plan& p, const void* x, const void* din, void* do
 template <typename T>
 static cudaError_t tv_t(const Plan& p, const void* x, const void* din, void* dout, void* theta, void* psi,
                         double thr, int mode, bool stats) {
+  if (mode == 0 && p.tv_aniso) mode = 2;  // the plan's TV is anisotropic
   if (tv_vec4(p)) {
     if (mode == 0)
       return stats ? tv4_k<0, true>(p, x, din, dout, theta, psi, thr) : tv4_k<0, false>(p, x, din, dout, theta, psi, thr);
+    if (mode == 2)
+      return stats ? tv4_k<2, true>(p, x, din, dout, theta, psi, thr) : tv4_k<2, false>(p, x, din, dout, theta, psi, thr);
     return stats ? tv4_k<1, true>(p, x, din, dout, theta, psi, thr) : tv4_k<1, false>(p, x, din, dout, theta, psi, thr);
   }
   if (mode == 0)
     return stats ? tv_k<T, 0, true>(p, x, din, dout, theta, psi, thr)
                  : tv_k<T, 0, false>(p, x, din, dout, theta, psi, thr);
+  if (mode == 2)
+    return stats ? tv_k<T, 2, true>(p, x, din, dout, theta, psi, thr)
+                 : tv_k<T, 2, false>(p, x, din, dout, theta, psi, thr);
   return stats ? tv_k<T, 1, true>(p, x, din, dout, theta, psi, thr)
                : tv_k<T, 1, false>(p, x, din, dout, theta, psi, thr);
 }

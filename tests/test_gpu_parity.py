@@ -333,3 +333,58 @@ def test_separable_psf_path(lib, dtype):
     plan = lib.Plan(dims, dec, psf_ns / psf_ns.sum(), dtype)
     assert not plan.separable()
     plan.close()
+
+
+# ---------------------------------------------------------------------------
+# other regularisers through the same x-update
+# ---------------------------------------------------------------------------
+
+def test_tikhonov_grad(case, tag):
+    y, psf, dec, dt = case["y"], case["psf"], case["dec"], case["dtype"]
+    for tau in (3e-2, 0.7):
+        x = case["plan"].tikhonov_grad(T(y, dt), tau)
+        ref = O.tikhonov_grad(y, psf, dec, tau)
+        assert rel_l2(H(x), ref, tag(f"x_tau{tau}")) < TOL[dt]
+
+
+def test_admm_anisotropic_tv_iterates(case, tag):
+    import torch
+    y, psf, dec, dt = case["y"], case["psf"], case["dec"], case["dtype"]
+    plan = case["plan"]
+    lam, mu, tau0, iters = 1e-3, 1e-2, 1e-2, 10
+    x0 = O.tikhonov(y, psf, dec, tau0, O.nearest_neighbour(y, dec))
+    ref = O.admm_tv(y, psf, dec, lam, mu, iters, x0, record=True, aniso=True)
+    plan.set_tv("anisotropic")
+    try:
+        x = T(np.zeros_like(x0), dt)
+        d = torch.zeros((3,) + x0.shape, dtype=x.dtype, device="cuda")
+        st = plan.admm_tv(T(y, dt), x, lam, mu, iters, d=d, tau_init=tau0, eval_every=1, hist_len=iters)
+    finally:
+        plan.set_tv("isotropic")
+    assert rel_l2(H(x), ref["x"], tag("x")) < TOL[dt]
+    assert rel_l2(H(d), ref["d"], tag("d")) < (TOL[dt] * 10 if dt == "f32" else TOL[dt])
+    assert np.allclose(st["objective_hist"], ref["hist"]["objective"], rtol=TOL[dt] * 10, atol=0)
+    assert np.isclose(st["primal"], ref["hist"]["primal"][-1], rtol=1e-4)
+
+
+def test_switching_the_tv_recaptures_the_loop_graphs(lib):
+    """Fixed-iteration solves replay a cached graph; switching the TV must
+    re-capture it: isotropic, anisotropic, isotropic again with the same
+    buffers gives the first result bit for bit and a different second one."""
+    dims, dec = (128, 32, 16), (2, 2, 2)
+    psf, xt, y = make_problem(dims, dec, seed=91)
+    plan = lib.Plan(dims, dec, psf, "f32")
+    yd = T(y, "f32")
+    x = plan.empty_hr()
+    outs = []
+    for kind in ("isotropic", "anisotropic", "isotropic"):
+        plan.set_tv(kind)
+        plan.admm_tv(yd, x, 3e-3, 1e-2, 9, tau_init=1e-2)
+        outs.append(x.clone())
+    import torch
+    assert torch.equal(outs[0], outs[2])
+    assert not torch.equal(outs[0], outs[1])
+    x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
+    ref = O.admm_tv(y, psf, dec, 3e-3, 1e-2, 9, x0, aniso=True)
+    assert rel_l2(H(outs[1]), ref["x"]) < TOL["f32"]
+    plan.close()
