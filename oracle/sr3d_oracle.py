@@ -40,7 +40,7 @@ __all__ = [
     "otf", "blur", "decimate", "zero_fill", "forward", "nearest_neighbour",
     "fold", "replicate", "tikhonov", "grad", "grad_adj", "laplacian_symbol",
     "shrink", "shrink_aniso", "tv_term", "admm_xstep", "admm_tv", "objective", "augmented_lagrangian",
-    "tikhonov_grad",
+    "tikhonov_grad", "tikhonov_cg",
     "psnr",
 ]
 
@@ -269,6 +269,41 @@ def augmented_lagrangian(x, u, dvar, y, psf, dec, lam_tv, mu) -> float:
     tv = float(np.sqrt((u ** 2).sum(axis=0)).sum())
     c = grad(x) - (u - dvar)
     return 0.5 * float((r ** 2).sum()) + lam_tv * tv + 0.5 * mu * float((c ** 2).sum())
+
+
+def tikhonov_cg(y: np.ndarray, psf: np.ndarray, dec, tau: float, xbar=None, iters: int = 100,
+                tol: float = 0.0) -> dict:
+    """The iterative comparator of Sec. IV (Table 1 solves eq. 5 both by eq. 12
+    and iteratively): conjugate gradients on the normal equations of eq. 6,
+    (H^T D^T D H + tau I) x = H^T D^T y + tau xbar, from x = 0.  Every operator
+    application is spatial: H by its DFT diagonalisation (eq. 2), D^T D as the
+    sampling mask.  Stops after `iters` iterations or when ||r|| <= tol ||b||.
+    Returns x, the iterations run and the residual norms ||r_k||."""
+    lam = otf(psf, _hr_shape(y.shape, dec))
+    H = lambda v: np.real(np.fft.ifftn(lam * np.fft.fftn(v)))  # noqa: E731
+    Ht = lambda v: np.real(np.fft.ifftn(np.conj(lam) * np.fft.fftn(v)))  # noqa: E731
+    A = lambda v: Ht(zero_fill(decimate(H(v), dec), dec)) + tau * v  # noqa: E731
+    b = Ht(zero_fill(y, dec))
+    if xbar is not None:
+        b = b + tau * xbar
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = float((r * r).sum())
+    bnorm = np.sqrt(float((b * b).sum()))
+    res = [np.sqrt(rr)]
+    k = 0
+    while k < iters and not (tol > 0 and np.sqrt(rr) <= tol * bnorm):
+        Ap = A(p)
+        alpha = rr / float((p * Ap).sum())
+        x = x + alpha * p
+        r = r - alpha * Ap
+        rr_new = float((r * r).sum())
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        res.append(np.sqrt(rr))
+        k += 1
+    return {"x": x, "iters": k, "residuals": res}
 
 
 def admm_tv(y: np.ndarray, psf: np.ndarray, dec, lam_tv: float, mu: float, iters: int,

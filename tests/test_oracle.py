@@ -346,3 +346,43 @@ def test_tikhonov_grad_equals_dense_normal_equations():
         # the residual of the dense system, not only agreement
         A = D.decimation_matrix(shape, dec) @ D.blur_matrix(psf, shape)
         assert np.linalg.norm(M @ x.ravel() - A.T @ y.ravel()) <= 1e-10 * np.linalg.norm(A.T @ y.ravel())
+
+
+# ---------------------------------------------------------------------------
+# the iterative comparator (conjugate gradients on eq. 6)
+# ---------------------------------------------------------------------------
+
+def _cg_problem(seed):
+    rng = np.random.default_rng(seed)
+    shape, dec = (4, 6, 8), (2, 3, 2)
+    psf = rand_psf(rng, (3, 3, 3))
+    y = rng.standard_normal((2, 2, 4))
+    xbar = rng.standard_normal(shape)
+    return shape, dec, psf, y, xbar
+
+
+def test_cg_first_step_is_the_steepest_descent_step():
+    """From x = 0: x_1 = (b.b / b.Ab) b (textbook closed form)."""
+    shape, dec, psf, y, xbar = _cg_problem(31)
+    tau = 0.3
+    x1 = O.tikhonov_cg(y, psf, dec, tau, xbar, iters=1)["x"]
+    _, M, rhs = D.tikhonov_dense(y, psf, dec, tau, xbar)
+    alpha = (rhs @ rhs) / (rhs @ (M @ rhs))
+    assert np.allclose(x1.ravel(), alpha * rhs, rtol=1e-12, atol=1e-14)
+
+
+def test_cg_converges_to_the_dense_solution_and_error_decreases():
+    shape, dec, psf, y, xbar = _cg_problem(32)
+    tau = 0.05
+    xd, M, _ = D.tikhonov_dense(y, psf, dec, tau, xbar)
+    errs = []
+    for k in (2, 5, 10, 20, 40):
+        xk = O.tikhonov_cg(y, psf, dec, tau, xbar, iters=k)["x"]
+        e = (xk - xd).ravel()
+        errs.append(float(e @ (M @ e)))  # A-norm error: non-increasing in k
+    assert all(b <= a * (1 + 1e-9) for a, b in zip(errs, errs[1:]))
+    r = O.tikhonov_cg(y, psf, dec, tau, xbar, iters=500, tol=1e-13)
+    assert r["iters"] < 500
+    assert np.allclose(r["x"], xd, atol=1e-10)
+    # and it matches the closed form of eq. 12 used by the fast path
+    assert np.allclose(r["x"], O.tikhonov(y, psf, dec, tau, xbar), atol=1e-10)
