@@ -12,13 +12,14 @@ working set (x, two dual buffers, Theta, Lambda, spectrum: ~0.65 GB) is far
 larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload headline|batch|warmstart|regularisers]
+                  [--workload headline|batch|warmstart|regularisers|comparator]
 
 --workload batch: 64 volumes of uneven size and decimation solved together;
 --workload warmstart: wall-clock to tolerance at 256^3, cold start against
 the learned U-Net warm start (parameters in paper_2010_15491_gb300/weights/);
 --workload regularisers: the 256^3 solve with the anisotropic TV and the
-Tikhonov-on-gradient solve, separable-PSF path on and off.
+Tikhonov-on-gradient solve, separable-PSF path on and off; --workload
+comparator: the closed form of eq. 12 against conjugate gradients on eq. 6.
 
 One JSON line on stdout (rank 0).  Under torchrun with N > 1 every rank solves
 its own replica (the single-volume path does not shard: replicas only).
@@ -412,6 +413,52 @@ def run_regularisers(args, rank, world, local_rank):
     plan.close()
 
 
+def run_comparator(args, rank, world, local_rank):
+    """--workload comparator: the Tikhonov problem of eq. 5 at 256^3 (tau 1e-2,
+    nearest-neighbour prior) solved by the closed form of eq. 12 and by the
+    iterative comparator (conjugate gradients on eq. 6 to ||r|| <= 1e-5 ||b||),
+    both on the GPU with the same FFT passes: the Table 1 comparison."""
+    import torch
+    from paper_2010_15491_gb300.build import build
+    import paper_2010_15491_gb300 as sr3d
+    from synth import HEADLINE_256 as w
+    build()
+    torch.cuda.set_device(local_rank)
+    stream = torch.cuda.Stream()
+    plan = sr3d.Plan(w.dims, w.dec, w.psf(), "f32", stream=stream)
+    plan.autotune()
+    with torch.cuda.stream(stream):
+        y = make_inputs(w, plan, torch)
+        x = plan.empty_hr()
+        xc = plan.empty_hr()
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 1)):
+            out = fn()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return out, ev0.elapsed_time(ev1) / reps
+
+    _, t_closed = timed(lambda: plan.tikhonov(y, w.tau, x, xbar="nearest"), max(args.steps, 5))
+    (xcg, iters, rel, ok), t_cg = timed(
+        lambda: plan.tikhonov_cg(y, w.tau, xbar="nearest", tol=1e-5, max_iters=5000, x=xc), max(args.steps // 2, 1))
+    diff = float(torch.linalg.vector_norm(xcg - x) / torch.linalg.vector_norm(x))
+    if rank == 0:
+        print(json.dumps({
+            "metric": "closed-form Tikhonov (eq. 12) speed-up over CG on eq. 6 at 256³", "value": t_cg / t_closed,
+            "unit": "x", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{w.name}: Tikhonov tau {w.tau:g}, nearest-neighbour prior; CG to 1e-5"},
+            "closed_form_ms": t_closed, "cg_ms": t_cg, "cg_iters": iters, "cg_relres": rel, "cg_converged": ok,
+            "rel_l2_cg_vs_closed_form": diff}), flush=True)
+    plan.close()
+
+
 WEIGHTS = os.path.join(ROOT, "paper_2010_15491_gb300", "weights", "unet_warmstart.npy")
 # forward multiply-adds per HR voxel of the warm-start U-Net: ten 3x3x3 layers
 # at full, 1/8 and 1/64 voxel density, plus the 1x1x1 head
@@ -509,7 +556,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["headline", "batch", "warmstart", "regularisers"], default="headline")
+    ap.add_argument("--workload", choices=["headline", "batch", "warmstart", "regularisers", "comparator"],
+                    default="headline")
     args = ap.parse_args()
     from synth import HEADLINE_256 as w
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -531,6 +579,9 @@ def main():
     elif args.workload == "regularisers":
         if rank == 0:
             run_regularisers(args, rank, world, local_rank)
+    elif args.workload == "comparator":
+        if rank == 0:
+            run_comparator(args, rank, world, local_rank)
     else:
         run_ours(args, w, rank, world, local_rank)
     if world > 1:

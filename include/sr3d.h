@@ -313,6 +313,20 @@ int sr3d_set_tv(sr3d_plan_t plan, int kind);
  * SINGULAR (PSF taps sum to zero), CUDA. */
 int sr3d_tikhonov_grad(sr3d_plan_t plan, const void* y_dev, double tau, void* x_dev);
 
+/* The iterative comparator of Sec. IV: Table 1 solves eq. 5 both by the
+ * closed form of eq. 12 and iteratively.  This entry solves the same problem
+ * as sr3d_tikhonov (tau, xbar as there: NULL, SR3D_XBAR_NEAREST or a device
+ * HR array not aliasing x) by conjugate gradients on the normal equations of
+ * eq. 6, (H^T D^T D H + tau I) x = H^T D^T y + tau xbar, from x = 0: every
+ * iteration applies H, the sampling mask D^T D and H^T through two 3D FFT
+ * round trips of the library's FFT passes, with FP64 inner products.  Stops
+ * after max_iters iterations or when ||r|| <= tol ||b|| (tol <= 0: exactly
+ * max_iters).  *iters and *relres (if not NULL) receive the iterations run and
+ * ||r|| / ||b||.  Errors: INVALID_ARG, NUMERIC, NOT_CONVERGED (tol > 0, x
+ * still written), CUDA. */
+int sr3d_tikhonov_cg(sr3d_plan_t plan, const void* y_dev, const void* xbar_dev, double tau, double tol,
+                     int max_iters, void* x_dev, int* iters, double* relres);
+
 /* Separable-PSF fast path.  When the PSF is an outer product of three 1-D
  * factors (a Gaussian, for instance, as in the experiments of Sec. IV), the
  * eigenvalues of eq. 2 factor as Lambda(k_m, k_n, k_s) = L_m(k_m) L_n(k_n)

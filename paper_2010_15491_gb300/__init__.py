@@ -32,7 +32,7 @@ EXPORTED = [
     "sr3d_plan", "sr3d_destroy", "sr3d_forward", "sr3d_tikhonov", "sr3d_admm_tv", "sr3d_admm_tv_host",
     "sr3d_last_error", "sr3d_get_otf", "sr3d_fft3", "sr3d_xstep", "sr3d_tv_step", "sr3d_plan_info",
     "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc", "sr3d_admm_tv_batched", "sr3d_autotune",
-    "sr3d_separable", "sr3d_set_tv", "sr3d_tikhonov_grad",
+    "sr3d_separable", "sr3d_set_tv", "sr3d_tikhonov_grad", "sr3d_tikhonov_cg",
     "sr3d_dual_init", "sr3d_unet_param_count", "sr3d_unet_create", "sr3d_unet_destroy", "sr3d_unet_set_params",
     "sr3d_unet_get_params", "sr3d_unet_forward", "sr3d_unet_train_step", "sr3d_unet_read",
 ]
@@ -97,6 +97,7 @@ def load() -> ctypes.CDLL:
         "sr3d_separable": (i, [vp, i, ctypes.POINTER(i)]),
         "sr3d_set_tv": (i, [vp, i]),
         "sr3d_tikhonov_grad": (i, [vp, vp, d, vp]),
+        "sr3d_tikhonov_cg": (i, [vp, vp, vp, d, d, i, vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
         "sr3d_unet_param_count": (ctypes.c_longlong, []),
         "sr3d_unet_create": (i, [ctypes.POINTER(vp), vp]),
         "sr3d_unet_destroy": (i, [vp]),
@@ -196,6 +197,23 @@ class Plan:
         x = self.empty_hr() if x is None else x
         _check(load().sr3d_tikhonov_grad(self._h, self._lr(y), float(tau), self._hr(x)))
         return x
+
+    def tikhonov_cg(self, y, tau: float, xbar=None, tol: float = 0.0, max_iters: int = 100, x=None):
+        """eq. (5) solved iteratively by conjugate gradients (sr3d_tikhonov_cg);
+        returns (x, iterations, ||r|| / ||b||, converged)."""
+        x = self.empty_hr() if x is None else x
+        if isinstance(xbar, str):
+            if xbar != "nearest":
+                raise ValueError("xbar must be None, 'nearest' or a tensor")
+            xb = XBAR_NEAREST
+        else:
+            xb = self._hr(xbar) if xbar is not None else None
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        rc = load().sr3d_tikhonov_cg(self._h, self._lr(y), xb, float(tau), float(tol), int(max_iters),
+                                     self._hr(x), ctypes.byref(it), ctypes.byref(rel))
+        _check(rc, allow=(-9,))
+        return x, it.value, rel.value, rc == SR3D_OK
 
     def separable(self, use: Optional[bool] = None) -> bool:
         """Separable-PSF fast path (sr3d_separable): enable / disable it, or

@@ -179,7 +179,8 @@ static void free_plan(Plan& p) {
   void* bufs[] = {p.twM, p.twN, p.twS, p.twMl, p.twNl, p.twSl, p.symM, p.symN, p.symS, p.lam, p.lam_solve,
                   p.yhat_solve, p.yhat, p.spec,
                   p.theta, p.dbuf[0], p.dbuf[1], p.psi, p.xh, p.yh, p.partial, p.partial_s, p.result, p.hist,
-                  p.lamM1, p.lamN1, p.lamS1};
+                  p.lamM1, p.lamN1, p.lamS1, p.cg_buf[0], p.cg_buf[1], p.cg_buf[2], p.cg_buf[3],
+                  p.cg_partial, p.cg_scal};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p.iter_graph) cudaGraphExecDestroy(p.iter_graph);
@@ -243,6 +244,7 @@ static SolveArgs solve_args(const Plan& p, int mode_alpha_nn, double alpha) {
   sv.partial = p.partial_s;
   sv.lamM = p.lamM1; sv.lamN = p.lamN1; sv.lamS = p.lamS1;
   sv.sep = (p.sep_avail && p.sep_on) ? 1 : 0;
+  sv.lam_nat = p.lam;
   return sv;
 }
 
@@ -651,6 +653,76 @@ int sr3d_tikhonov_grad(sr3d_plan_t plan, const void* y, double tau, void* x) {
   LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_ADMM, false, &sv));
   TRY(hr_inverse_partial(p, x));
   return sync_plan(p);
+}
+
+// w = H^T D^T D H v through two FFT round trips (Lambda, then conj(Lambda))
+static int apply_normal(Plan& p, const void* v, void* w, void* tmp) {
+  SolveArgs sv = solve_args(p, 0, 1.0);
+  TRY(hr_forward_partial(p, v));
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_MUL, false, &sv));
+  TRY(hr_inverse_partial(p, tmp));
+  LAUNCH(SR3D_K_OTHER, launch_mask_lattice(p, tmp));
+  TRY(hr_forward_partial(p, tmp));
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_MULC, false, &sv));
+  return hr_inverse_partial(p, w);
+}
+
+static int read_scalar(Plan& p, int slot, double* out) {
+  CK(cudaMemcpyAsync(out, p.cg_scal + slot, sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+  return sync_plan(p);
+}
+
+int sr3d_tikhonov_cg(sr3d_plan_t plan, const void* y, const void* xbar, double tau, double tol, int max_iters,
+                     void* x, int* iters, double* relres) {
+  if (!plan || !y || !x) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  if (!(tau > 0) || !std::isfinite(tau) || max_iters < 0)
+    return fail(SR3D_ERR_INVALID_ARG, "need tau > 0 and max_iters >= 0");
+  if (xbar == x) return fail(SR3D_ERR_INVALID_ARG, "x and xbar must differ");
+  Plan& p = plan->p;
+  const size_t vb = (size_t)p.hr.V() * p.esz;
+  for (auto& b : p.cg_buf)
+    if (!b) TRY(dmalloc(p, &b, vb));
+  if (!p.cg_partial) TRY(dmalloc(p, (void**)&p.cg_partial, CG_BLOCKS * sizeof(double)));
+  if (!p.cg_scal) TRY(dmalloc(p, (void**)&p.cg_scal, 8 * sizeof(double)));
+  void* r = p.cg_buf[0];
+  void* pv = p.cg_buf[1];
+  void* w = p.cg_buf[2];
+  void* tmp = p.cg_buf[3];
+  // b = H^T D^T y + tau xbar
+  SolveArgs sv = solve_args(p, 0, 1.0);
+  LAUNCH(SR3D_K_OTHER, launch_zero_fill(p, y, tmp));
+  TRY(hr_forward_partial(p, tmp));
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_MULC, false, &sv));
+  TRY(hr_inverse_partial(p, w));
+  const void* xb = nullptr;
+  if (xbar == SR3D_XBAR_NEAREST) {
+    LAUNCH(SR3D_K_OTHER, launch_nn_replicate(p, y, tmp));
+    xb = tmp;
+  } else if (xbar) {
+    xb = xbar;
+  }
+  LAUNCH(SR3D_K_OTHER, launch_cg_init(p, w, xb, tau, x, r, pv));
+  LAUNCH(SR3D_K_OTHER, launch_cg_reduce(p, 2, -1, 0));  // r.r
+  double rr = 0;
+  TRY(read_scalar(p, 2, &rr));
+  const double bb = rr;
+  int k = 0;
+  while (k < max_iters && !(tol > 0 && rr <= tol * tol * bb)) {
+    TRY(apply_normal(p, pv, w, tmp));
+    LAUNCH(SR3D_K_OTHER, launch_cg_ap(p, w, pv, tau));         // w = A p; p.Ap
+    LAUNCH(SR3D_K_OTHER, launch_cg_reduce(p, 1, 2, 0));        // rr <- rr_new, pAp
+    LAUNCH(SR3D_K_OTHER, launch_cg_update(p, x, r, pv, w));    // x, r; r.r
+    LAUNCH(SR3D_K_OTHER, launch_cg_reduce(p, 2, -1, 0));       // rr_new
+    LAUNCH(SR3D_K_OTHER, launch_cg_dir(p, r, pv));             // p
+    ++k;
+    if (tol > 0) TRY(read_scalar(p, 2, &rr));
+  }
+  TRY(read_scalar(p, 2, &rr));
+  if (!std::isfinite(rr)) return fail(SR3D_ERR_NUMERIC, "NaN/Inf in the CG residual");
+  if (iters) *iters = k;
+  if (relres) *relres = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+  if (tol > 0 && rr > tol * tol * bb) return fail(SR3D_ERR_NOT_CONVERGED, "max_iters=%d reached before tol=%g", max_iters, tol);
+  return SR3D_OK;
 }
 
 int sr3d_separable(sr3d_plan_t plan, int use, int* active) {

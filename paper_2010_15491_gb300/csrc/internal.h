@@ -17,6 +17,8 @@ enum SMode {
   S_TIK_USER = 3,  // Tikhonov with a user prior: forward, B = conj(L) Y + tau Xbar, solve, inverse
   S_ADMM = 4,      // ADMM x-update: forward, B = conj(L) Y + mu Theta^, Gamma-weighted solve, inverse
   S_FOLD = 5,      // forward, then (1/d) sum_p L_p X_p per class into the LR spectrum
+  S_MUL = 6,       // forward, X *= Lambda (natural layout or separable tables), inverse
+  S_MULC = 7,      // forward, X *= conj(Lambda), inverse
 };
 
 // Arguments of the per-aliasing-class solve inside the s pass.
@@ -43,6 +45,7 @@ struct SolveArgs {
   const void* lamN;
   const void* lamS;
   int sep;
+  const void* lam_nat;  // Lambda in the natural spectral layout (S_MUL, S_MULC)
 };
 
 struct Geometry {
@@ -121,6 +124,11 @@ struct Plan {
   int eg_every = 0;
   long long eg_launches[2][8] = {};
   int* hcount = nullptr;       // device: objective-history entries written by graph replays
+  // conjugate-gradient comparator (sr3d_tikhonov_cg): r, p, Ap, a temporary,
+  // per-CTA FP64 partial sums and the scalars rr, pAp, rr_new
+  void* cg_buf[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* cg_partial = nullptr;
+  double* cg_scal = nullptr;
   double* res_host = nullptr;  // pinned host copy of the finalize results
 };
 
@@ -151,6 +159,16 @@ cudaError_t launch_wrap_psf(const Plan& p, void* out, const double* psf_dev, int
 cudaError_t launch_export_half(const Plan& p, const void* spec, void* out);
 
 cudaError_t launch_dft_factor(const Plan& p, void* out, const double* f_dev, int pf, int n);
+// conjugate-gradient comparator (kernels_cg.cu)
+constexpr int CG_BLOCKS = 1024;
+cudaError_t launch_zero_fill(const Plan& p, const void* y, void* z);
+cudaError_t launch_nn_replicate(const Plan& p, const void* y, void* xb);
+cudaError_t launch_mask_lattice(const Plan& p, void* v);
+cudaError_t launch_cg_init(const Plan& p, const void* hty, const void* xbar, double tau, void* x, void* r, void* pv);
+cudaError_t launch_cg_ap(const Plan& p, void* w_ap, const void* pv, double tau);
+cudaError_t launch_cg_update(const Plan& p, void* x, void* r, const void* pv, const void* ap);
+cudaError_t launch_cg_dir(const Plan& p, const void* r, void* pv);
+cudaError_t launch_cg_reduce(const Plan& p, int slot, int copy_from, int copy_to);
 // KKT-consistent initial dual from x (unet.cu)
 cudaError_t launch_dual_init(const Plan& p, const void* x, double thr, void* d);
 // sets the calling thread's last-error text (api.cu) and returns code

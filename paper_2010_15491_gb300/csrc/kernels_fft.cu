@@ -452,7 +452,31 @@ __global__ void __launch_bounds__(NC > 0 ? 256 : 512, NC > 0 ? 3 : 1) k_fft_s(cp
     else fft_line_gs<T, EMAX>(ld, line, rowlen, a.f, tl, tpl, twS, 1);
   }
 
-  if (MODE >= S_TIK_GEN) {
+  if (MODE == S_MUL || MODE == S_MULC) {
+    // multiply every frequency of the tile by Lambda (or its conjugate)
+    __syncthreads();
+    const C* __restrict__ lamn = reinterpret_cast<const C*>(sv.lam_nat);
+    const C* __restrict__ lamM = reinterpret_cast<const C*>(sv.lamM);
+    const C* __restrict__ lamN = reinterpret_cast<const C*>(sv.lamN);
+    const C* __restrict__ lamS = reinterpret_cast<const C*>(sv.lamS);
+    for (int i = tid; i < S * rowlen; i += nthr) {
+      const int ks = i / rowlen, rem = i - ks * rowlen, r = rem / TW, c = rem - r * TW;
+      if (c >= tv) continue;
+      const int n = b0 / ndc + r / ndc + (r % ndc) * nNl;
+      const int slot = a0 + c;
+      C lv;
+      if (sv.sep) {
+        const int km = (slot / sv.dr) + (slot % sv.dr) * sv.Ml;  // slot g*dr + p holds frequency g + p*Ml
+        lv = cmul(cmul(__ldg(&lamM[km]), __ldg(&lamN[n])), __ldg(&lamS[ks]));
+      } else {
+        lv = __ldg(&lamn[((long long)ks * Nn + n) * Mp + slot]);
+      }
+      const C X = MODE == S_MUL ? cmul(sm[i], lv) : cmulc(lv, sm[i]);
+      sm[i] = conjc(X);  // conjugated: the inverse runs through the forward engine
+    }
+    __syncthreads();
+  }
+  if (MODE >= S_TIK_GEN && MODE <= S_FOLD) {
     double acc = solve_tile<T, MODE, STATS, DR_, DC_, DS_>(sm, TW, G, a0, b0, Ms, sv, tid, nthr);
     if (STATS) {
       __shared__ double red[32];
@@ -639,6 +663,15 @@ static cudaError_t fft_s_e(const Plan& p, const Geometry& g, void* spec, const v
       return stats ? fft_s_k<T, EMAX, S_ADMM, true, 0>(p, g, spec, tw, sv)
                    : fft_s_k<T, EMAX, S_ADMM, false, 0>(p, g, spec, tw, sv);
     case S_FOLD: return fft_s_k<T, EMAX, S_FOLD, false, 0>(p, g, spec, tw, sv);
+    case S_MUL:
+    case S_MULC:
+      if constexpr (sizeof(T) == 4 && EMAX == 16) {
+        if (ct_len<T>(g.S, g.fs) == 256 && g.tw_s * g.g_s * (256 / 16) <= 256)
+          return mode == S_MUL ? fft_s_k<T, EMAX, S_MUL, false, 256>(p, g, spec, tw, sv)
+                               : fft_s_k<T, EMAX, S_MULC, false, 256>(p, g, spec, tw, sv);
+      }
+      return mode == S_MUL ? fft_s_k<T, EMAX, S_MUL, false, 0>(p, g, spec, tw, sv)
+                           : fft_s_k<T, EMAX, S_MULC, false, 0>(p, g, spec, tw, sv);
   }
   return cudaErrorInvalidValue;
 }

@@ -388,3 +388,39 @@ def test_switching_the_tv_recaptures_the_loop_graphs(lib):
     ref = O.admm_tv(y, psf, dec, 3e-3, 1e-2, 9, x0, aniso=True)
     assert rel_l2(H(outs[1]), ref["x"]) < TOL["f32"]
     plan.close()
+
+
+# ---------------------------------------------------------------------------
+# the iterative comparator (conjugate gradients on eq. 6)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prior", ["zero", "nearest", "user"])
+def test_cg_iterates_match_oracle(case, tag, prior):
+    y, psf, dec, dt = case["y"], case["psf"], case["dec"], case["dtype"]
+    plan = case["plan"]
+    tau, iters = 2e-2, 8
+    xbar_np = {"zero": None, "nearest": O.nearest_neighbour(y, dec), "user": case["x"] * 0.5}[prior]
+    xbar = {"zero": None, "nearest": "nearest", "user": T(case["x"] * 0.5, dt)}[prior]
+    x, k, rel, ok = plan.tikhonov_cg(T(y, dt), tau, xbar=xbar, max_iters=iters)
+    ref = O.tikhonov_cg(y, psf, dec, tau, xbar_np, iters=iters)
+    assert k == iters and ok
+    assert rel_l2(H(x), ref["x"], tag("x")) < (1e-4 if dt == "f32" else 1e-10)
+    assert np.isclose(rel, ref["residuals"][-1] / ref["residuals"][0], rtol=1e-2 if dt == "f32" else 1e-8)
+
+
+@pytest.mark.parametrize("dtype,tol,agree", [("f64", 1e-9, 1e-7), ("f32", 1e-5, 2e-4)])
+def test_cg_converges_to_the_closed_form(lib, dtype, tol, agree):
+    """Run to tolerance, the comparator reaches the solution of eq. 12."""
+    dims, dec = (64, 32, 16), (2, 2, 2)
+    psf, xt, y = make_problem(dims, dec, seed=95)
+    plan = lib.Plan(dims, dec, psf, dtype)
+    yd = T(y, dtype)
+    x, k, rel, ok = plan.tikhonov_cg(yd, 1e-2, xbar="nearest", tol=tol, max_iters=2000)
+    assert ok and rel <= tol and 1 < k < 2000
+    closed = plan.tikhonov(yd, 1e-2, xbar="nearest")
+    ref = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
+    assert rel_l2(H(x), ref) < agree
+    assert rel_l2(H(x), H(closed)) < agree
+    _, k, rel, ok = plan.tikhonov_cg(yd, 1e-2, tol=1e-30, max_iters=3)  # NOT_CONVERGED: x still written
+    assert not ok and k == 3 and rel > 1e-30
+    plan.close()
