@@ -273,6 +273,21 @@ int sr3d_unet_forward(sr3d_unet_t net, int m, int n, int s, const float* x_dev, 
 int sr3d_unet_train_step(sr3d_unet_t net, int m, int n, int s, const float* x_dev, const float* target_dev,
                          double lr, double* loss, float* grad_host, int update);
 
+/* Kernel path of the 3x3x3 convolutions.  The tcgen05 kernel (5th-generation
+ * tensor cores: tcgen05.mma with TMEM accumulators, one thread issuing, a
+ * persistent CTA per row marching over s) takes levels whose m extent is a
+ * multiple of 128 with 16, 32 or 48 input and output channels; the mma.sync
+ * kernel takes every shape.  SR3D_UNET_PATH_TCGEN05 (default): tcgen05 for
+ * the shapes where it is the faster one (16 -> 16 channels), mma.sync for the
+ * rest; SR3D_UNET_PATH_MMA: mma.sync everywhere; SR3D_UNET_PATH_TCGEN05_ALL:
+ * tcgen05 wherever it applies.  All compute the same convolution with FP32
+ * accumulation (the order of the sums differs).  A tcgen05 wait that runs out
+ * (about one second) makes the calling entry point return SR3D_ERR_TIMEOUT. */
+#define SR3D_UNET_PATH_TCGEN05 0
+#define SR3D_UNET_PATH_MMA 1
+#define SR3D_UNET_PATH_TCGEN05_ALL 2
+int sr3d_unet_set_path(sr3d_unet_t net, int path);
+
 /* Copies an activation of the last forward pass (sr3d_unet_forward or
  * sr3d_unet_train_step) to host memory, for inspection and layer-by-layer
  * tests: which = 0 x, 1 e1a, 2 e1, 3 maxpool(e1), 4 e2a, 5 e2,

@@ -34,7 +34,7 @@ EXPORTED = [
     "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc", "sr3d_admm_tv_batched", "sr3d_autotune",
     "sr3d_separable", "sr3d_set_tv", "sr3d_tikhonov_grad", "sr3d_tikhonov_cg",
     "sr3d_dual_init", "sr3d_unet_param_count", "sr3d_unet_create", "sr3d_unet_destroy", "sr3d_unet_set_params",
-    "sr3d_unet_get_params", "sr3d_unet_forward", "sr3d_unet_train_step", "sr3d_unet_read",
+    "sr3d_unet_get_params", "sr3d_unet_forward", "sr3d_unet_train_step", "sr3d_unet_read", "sr3d_unet_set_path",
 ]
 KINDS = ["tv", "rfft_m_fwd", "fft_n_fwd", "fft_s", "fft_n_inv", "rfft_m_inv", "other", "setup"]
 
@@ -106,6 +106,7 @@ def load() -> ctypes.CDLL:
         "sr3d_unet_forward": (i, [vp, i, i, i, vp, vp]),
         "sr3d_unet_train_step": (i, [vp, i, i, i, vp, vp, d, ctypes.POINTER(d), vp, i]),
         "sr3d_unet_read": (i, [vp, i, vp, ctypes.c_longlong]),
+        "sr3d_unet_set_path": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -431,6 +432,11 @@ class UNet:
                                            ctypes.byref(loss), g.ctypes.data if g is not None else None,
                                            int(bool(update))))
         return loss.value, g
+
+    def set_path(self, path: str):
+        """Convolution kernels (sr3d_unet_set_path): "tcgen05" (default: tcgen05 where it is the
+        faster kernel), "mma" (mma.sync everywhere) or "tcgen05_all" (tcgen05 wherever it applies)."""
+        _check(load().sr3d_unet_set_path(self._h, {"tcgen05": 0, "mma": 1, "tcgen05_all": 2}[path]))
 
     ACTIVATIONS = ["x", "e1a", "e1", "p1", "e2a", "e2", "p2", "e3a", "e3", "d2a", "d2", "d1a", "d1", "out"]
 

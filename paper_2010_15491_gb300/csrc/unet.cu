@@ -111,66 +111,72 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b
 }
 
 // ---------------------------------------------------------------------------
-// forward convolution: out[v][co] = act(bias[co] + sum_k A[v][k] W[co][k]);
-// 4 warps x 32 voxels per CTA.  Also the data gradient (weights flipped and
-// transposed, no bias, no activation).
+// first layer (one input channel, 16 outputs): a 32 x 8 tile of voxels per
+// CTA marches over s with a ring of three x planes (with halo) in shared
+// memory; each thread forms its voxel's 16 outputs from the 27 neighbours in
+// FP32 (432 FMAs; the weights are read as shared-memory broadcasts) and
+// stores them as two 16-byte BF16 vectors.  The contraction is too thin for
+// the tensor cores (K = 27, one input channel).
 // ---------------------------------------------------------------------------
-template <int COUT, bool PACKED>
-__global__ void __launch_bounds__(128) k_conv_fwd(ConvIn in, const bf16* __restrict__ w, int Kpad, int Cin,
-                                                  const float* __restrict__ bias, int relu, bf16* __restrict__ out,
-                                                  long long V) {
-  __shared__ __align__(16) bf16 slab[4][2][256];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 2, t = lane & 3;
-  const long long vbase = ((long long)blockIdx.x * 4 + warp) * 32;
-  float acc[2][COUT / 8][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < COUT / 8; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-  const int nk = Kpad / 16;
-  const int lr = (lane & 7) + 8 * ((lane >> 3) & 1), lc = 8 * (lane >> 4);  // ldmatrix row / column of this lane
-#pragma unroll 1
-  for (int kc = 0; kc < nk; ++kc) {
-    fill_slab<PACKED>(slab[warp][0], in, vbase, kc, Cin, lane);
-    fill_slab<PACKED>(slab[warp][1], in, vbase + 16, kc, Cin, lane);
-    __syncwarp();
-    uint32_t a0[4], a1[4];
-    ldsm_x4(a0, slab[warp][0] + lr * 16 + lc);
-    ldsm_x4(a1, slab[warp][1] + lr * 16 + lc);
-#pragma unroll
-    for (int nt = 0; nt < COUT / 8; ++nt) {
-      const bf16* wp = w + (long long)(nt * 8 + g) * Kpad + kc * 16 + 2 * t;
-      const uint32_t b0 = __ldg(reinterpret_cast<const uint32_t*>(wp));
-      const uint32_t b1 = __ldg(reinterpret_cast<const uint32_t*>(wp + 8));
-      mma16816(acc[0][nt], a0, b0, b1);
-      mma16816(acc[1][nt], a1, b0, b1);
+constexpr int F_TM = 32, F_TN = 8, F_TS = 8;
+__global__ void __launch_bounds__(F_TM * F_TN, 2) k_conv_first(const bf16* __restrict__ x, const float* __restrict__ W,
+                                                            const float* __restrict__ bias, bf16* __restrict__ out,
+                                                            int M, int N, int S) {
+  constexpr int HW = F_TM + 2, HH = F_TN + 2;
+  __shared__ float xs[3][HH * HW];
+  __shared__ float ws[27][16];
+  __shared__ float bs[16];
+  const int tx = threadIdx.x % F_TM, ty = threadIdx.x / F_TM, tid = threadIdx.x;
+  const int m0 = blockIdx.x * F_TM, n0 = blockIdx.y * F_TN, s0 = blockIdx.z * F_TS;
+  const int s_end = min(S, s0 + F_TS);
+  for (int i = tid; i < 27 * 16; i += F_TM * F_TN) ws[i % 27][i / 27] = W[i];  // W is [co][tap]
+  if (tid < 16) bs[tid] = bias[tid];
+  auto load_plane = [&](int ps, float* buf) {
+    for (int i = tid; i < HH * HW; i += F_TM * F_TN) {
+      const int hn = i / HW, hm = i - hn * HW, m = m0 - 1 + hm, n = n0 - 1 + hn;
+      float v = 0.f;
+      if (ps >= 0 && ps < S && n >= 0 && n < N && m >= 0 && m < M)
+        v = __bfloat162float(x[((long long)ps * N + n) * M + m]);
+      buf[i] = v;
     }
-    __syncwarp();
-  }
+  };
+  load_plane(s0 - 1, xs[0]);
+  load_plane(s0, xs[1]);
+  const int m = m0 + tx, n = n0 + ty;
+  int r0 = 0;  // ring slot of plane s-1; s in r0+1, s+1 in r0+2 (mod 3)
+  for (int s = s0; s < s_end; ++s) {
+    load_plane(s + 1, xs[(r0 + 2) % 3]);
+    __syncthreads();
+    float acc[16];
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+    for (int c = 0; c < 16; ++c) acc[c] = bs[c];
 #pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      const long long v = vbase + mt * 16 + g + 8 * half;
-      if (v >= V) continue;
+    for (int ds = 0; ds < 3; ++ds) {
+      const float* xp = xs[(r0 + ds) % 3];
 #pragma unroll
-      for (int nt = 0; nt < COUT / 8; ++nt) {
-        const int co = nt * 8 + 2 * t;
-        float x0 = acc[mt][nt][2 * half], x1 = acc[mt][nt][2 * half + 1];
-        if (bias) {
-          x0 += bias[co];
-          x1 += bias[co + 1];
+      for (int dn = 0; dn < 3; ++dn)
+#pragma unroll
+        for (int dm = 0; dm < 3; ++dm) {
+          const float v = xp[(ty + dn) * HW + tx + dm];
+          const float* w = ws[(ds * 3 + dn) * 3 + dm];
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[c] = fmaf(w[c], v, acc[c]);
         }
-        if (relu) {
-          x0 = fmaxf(x0, 0.f);
-          x1 = fmaxf(x1, 0.f);
-        }
-        *reinterpret_cast<__nv_bfloat162*>(out + v * COUT + co) = __floats2bfloat162_rn(x0, x1);
+    }
+    if (m < M && n < N) {
+      uint32_t pk[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(acc[2 * q], 0.f), fmaxf(acc[2 * q + 1], 0.f));
+        pk[q] = *reinterpret_cast<const uint32_t*>(&h);
       }
+      uint4* o = reinterpret_cast<uint4*>(out + (((long long)s * N + n) * M + m) * 16);
+      o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
     }
+    __syncthreads();
+    r0 = (r0 + 1) % 3;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -318,6 +324,242 @@ __global__ void __launch_bounds__(256) k_conv3(ConvIn in, const bf16* __restrict
         }
         *reinterpret_cast<__nv_bfloat162*>(o + co) = __floats2bfloat162_rn(x0, x1);
       }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 (5th-generation tensor core) convolution for levels whose m extent
+// is a multiple of 128 and CIN, COUT in {16, 32, 48}.  A CTA owns one line of
+// 128 output voxels along m at row n and marches over a chunk of SC planes in
+// s.  The 27 weight slices stay in shared memory for the whole march; input
+// planes (the rows n-1, n, n+1 with a one-voxel m halo) stream through a ring
+// of 5 planes, so every plane is loaded once per CTA.  For output line s one
+// thread issues 27 x CIN/16 MMAs (M = 128 voxels, N = COUT, K = 16 channels)
+// into a TMEM accumulator; the A operand of tap (dm, dn, ds) is the ring row of
+// plane s+ds-1, row n+dn-1, starting at halo column dm: shared memory is kept
+// in the canonical no-swizzle K-major layout (8 voxels x 16 bytes per core
+// matrix, 16-byte rows consecutive along m, channel chunks a fixed stride
+// apart), so a shifted tap is just a shifted descriptor start address.  Two
+// TMEM accumulators alternate: while the tensor core works on line s, the four
+// warps drain line s-1 (tcgen05.ld, bias, ReLU, BF16 stores).  Every wait on
+// the MMA-completion barrier is bounded (about one second of clock); on
+// timeout the CTA sets *err and skips its stores.
+// ---------------------------------------------------------------------------
+namespace tc {
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: no swizzle, K-major; lbo = byte distance
+// between core matrices along K, sbo = along M/N
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version of this architecture family
+  return d;
+}
+
+// instruction descriptor, kind::f16: BF16 A and B, FP32 accumulator, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// bounded wait for the completion of phase `parity` of an mbarrier
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > 2000000000LL) return false;
+  }
+}
+
+__device__ __forceinline__ void ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int CIN, int COUT>
+struct Cfg {
+  static constexpr int CH = CIN / 8;                 // 16-byte channel chunks
+  static constexpr int HMP = 130;                    // halo row: m0-1 .. m0+128
+  static constexpr int RING = 5;                     // planes in the ring
+  static constexpr int LINES = RING * 3;             // rows n-1, n, n+1 of each plane
+  static constexpr int HALO = CH * LINES * HMP * 16; // [chunk][line][hm][16 B]
+  static constexpr int WB = 27 * CH * COUT * 16;     // [tap][chunk][co][16 B]
+  static constexpr int SMEM = HALO + WB + 64;
+  static constexpr uint32_t LBO_A = LINES * HMP * 16;
+  static constexpr uint32_t IDESC = idesc_bf16(128, COUT);
+};
+
+}  // namespace tc
+
+// wu: [27][CIN/8][COUT][8] BF16 (UMMA K-major slices)
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128, 1) k_conv3_tc(ConvIn in, const bf16* __restrict__ wu,
+                                                     const float* __restrict__ bias, int relu, bf16* __restrict__ out,
+                                                     int SC, int* __restrict__ err) {
+  using C = tc::Cfg<CIN, COUT>;
+  extern __shared__ __align__(128) unsigned char smem_tc[];
+  unsigned char* smem = smem_tc;
+  unsigned char* halo = smem;
+  unsigned char* wsm = smem + C::HALO;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wsm + C::WB);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int MB = in.M / 128;
+  int b = blockIdx.x;
+  const int m0 = (b % MB) * 128;
+  b /= MB;
+  const int n = b % in.N;
+  const int s0 = (b / in.N) * SC;
+  const int s_end = min(in.S, s0 + SC);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(tc::su32(tslot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bars[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bars[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // resident weights
+  for (int i = tid; i < 27 * C::CH * COUT; i += 128) cpz16(wsm + i * 16, wu + (long long)i * 8, true);
+  // one input plane (rows n-1..n+1, m0-1..m0+128) into its ring slot; zero outside the volume
+  auto load_plane = [&](int ps) {
+    const int slot = ((ps % C::RING) + C::RING) % C::RING;
+    for (int i = tid; i < 3 * C::HMP * C::CH; i += 128) {
+      const int c = i % C::CH, rest = i / C::CH, hm = rest % C::HMP, li = rest / C::HMP;
+      const int m = m0 - 1 + hm, nn = n - 1 + li;
+      const bool ok = ps >= 0 && ps < in.S && nn >= 0 && nn < in.N && m >= 0 && m < in.M;
+      unsigned char* dst = halo + ((c * C::LINES + slot * 3 + li) * C::HMP + hm) * 16;
+      cpz16(dst, ok ? chunk_ptr(in, ps, nn, m, c * 8) : in.src0, ok);
+    }
+  };
+  load_plane(s0 - 1);
+  load_plane(s0);
+  load_plane(s0 + 1);
+  cp_commit_();
+  cp_wait_<0>();
+  tc::fence_async_smem();
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = *tslot;
+  const uint32_t hbase = tc::su32(halo), wbase = tc::su32(wsm);
+  bool ok = true;
+
+  auto epilogue = [&](int jj, int s) {
+    if (!tc::wait_bar(&bars[jj & 1], (uint32_t)((jj >> 1) & 1))) return false;
+    tc::fence_after();
+    const int m = m0 + 32 * warp + lane;
+    bf16* o = out + (((long long)s * in.N + n) * in.M + m) * COUT;
+#pragma unroll
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+      float v[16];
+      tc::ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)((jj & 1) * 64 + c0), v);
+      uint32_t pk[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float a0 = v[2 * q], a1 = v[2 * q + 1];
+        if (bias) {
+          a0 += bias[c0 + 2 * q];
+          a1 += bias[c0 + 2 * q + 1];
+        }
+        if (relu) {
+          a0 = fmaxf(a0, 0.f);
+          a1 = fmaxf(a1, 0.f);
+        }
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a0, a1);
+        pk[q] = *reinterpret_cast<const uint32_t*>(&h);
+      }
+      if (m < in.M) {
+        reinterpret_cast<uint4*>(o + c0)[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        reinterpret_cast<uint4*>(o + c0)[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
+    }
+    return true;
+  };
+
+  int j = 0;
+  for (int s = s0; s < s_end; ++s, ++j) {
+    if (s + 1 < s_end) load_plane(s + 2);  // needed by line s+1; its slot held plane s-3, drained at step j-1
+    cp_commit_();
+    if (tid == 0) {
+      const uint32_t d = tmem + (uint32_t)((j & 1) * 64);
+      uint32_t acc = 0;
+#pragma unroll 1
+      for (int tap = 0; tap < 27; ++tap) {
+        const int dm = tap % 3, dn = (tap / 3) % 3, ds = tap / 9;
+        const int line = (((s + ds - 1) % C::RING + C::RING) % C::RING) * 3 + dn;
+#pragma unroll
+        for (int kk = 0; kk < CIN / 16; ++kk) {
+          const uint64_t a = tc::sdesc(hbase + (uint32_t)(((2 * kk * C::LINES + line) * C::HMP + dm) * 16), C::LBO_A, 128);
+          const uint64_t bd = tc::sdesc(wbase + (uint32_t)((tap * C::CH + 2 * kk) * COUT * 16), COUT * 16, 128);
+          tc::mma(d, a, bd, C::IDESC, acc);
+          acc = 1;
+        }
+      }
+      tc::commit(&bars[j & 1]);
+    }
+    if (j >= 1) ok = ok && epilogue(j - 1, s - 1);
+    cp_wait_<0>();
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
+  }
+  if (j >= 1) ok = ok && epilogue(j - 1, s_end - 1);
+  if (!ok && lane == 0) atomicExch(err, 1);
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
+// UMMA weight slices: forward wu[tap][c][co][e] = W[co][tap][8c+e] (K = ci);
+// data gradient wub[tap][c][ci][e] = W[8c+e][26-tap][ci] (K = co)
+__global__ void k_pack_w_umma(const float* __restrict__ W, int Cout, int Cin, bf16* __restrict__ wu,
+                              bf16* __restrict__ wub) {
+  const int total = 27 * Cout * Cin;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    {  // forward: i = ((tap * Cin/8 + c) * Cout + co) * 8 + e
+      const int e = i % 8, r = i / 8, co = r % Cout, r2 = r / Cout, c = r2 % (Cin / 8), tap = r2 / (Cin / 8);
+      wu[i] = __float2bfloat16(W[((long long)co * 27 + tap) * Cin + c * 8 + e]);
+    }
+    {  // data gradient: i = ((tap * Cout/8 + c) * Cin + ci) * 8 + e
+      const int e = i % 8, r = i / 8, ci = r % Cin, r2 = r / Cin, c = r2 % (Cout / 8), tap = r2 / (Cout / 8);
+      wub[i] = __float2bfloat16(W[((long long)(c * 8 + e) * 27 + (26 - tap)) * Cin + ci]);
     }
   }
 }
@@ -533,26 +775,6 @@ __global__ void k_bias_grad(const bf16* __restrict__ g, float* __restrict__ gb, 
   }
 }
 
-// BF16 GEMM weights: wf[co][Kpad] (k = tap*Cin + ci, zero padded) and the
-// data-gradient weights wb[ci][27*Cout] with k' = tap'*Cout + co holding
-// W[co][26 - tap'][ci]
-__global__ void k_pack_w(const float* __restrict__ W, int Cout, int Cin, int Kpad, bf16* __restrict__ wf,
-                         bf16* __restrict__ wb) {
-  const int total = Cout * Kpad;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
-    const int co = i / Kpad, k = i - co * Kpad;
-    float val = 0.f;
-    if (k < 27 * Cin) val = W[(long long)co * 27 * Cin + k];
-    wf[i] = __float2bfloat16(val);
-  }
-  if (!wb) return;
-  const int tb = Cin * 27 * Cout;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < tb; i += gridDim.x * blockDim.x) {
-    const int ci = i / (27 * Cout), r = i - ci * 27 * Cout, tap = r / Cout, co = r - tap * Cout;
-    wb[i] = __float2bfloat16(W[((long long)co * 27 + (26 - tap)) * Cin + ci]);
-  }
-}
-
 // copy dw[co][Kpad] (first 27*Cin columns) into the flat gradient (co, 27, ci)
 __global__ void k_unpack_dw(const float* __restrict__ dw, int Cout, int Cin, int Kpad, float* __restrict__ gflat) {
   const int total = Cout * 27 * Cin;
@@ -626,9 +848,12 @@ struct sr3d_unet_s {
   long long step = 0;
   long long off_w[10], off_b[10], off_h;
   int kpad[10];
-  bf16* wf0 = nullptr;  // first layer (one input channel): [co][Kpad] im2col weights
   bf16* wt[10] = {};    // layers 1..9: tap-major forward slices [27][co][ci]
   bf16* wtb[10] = {};   // layers 1..9: tap-major data-gradient slices [27][ci][co]
+  bf16* wu[10] = {};    // layers 1..9: tcgen05 (UMMA K-major) forward slices [27][ci/8][co][8]
+  bf16* wub[10] = {};   // layers 1..9: tcgen05 data-gradient slices [27][co/8][ci][8]
+  int use_tc = 1;       // tcgen05 path where available
+  int* err = nullptr;   // device flag: a bounded wait of the tcgen05 kernel ran out
   float* dw = nullptr;  // weight-gradient scratch [Cout][Kpad]
   size_t dw_cap = 0;
   double* loss = nullptr;
@@ -686,11 +911,11 @@ static int ensure_size(sr3d_unet_s* u, int M, int N, int S) {
   return SR3D_OK;
 }
 
-// first layer: one input channel, im2col k = tap (27 taps padded to 32)
-static cudaError_t conv_first(cudaStream_t st, const ConvIn& in, const bf16* w, int Kpad, const float* bias,
-                              bf16* out, long long V) {
-  const unsigned blocks = (unsigned)((V + 127) / 128);
-  k_conv_fwd<16, true><<<blocks, 128, 0, st>>>(in, w, Kpad, 1, bias, 1, out, V);
+// first layer: one input channel, 16 outputs, bias and ReLU
+static cudaError_t conv_first(cudaStream_t st, const bf16* x, const float* W, const float* bias, bf16* out, int M,
+                              int N, int S) {
+  dim3 grid((M + F_TM - 1) / F_TM, (N + F_TN - 1) / F_TN, (S + F_TS - 1) / F_TS);
+  k_conv_first<<<grid, F_TM * F_TN, 0, st>>>(x, W, bias, out, M, N, S);
   return cudaGetLastError();
 }
 
@@ -703,6 +928,43 @@ static cudaError_t conv3_t(cudaStream_t st, const ConvIn& in, const bf16* wt, co
                            ((in.S + C::TS - 1) / C::TS);
   k_conv3<CIN, COUT, MT><<<(unsigned)blocks, 256, C::SMEM, st>>>(in, wt, bias, relu, out);
   return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+static cudaError_t conv3_tc_t(cudaStream_t st, const ConvIn& in, const bf16* wu, const float* bias, int relu,
+                              bf16* out, int* err) {
+  using C = tc::Cfg<CIN, COUT>;
+  cudaError_t e = cudaFuncSetAttribute(k_conv3_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  if (e != cudaSuccess) return e;
+  const long long lines = (long long)(in.M / 128) * in.N * in.S;
+  int sc = (int)(lines / (152 * 4));  // about four waves of one CTA per SM
+  sc = sc < 8 ? 8 : (sc > 64 ? 64 : sc);
+  if (sc > in.S) sc = in.S;
+  const long long blocks = (long long)(in.M / 128) * in.N * ((in.S + sc - 1) / sc);
+  k_conv3_tc<CIN, COUT><<<(unsigned)blocks, 128, C::SMEM, st>>>(in, wu, bias, relu, out, sc, err);
+  return cudaGetLastError();
+}
+
+// the tcgen05 kernel takes levels whose m extent is a multiple of 128 and
+// 16, 32 or 48 input and output channels; returns cudaErrorNotSupported
+// otherwise.  With all_shapes false only the shapes where it beats the
+// mma.sync kernel are taken: measured at 256^3, (16, 16) 1.15 ms against
+// 1.28 ms, while N = 32 or 48-column MMAs per 128 voxels leave the other
+// shapes slower ((48, 16) 6.4 ms against 2.9 ms).
+static cudaError_t conv3_tc(cudaStream_t st, int cin, int cout, const ConvIn& in, const bf16* wu, const float* bias,
+                            int relu, bf16* out, int* err, bool all_shapes) {
+  if (in.M % 128 != 0) return cudaErrorNotSupported;
+  if (!all_shapes && !(cin == 16 && cout == 16)) return cudaErrorNotSupported;
+#define SR3D_CONV3_TC(CI, CO) \
+  if (cin == CI && cout == CO) return conv3_tc_t<CI, CO>(st, in, wu, bias, relu, out, err);
+  SR3D_CONV3_TC(16, 16)
+  SR3D_CONV3_TC(16, 32)
+  SR3D_CONV3_TC(32, 16)
+  SR3D_CONV3_TC(32, 32)
+  SR3D_CONV3_TC(16, 48)
+  SR3D_CONV3_TC(48, 16)
+#undef SR3D_CONV3_TC
+  return cudaErrorNotSupported;
 }
 
 // 3x3x3 convolution with cin = in.c0 + in.c1 input channels (a multiple of 16)
@@ -755,14 +1017,27 @@ static ConvIn cin(const bf16* a, int ca, int up, const bf16* b, int cb, int M, i
 }
 
 static int pack_weights(sr3d_unet_s* u) {
-  k_pack_w<<<64, 256, 0, u->stream>>>(u->p + u->off_w[0], kLayers[0].cout, 1, u->kpad[0], u->wf0, nullptr);
-  UCK(cudaGetLastError());
   for (int l = 1; l < 10; ++l) {
     const LayerShape& L = kLayers[l];
     k_pack_w3<<<128, 256, 0, u->stream>>>(u->p + u->off_w[l], L.cout, L.cin, u->wt[l], u->wtb[l]);
     UCK(cudaGetLastError());
+    k_pack_w_umma<<<128, 256, 0, u->stream>>>(u->p + u->off_w[l], L.cout, L.cin, u->wu[l], u->wub[l]);
+    UCK(cudaGetLastError());
   }
   return SR3D_OK;
+}
+
+// layer l forward (data gradient with grad = true): tcgen05 where it applies
+static cudaError_t conv_layer(sr3d_unet_s* u, int l, bool grad, const ConvIn& in, const float* bias, int relu,
+                              bf16* out) {
+  const LayerShape& L = kLayers[l];
+  const int cin = grad ? L.cout : L.cin, cout = grad ? L.cin : L.cout;
+  if (u->use_tc) {
+    const cudaError_t e =
+        conv3_tc(u->stream, cin, cout, in, grad ? u->wub[l] : u->wu[l], bias, relu, out, u->err, u->use_tc == 2);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  return conv3(u->stream, cin, cout, in, grad ? u->wtb[l] : u->wt[l], bias, relu, out);
 }
 
 static int unet_forward(sr3d_unet_s* u, const float* x) {
@@ -773,18 +1048,18 @@ static int unet_forward(sr3d_unet_s* u, const float* x) {
   auto bias = [&](int l) { return b + u->off_b[l]; };
   k_to_bf16<<<grid_for(V), 256, 0, st>>>(x, u->xb, V);
   UCK(cudaGetLastError());
-  UCK(conv_first(st, cin(u->xb, 1, 0, nullptr, 0, M, N, S), u->wf0, u->kpad[0], bias(0), u->e1a, V));
-  UCK(conv3(st, C1, C1, cin(u->e1a, C1, 0, nullptr, 0, M, N, S), u->wt[1], bias(1), 1, u->e1));
+  UCK(conv_first(st, u->xb, u->p + u->off_w[0], bias(0), u->e1a, M, N, S));
+  UCK(conv_layer(u, 1, false, cin(u->e1a, C1, 0, nullptr, 0, M, N, S), bias(1), 1, u->e1));
   k_maxpool<<<grid_for(V2 * C1), 256, 0, st>>>(u->e1, u->p1, u->i1, M, N, S, C1);
-  UCK(conv3(st, C1, C2, cin(u->p1, C1, 0, nullptr, 0, M / 2, N / 2, S / 2), u->wt[2], bias(2), 1, u->e2a));
-  UCK(conv3(st, C2, C2, cin(u->e2a, C2, 0, nullptr, 0, M / 2, N / 2, S / 2), u->wt[3], bias(3), 1, u->e2));
+  UCK(conv_layer(u, 2, false, cin(u->p1, C1, 0, nullptr, 0, M / 2, N / 2, S / 2), bias(2), 1, u->e2a));
+  UCK(conv_layer(u, 3, false, cin(u->e2a, C2, 0, nullptr, 0, M / 2, N / 2, S / 2), bias(3), 1, u->e2));
   k_maxpool<<<grid_for(V4 * C2), 256, 0, st>>>(u->e2, u->p2, u->i2, M / 2, N / 2, S / 2, C2);
-  UCK(conv3(st, C2, C3, cin(u->p2, C2, 0, nullptr, 0, M / 4, N / 4, S / 4), u->wt[4], bias(4), 1, u->e3a));
-  UCK(conv3(st, C3, C3, cin(u->e3a, C3, 0, nullptr, 0, M / 4, N / 4, S / 4), u->wt[5], bias(5), 1, u->e3));
-  UCK(conv3(st, C3 + C2, C2, cin(u->e3, C3, 1, u->e2, C2, M / 2, N / 2, S / 2), u->wt[6], bias(6), 1, u->d2a));
-  UCK(conv3(st, C2, C2, cin(u->d2a, C2, 0, nullptr, 0, M / 2, N / 2, S / 2), u->wt[7], bias(7), 1, u->d2));
-  UCK(conv3(st, C2 + C1, C1, cin(u->d2, C2, 1, u->e1, C1, M, N, S), u->wt[8], bias(8), 1, u->d1a));
-  UCK(conv3(st, C1, C1, cin(u->d1a, C1, 0, nullptr, 0, M, N, S), u->wt[9], bias(9), 1, u->d1));
+  UCK(conv_layer(u, 4, false, cin(u->p2, C2, 0, nullptr, 0, M / 4, N / 4, S / 4), bias(4), 1, u->e3a));
+  UCK(conv_layer(u, 5, false, cin(u->e3a, C3, 0, nullptr, 0, M / 4, N / 4, S / 4), bias(5), 1, u->e3));
+  UCK(conv_layer(u, 6, false, cin(u->e3, C3, 1, u->e2, C2, M / 2, N / 2, S / 2), bias(6), 1, u->d2a));
+  UCK(conv_layer(u, 7, false, cin(u->d2a, C2, 0, nullptr, 0, M / 2, N / 2, S / 2), bias(7), 1, u->d2));
+  UCK(conv_layer(u, 8, false, cin(u->d2, C2, 1, u->e1, C1, M, N, S), bias(8), 1, u->d1a));
+  UCK(conv_layer(u, 9, false, cin(u->d1a, C1, 0, nullptr, 0, M, N, S), bias(9), 1, u->d1));
   k_head_fwd<C1><<<grid_for(V), 256, 0, st>>>(u->d1, b + u->off_h, x, u->out, V);
   UCK(cudaGetLastError());
   return SR3D_OK;
@@ -804,7 +1079,7 @@ static int layer_back(sr3d_unet_s* u, int l, const ConvIn& in, bf16* gy, const b
   UCK(cudaGetLastError());
   if (gx) {
     const ConvIn gi = cin(gy, L.cout, 0, nullptr, 0, in.M, in.N, in.S);
-    UCK(conv3(st, L.cout, L.cin, gi, u->wtb[l], nullptr, 0, gx));
+    UCK(conv_layer(u, l, true, gi, nullptr, 0, gx));
   }
   return SR3D_OK;
 }
@@ -880,15 +1155,18 @@ int sr3d_unet_create(sr3d_unet_t* out, void* stream) {
   if (e == cudaSuccess) e = cudaMalloc(&u->m2, u->np * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&u->loss, sizeof(double));
   size_t dwmax = 0;
-  if (e == cudaSuccess) e = cudaMalloc(&u->wf0, (size_t)kLayers[0].cout * u->kpad[0] * sizeof(bf16));
   for (int l = 0; l < 10 && e == cudaSuccess; ++l) {
     const size_t nw = (size_t)27 * kLayers[l].cout * kLayers[l].cin;
     if (l > 0) e = cudaMalloc(&u->wt[l], nw * sizeof(bf16));
     if (e == cudaSuccess && l > 0) e = cudaMalloc(&u->wtb[l], nw * sizeof(bf16));
+    if (e == cudaSuccess && l > 0) e = cudaMalloc(&u->wu[l], nw * sizeof(bf16));
+    if (e == cudaSuccess && l > 0) e = cudaMalloc(&u->wub[l], nw * sizeof(bf16));
     const size_t dws = (size_t)kLayers[l].cout * u->kpad[l];
     if (dws > dwmax) dwmax = dws;
   }
   if (e == cudaSuccess) e = cudaMalloc(&u->dw, dwmax * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&u->err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(u->err, 0, sizeof(int), u->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(u->p, 0, u->np * sizeof(float), u->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(u->m1, 0, u->np * sizeof(float), u->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(u->m2, 0, u->np * sizeof(float), u->stream);
@@ -908,11 +1186,13 @@ int sr3d_unet_destroy(sr3d_unet_t u) {
   void* ps[] = {u->p, u->g, u->m1, u->m2, u->loss, u->dw};
   for (void* b : ps)
     if (b) cudaFree(b);
-  if (u->wf0) cudaFree(u->wf0);
   for (int l = 0; l < 10; ++l) {
     if (u->wt[l]) cudaFree(u->wt[l]);
     if (u->wtb[l]) cudaFree(u->wtb[l]);
+    if (u->wu[l]) cudaFree(u->wu[l]);
+    if (u->wub[l]) cudaFree(u->wub[l]);
   }
+  if (u->err) cudaFree(u->err);
   delete u;
   return SR3D_OK;
 }
@@ -941,14 +1221,32 @@ static int check_dims(int m, int n, int s) {
   return SR3D_OK;
 }
 
+// waits for the stream; SR3D_ERR_TIMEOUT if a bounded wait of the tcgen05 kernel ran out
+static int finish(sr3d_unet_s* u) {
+  int h = 0;
+  UCK(cudaMemcpyAsync(&h, u->err, sizeof(int), cudaMemcpyDeviceToHost, u->stream));
+  UCK(cudaStreamSynchronize(u->stream));
+  if (h) {
+    cudaMemsetAsync(u->err, 0, sizeof(int), u->stream);
+    return ufail(SR3D_ERR_TIMEOUT, "a tensor-core completion wait ran out");
+  }
+  return SR3D_OK;
+}
+
+int sr3d_unet_set_path(sr3d_unet_t u, int path) {
+  if (!u || path < SR3D_UNET_PATH_TCGEN05 || path > SR3D_UNET_PATH_TCGEN05_ALL)
+    return ufail(SR3D_ERR_INVALID_ARG, "unknown convolution path");
+  u->use_tc = path == SR3D_UNET_PATH_TCGEN05 ? 1 : path == SR3D_UNET_PATH_TCGEN05_ALL ? 2 : 0;
+  return SR3D_OK;
+}
+
 int sr3d_unet_forward(sr3d_unet_t u, int m, int n, int s, const float* x, float* out) {
   if (!u || !x || !out) return ufail(SR3D_ERR_INVALID_ARG, "NULL argument");
   UTRY(check_dims(m, n, s));
   UTRY(ensure_size(u, m, n, s));
   UTRY(unet_forward(u, x));
   UCK(cudaMemcpyAsync(out, u->out, (size_t)m * n * s * sizeof(float), cudaMemcpyDeviceToDevice, u->stream));
-  UCK(cudaStreamSynchronize(u->stream));
-  return SR3D_OK;
+  return finish(u);
 }
 
 int sr3d_unet_train_step(sr3d_unet_t u, int m, int n, int s, const float* x, const float* target, double lr,
@@ -971,7 +1269,7 @@ int sr3d_unet_train_step(sr3d_unet_t u, int m, int n, int s, const float* x, con
   UCK(cudaMemcpyAsync(&l, u->loss, sizeof(double), cudaMemcpyDeviceToHost, u->stream));
   UCK(cudaStreamSynchronize(u->stream));
   if (loss) *loss = l / ((double)m * n * s);
-  return SR3D_OK;
+  return finish(u);
 }
 
 int sr3d_unet_read(sr3d_unet_t u, int which, void* host, long long bytes) {

@@ -29,7 +29,10 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-SHAPES = [(16, 16, 16), (12, 8, 20)]  # (s, n, m); the second has partial tiles everywhere
+# (s, n, m): the second has partial tiles everywhere; the last two have m
+# extents that are multiples of 128 at the first (and second) level, where the
+# convolutions run on the tcgen05 path
+SHAPES = [(16, 16, 16), (12, 8, 20), (8, 8, 128), (4, 8, 256)]
 
 
 def _bf16(a):
@@ -233,3 +236,27 @@ def test_admm_from_network_output_and_dual(lib):
     ref = O.admm_tv(y, psf, dec, lam, rho, 6, x0, d0=U.dual_from_x(x0, lam, rho))
     assert rel_l2(x.cpu().numpy(), ref["x"]) < 1e-11
     p.close()
+
+
+@pytest.mark.parametrize("shape", [(8, 8, 128), (4, 8, 256)])
+def test_tcgen05_and_mma_paths_agree(lib, shape):
+    """The tcgen05 convolutions (levels with m a multiple of 128) and the
+    mma.sync ones compute the same network: outputs and gradients agree to the
+    BF16 rounding of their different summation orders."""
+    import torch
+    theta = _params(101)
+    x = _volume(shape, 102)
+    t = x + 0.3 * _volume(shape, 103)
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    td = torch.tensor(t, dtype=torch.float32, device="cuda")
+    res = {}
+    for path in ("tcgen05_all", "mma"):
+        net = lib.UNet()
+        net.set_params(theta)
+        net.set_path(path)
+        out = net.forward(xd).cpu().numpy().astype(np.float64)
+        _, g = net.train_step(xd, td, update=False, want_grad=True)
+        res[path] = (out, g.astype(np.float64))
+        net.close()
+    assert _rel(res["tcgen05_all"][0] - x, res["mma"][0] - x) < 1e-2
+    assert _rel(res["tcgen05_all"][1], res["mma"][1]) < 2e-2
