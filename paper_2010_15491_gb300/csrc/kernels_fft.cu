@@ -59,20 +59,44 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_fwd(const T* __restrict__ in,
   }
   auto pos = [](int i) { return NC > 0 ? ct_pos<true>(i) : i; };
   // split the packed transform: X[k] = E[k] + W^k O[k], E/O from Z[k], conj(Z[H-k])
-  for (int i = threadIdx.x; i < L * a.Ms; i += blockDim.x) {
-    const int l = i / a.Ms, slot = i - l * a.Ms;
+  auto emit = [&](int l, int slot, int k, bool cj) {
     const long long gl = line0 + l;
-    if (gl >= nlines) continue;
-    const int grp = slot / a.dr, p = slot - grp * a.dr;
-    int k = grp + p * a.Ml;
-    const bool cj = k > H;
-    if (cj) k = a.M - k;
     const C zk = sm[l * Hp + pos(k == H ? 0 : k)];
     const C zc = conjc(sm[l * Hp + pos(k == 0 ? 0 : H - k)]);
     const C e = (zk + zc) * (T)0.5;
     const C o = mul_mi(zk - zc) * (T)0.5;
     const C X = e + cmul(NC > 0 ? tw[k] : __ldg(&twM[k]), o);
     out[gl * a.Mp + slot] = cj ? conjc(X) : X;
+  };
+  if constexpr (NC > 0) {
+    // slot -> (frequency, conjugate) once per CTA; a warp writes 32 slots of a line
+    short2* tab = reinterpret_cast<short2*>(sm + L * Hp + 2 * NC);
+    for (int i = threadIdx.x; i < a.Ms; i += blockDim.x) {
+      const int grp = i / a.dr, p = i - grp * a.dr;
+      int k = grp + p * a.Ml;
+      const bool cj = k > H;
+      if (cj) k = a.M - k;
+      tab[i] = make_short2((short)k, (short)cj);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int l = warp; l < L; l += nw) {
+      if (line0 + l >= nlines) break;
+      for (int slot = lane; slot < a.Ms; slot += 32) {
+        const short2 t = tab[slot];
+        emit(l, slot, t.x, t.y != 0);
+      }
+    }
+  } else {
+    for (int i = threadIdx.x; i < L * a.Ms; i += blockDim.x) {
+      const int l = i / a.Ms, slot = i - l * a.Ms;
+      if (line0 + l >= nlines) continue;
+      const int grp = slot / a.dr, p = slot - grp * a.dr;
+      int k = grp + p * a.Ml;
+      const bool cj = k > H;
+      if (cj) k = a.M - k;
+      emit(l, slot, k, cj);
+    }
   }
 }
 
@@ -89,7 +113,13 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_inv(const cplx<T>* __restrict
   const int tpl = NC > 0 ? NC / 16 : H / a.f.e;
   const C* tw = twM;
   C* slots = sm + L * Hp + (NC > 0 ? 2 * NC : 0);  // NC > 0: the CTA's L slot rows, staged
+  short2* stab = reinterpret_cast<short2*>(slots + (NC > 0 ? L * a.Mp : 0));  // NC > 0: k -> (slot, conj)
   if constexpr (NC > 0) {
+    for (int k = threadIdx.x; k <= H; k += blockDim.x) {
+      bool c;
+      const int sl = mslot_of(k, a.M, a.Ml, a.dr, c);
+      stab[k] = make_short2((short)sl, (short)c);
+    }
     C* tws = sm + L * Hp;
     // the L rows of Mp complex are contiguous in global memory: 16-byte async copies
     const long long line0s = (long long)blockIdx.x * L;
@@ -117,8 +147,15 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_inv(const cplx<T>* __restrict
   auto ld = [&](int k) -> C {
     if (!ok) return czero<C>();
     bool c1, c2;
-    const int s1 = mslot_of(k, a.M, a.Ml, a.dr, c1);
-    const int s2 = mslot_of(H - k, a.M, a.Ml, a.dr, c2);
+    int s1, s2;
+    if constexpr (NC > 0) {
+      const short2 t1 = stab[k], t2 = stab[H - k];
+      s1 = t1.x; c1 = t1.y != 0;
+      s2 = t2.x; c2 = t2.y != 0;
+    } else {
+      s1 = mslot_of(k, a.M, a.Ml, a.dr, c1);
+      s2 = mslot_of(H - k, a.M, a.Ml, a.dr, c2);
+    }
     C xk = NC > 0 ? row[s1] : __ldg(&row[s1]);
     if (c1) xk = conjc(xk);
     C xh = NC > 0 ? row[s2] : __ldg(&row[s2]);
@@ -541,7 +578,7 @@ static cudaError_t rfft_fwd_k(const Plan& p, const Geometry& g, const void* in, 
   m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
   if (NC > 0) {
     Hp = ct_line_pitch<true>(NC);
-    smem = (size_t)(L * Hp + 2 * NC) * sizeof(cplx<T>);
+    smem = (size_t)(L * Hp + 2 * NC) * sizeof(cplx<T>) + (size_t)g.Ms * sizeof(short2);  // + slot table
   }
   const long long nlines = (long long)g.S * g.N;
   const unsigned blocks = (unsigned)((nlines + L - 1) / L);
@@ -561,7 +598,7 @@ static cudaError_t rfft_inv_k(const Plan& p, const Geometry& g, const void* in, 
   m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
   if (NC > 0) {
     Hp = ct_line_pitch<true>(NC);
-    smem = (size_t)(L * Hp + 2 * NC + L * g.Mp) * sizeof(cplx<T>);
+    smem = (size_t)(L * Hp + 2 * NC + L * g.Mp) * sizeof(cplx<T>) + (size_t)(NC + 1) * sizeof(short2);
   }
   const long long nlines = (long long)g.S * g.N;
   const unsigned blocks = (unsigned)((nlines + L - 1) / L);
