@@ -12,14 +12,15 @@ working set (x, two dual buffers, Theta, Lambda, spectrum: ~0.65 GB) is far
 larger than L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload headline|batch|warmstart|regularisers|comparator]
+                  [--workload headline|batch|warmstart|regularisers|comparator|unet]
 
 --workload batch: 64 volumes of uneven size and decimation solved together;
 --workload warmstart: wall-clock to tolerance at 256^3, cold start against
 the learned U-Net warm start (parameters in paper_2010_15491_gb300/weights/);
 --workload regularisers: the 256^3 solve with the anisotropic TV and the
 Tikhonov-on-gradient solve, separable-PSF path on and off; --workload
-comparator: the closed form of eq. 12 against conjugate gradients on eq. 6.
+comparator: the closed form of eq. 12 against conjugate gradients on eq. 6;
+--workload unet: the warm-start U-Net alone (forward 256^3, training 128^3).
 
 One JSON line on stdout (rank 0).  Under torchrun with N > 1 every rank solves
 its own replica (the single-volume path does not shard: replicas only).
@@ -48,12 +49,12 @@ STEP_BYTES = 80
 # kernel from one ncu capture of this workload (profiles/admm_tv_256_kernels_ncu.md),
 # valid while the kernel's sources hash to the recorded value
 NCU_TRAFFIC = {
-    "tv": (516.4e6, ("kernels_tv.cu", "common.cuh"), "c8cf7651b7dee524"),
-    "rfft_m_fwd": (87.7e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "d71d6d29773ae8aa"),
-    "fft_n_fwd": (80.4e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "d71d6d29773ae8aa"),
-    "fft_s": (185.3e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "d71d6d29773ae8aa"),
-    "fft_n_inv": (80.5e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "d71d6d29773ae8aa"),
-    "rfft_m_inv": (89.7e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "d71d6d29773ae8aa"),
+    "tv": (516.2e6, ("kernels_tv.cu", "common.cuh"), "dfbc2c4db411ebe4"),
+    "rfft_m_fwd": (86.9e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "4aa889e8daf20ca8"),
+    "fft_n_fwd": (80.4e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "4aa889e8daf20ca8"),
+    "fft_s": (111.3e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "4aa889e8daf20ca8"),
+    "fft_n_inv": (80.5e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "4aa889e8daf20ca8"),
+    "rfft_m_inv": (90.1e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "4aa889e8daf20ca8"),
 }
 
 
@@ -459,6 +460,68 @@ def run_comparator(args, rank, world, local_rank):
     plan.close()
 
 
+def run_unet(args, rank, world, local_rank):
+    """--workload unet: the warm-start U-Net alone, forward at 256^3 and one
+    training step at 128^3, for each convolution path (tcgen05 where faster =
+    the default, mma.sync everywhere, tcgen05 wherever it applies), CUDA
+    events; tensor-core throughput against the measured BF16 peak."""
+    import numpy as np
+    import torch
+    from paper_2010_15491_gb300.build import build
+    import paper_2010_15491_gb300 as sr3d
+    from paper_2010_15491_gb300 import warmstart as W
+    build()
+    torch.cuda.set_device(local_rank)
+    net = sr3d.UNet()
+    theta = np.load(WEIGHTS) if os.path.exists(WEIGHTS) else W.init_params(3)
+    net.set_params(theta)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.rand((256, 256, 256), device="cuda", generator=g)
+    x2 = torch.rand((128, 128, 128), device="cuda", generator=g)
+    t2 = torch.rand((128, 128, 128), device="cuda", generator=g)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16 = None
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as f:
+            bf16 = json.load(f).get("bf16_tflops")
+    out = {}
+    for path in ("tcgen05", "mma", "tcgen05_all"):
+        net.set_path(path)
+        for _ in range(max(args.warmup, 1)):
+            net.forward(x)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            net.forward(x)
+        ev1.record()
+        torch.cuda.synchronize()
+        fwd = ev0.elapsed_time(ev1) / args.steps
+        net.train_step(x2, t2, lr=0.0, update=False)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(args.steps):
+            net.train_step(x2, t2, lr=0.0, update=False)
+        ev1.record()
+        torch.cuda.synchronize()
+        trn = ev0.elapsed_time(ev1) / args.steps
+        tf = 2 * UNET_MACS * x.numel() / (fwd * 1e-3) / 1e12
+        out[path] = {"forward_256_ms": fwd, "train_step_128_ms": trn, "forward_tflops": tf}
+    net.set_path("tcgen05")
+    if rank == 0:
+        d = out["tcgen05"]
+        print(json.dumps({
+            "metric": "U-Net forward TFLOP/s at 256³ (BF16 tensor cores)", "value": d["forward_tflops"],
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "warm-start U-Net 16/32/64 channels, forward 256^3, training step 128^3",
+                       "flops_per_voxel": 2 * UNET_MACS},
+            "roofline": {"bound": "tensor", "achieved": d["forward_tflops"], "peak": bf16, "unit": "TFLOP/s",
+                         "frac": d["forward_tflops"] / bf16 if bf16 else None},
+            "paths": out}), flush=True)
+    net.close()
+
+
 WEIGHTS = os.path.join(ROOT, "paper_2010_15491_gb300", "weights", "unet_warmstart.npy")
 # forward multiply-adds per HR voxel of the warm-start U-Net: ten 3x3x3 layers
 # at full, 1/8 and 1/64 voxel density, plus the 1x1x1 head
@@ -556,7 +619,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["headline", "batch", "warmstart", "regularisers", "comparator"],
+    ap.add_argument("--workload", choices=["headline", "batch", "warmstart", "regularisers", "comparator", "unet"],
                     default="headline")
     args = ap.parse_args()
     from synth import HEADLINE_256 as w
@@ -582,6 +645,9 @@ def main():
     elif args.workload == "comparator":
         if rank == 0:
             run_comparator(args, rank, world, local_rank)
+    elif args.workload == "unet":
+        if rank == 0:
+            run_unet(args, rank, world, local_rank)
     else:
         run_ours(args, w, rank, world, local_rank)
     if world > 1:

@@ -305,6 +305,13 @@ int sr3d_unet_read(sr3d_unet_t net, int which, void* host, long long bytes);
  * plan.  Pass d_dev to sr3d_admm_tv together with x_dev as x0. */
 int sr3d_dual_init(sr3d_plan_t plan, const void* x_dev, double lambda, double rho, void* d_dev);
 
+/* Replaces the plan's PSF (host taps psf[p_s][p_n][p_m], each size at most the
+ * HR size of its axis): recomputes Lambda (Algorithm 1 step 1) and the
+ * separable-PSF tables in the plan's buffers, without reallocating; later
+ * calls use the new PSF.  Used to fit a PSF to data (many forward-model
+ * evaluations with one plan).  Errors: INVALID_ARG, OOM, CUDA. */
+int sr3d_set_psf(sr3d_plan_t plan, const double* psf, int p_m, int p_n, int p_s);
+
 /* Other regularisers through the same Fourier-domain x-update (the
  * conclusion of the paper points to regularisation functions other than
  * Tikhonov and TV).

@@ -40,7 +40,7 @@ __all__ = [
     "otf", "blur", "decimate", "zero_fill", "forward", "nearest_neighbour",
     "fold", "replicate", "tikhonov", "grad", "grad_adj", "laplacian_symbol",
     "shrink", "shrink_aniso", "tv_term", "admm_xstep", "admm_tv", "objective", "augmented_lagrangian",
-    "tikhonov_grad", "tikhonov_cg",
+    "tikhonov_grad", "tikhonov_cg", "gaussian_psf_taps", "psf_fit_objective",
     "psnr",
 ]
 
@@ -269,6 +269,26 @@ def augmented_lagrangian(x, u, dvar, y, psf, dec, lam_tv, mu) -> float:
     tv = float(np.sqrt((u ** 2).sum(axis=0)).sum())
     c = grad(x) - (u - dvar)
     return 0.5 * float((r ** 2).sum()) + lam_tv * tv + 0.5 * mu * float((c ** 2).sum())
+
+
+def gaussian_psf_taps(sigma, size) -> np.ndarray:
+    """Separable Gaussian of standard deviations sigma = (sigma_m, sigma_n,
+    sigma_s) on an odd support size = (p_m, p_n, p_s), centre tap p // 2,
+    normalised to sum 1 after truncation; shape (p_s, p_n, p_m)."""
+    g = [np.exp(-0.5 * ((np.arange(p) - p // 2) / s) ** 2) for s, p in zip(sigma, size)]
+    psf = np.einsum("i,j,k->ijk", g[2], g[1], g[0])
+    return psf / psf.sum()
+
+
+def psf_fit_objective(sigma, size, x_ref: np.ndarray, y: np.ndarray, dec):
+    """Objective of the Gaussian PSF fit (Sec. IV estimates its PSF as a 3D
+    Gaussian with the HR reference volume at hand): the least-squares misfit
+    min_{a,b} ||y - a D H_sigma x_ref - b||^2 and its minimisers (a, b)."""
+    yh = forward(x_ref, gaussian_psf_taps(sigma, size), dec).ravel()
+    A = np.stack([yh, np.ones_like(yh)], axis=1)
+    (a, b), *_ = np.linalg.lstsq(A, y.ravel(), rcond=None)
+    r = y.ravel() - a * yh - b
+    return float(r @ r), float(a), float(b)
 
 
 def tikhonov_cg(y: np.ndarray, psf: np.ndarray, dec, tau: float, xbar=None, iters: int = 100,

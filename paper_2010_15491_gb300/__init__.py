@@ -32,7 +32,7 @@ EXPORTED = [
     "sr3d_plan", "sr3d_destroy", "sr3d_forward", "sr3d_tikhonov", "sr3d_admm_tv", "sr3d_admm_tv_host",
     "sr3d_last_error", "sr3d_get_otf", "sr3d_fft3", "sr3d_xstep", "sr3d_tv_step", "sr3d_plan_info",
     "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc", "sr3d_admm_tv_batched", "sr3d_autotune",
-    "sr3d_separable", "sr3d_set_tv", "sr3d_tikhonov_grad", "sr3d_tikhonov_cg",
+    "sr3d_separable", "sr3d_set_tv", "sr3d_tikhonov_grad", "sr3d_tikhonov_cg", "sr3d_set_psf",
     "sr3d_dual_init", "sr3d_unet_param_count", "sr3d_unet_create", "sr3d_unet_destroy", "sr3d_unet_set_params",
     "sr3d_unet_get_params", "sr3d_unet_forward", "sr3d_unet_train_step", "sr3d_unet_read", "sr3d_unet_set_path",
 ]
@@ -96,6 +96,7 @@ def load() -> ctypes.CDLL:
         "sr3d_dual_init": (i, [vp, vp, d, d, vp]),
         "sr3d_separable": (i, [vp, i, ctypes.POINTER(i)]),
         "sr3d_set_tv": (i, [vp, i]),
+        "sr3d_set_psf": (i, [vp, ctypes.POINTER(d), i, i, i]),
         "sr3d_tikhonov_grad": (i, [vp, vp, d, vp]),
         "sr3d_tikhonov_cg": (i, [vp, vp, vp, d, d, i, vp, ctypes.POINTER(i), ctypes.POINTER(d)]),
         "sr3d_unet_param_count": (ctypes.c_longlong, []),
@@ -188,6 +189,15 @@ class Plan:
         out = dict(zip(keys, list(sizes)))
         out["bytes"] = b.value
         return out
+
+    def set_psf(self, psf):
+        """Replaces the PSF (taps of shape (p_s, p_n, p_m)) and recomputes Lambda (sr3d_set_psf)."""
+        psf = np.ascontiguousarray(psf, dtype=np.float64)
+        if psf.ndim != 3:
+            raise ValueError("psf must be 3-D (p_s, p_n, p_m)")
+        _check(load().sr3d_set_psf(self._h, psf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   psf.shape[2], psf.shape[1], psf.shape[0]))
+        self._psf_keep = psf
 
     def set_tv(self, kind: str):
         """TV of admm_tv on this plan: "isotropic" (default) or "anisotropic" (sr3d_set_tv)."""

@@ -226,6 +226,54 @@ static bool separable_factors(const double* psf, int pm, int pn, int ps, std::ve
   return true;
 }
 
+// Lambda = DFT of the origin-wrapped PSF (Algorithm 1 step 1) into p.lam and
+// its solve-order copy; for a separable PSF also the three 1-D factor DFTs.
+// Uses p.theta as scratch; synchronises the stream.
+static int compute_lambda(Plan& p, const double* psf, int pm, int pn, int ps) {
+  const Geometry& g = p.hr;
+  const size_t csz = 2 * p.esz;
+  const long long np = (long long)pm * pn * ps;
+  double psum = 0;
+  for (long long i = 0; i < np; ++i) psum += psf[i];
+  p.psf_sum = psum;
+  void* psf_dev = nullptr;
+  cudaError_t e = cudaMalloc(&psf_dev, (size_t)np * sizeof(double));
+  if (e != cudaSuccess) return fail(SR3D_ERR_OOM, "PSF upload: %s", cudaGetErrorString(e));
+  e = cudaMemcpyAsync(psf_dev, psf, (size_t)np * sizeof(double), cudaMemcpyHostToDevice, p.stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p.theta, 0, (size_t)g.V() * p.esz, p.stream);
+  if (e == cudaSuccess) e = launch_wrap_psf(p, p.theta, (const double*)psf_dev, pm, pn, ps);
+  if (e == cudaSuccess) e = launch_rfft_m_fwd(p, g, p.theta, p.lam, p.twM);
+  if (e == cudaSuccess) e = launch_fft_n(p, g, p.lam, p.twN, false);
+  if (e == cudaSuccess) e = launch_fft_s(p, g, p.lam, p.twS, S_FWD, false, nullptr);
+  if (e == cudaSuccess) e = launch_perm_lam(p, p.lam, p.lam_solve);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
+  cudaFree(psf_dev);
+  if (e != cudaSuccess) return fail(SR3D_ERR_CUDA, "Lambda: %s", cudaGetErrorString(e));
+  // separable PSF: the 1-D factor DFTs, whose products the class solve uses
+  std::vector<double> fm, fn, fs;
+  p.sep_avail = false;
+  if (separable_factors(psf, pm, pn, ps, fm, fn, fs)) {
+    if (!p.lamM1) TRY(dmalloc(p, &p.lamM1, (size_t)g.M * csz));
+    if (!p.lamN1) TRY(dmalloc(p, &p.lamN1, (size_t)g.N * csz));
+    if (!p.lamS1) TRY(dmalloc(p, &p.lamS1, (size_t)g.S * csz));
+    double* fdev = nullptr;
+    const size_t nf = fm.size() + fn.size() + fs.size();
+    CK(cudaMalloc(&fdev, nf * sizeof(double)));
+    std::vector<double> all(fm);
+    all.insert(all.end(), fn.begin(), fn.end());
+    all.insert(all.end(), fs.begin(), fs.end());
+    e = cudaMemcpyAsync(fdev, all.data(), nf * sizeof(double), cudaMemcpyHostToDevice, p.stream);
+    if (e == cudaSuccess) e = launch_dft_factor(p, p.lamM1, fdev, pm, g.M);
+    if (e == cudaSuccess) e = launch_dft_factor(p, p.lamN1, fdev + fm.size(), pn, g.N);
+    if (e == cudaSuccess) e = launch_dft_factor(p, p.lamS1, fdev + fm.size() + fn.size(), ps, g.S);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
+    cudaFree(fdev);
+    if (e != cudaSuccess) return fail(SR3D_ERR_CUDA, "Lambda (separable PSF): %s", cudaGetErrorString(e));
+    p.sep_avail = true;
+  }
+  return SR3D_OK;
+}
+
 static SolveArgs solve_args(const Plan& p, int mode_alpha_nn, double alpha) {
   SolveArgs sv;
   memset(&sv, 0, sizeof(sv));
@@ -513,41 +561,7 @@ int sr3d_plan(sr3d_plan_t* out, const sr3d_desc* d) {
     CK(launch_symbol(p, p.symM, g.M));
     CK(launch_symbol(p, p.symN, g.N));
     CK(launch_symbol(p, p.symS, g.S));
-    // Lambda = DFT of the origin-wrapped PSF (Algorithm 1 step 1)
-    void* psf_dev = nullptr;
-    TRY(dmalloc(p, &psf_dev, (size_t)np * sizeof(double)));
-    p.bytes -= (long long)np * sizeof(double);
-    cudaError_t e = cudaMemcpyAsync(psf_dev, d->psf, (size_t)np * sizeof(double), cudaMemcpyHostToDevice, p.stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(p.theta, 0, (size_t)g.V() * p.esz, p.stream);
-    if (e == cudaSuccess) e = launch_wrap_psf(p, p.theta, (const double*)psf_dev, d->p_m, d->p_n, d->p_s);
-    if (e == cudaSuccess) e = launch_rfft_m_fwd(p, g, p.theta, p.lam, p.twM);
-    if (e == cudaSuccess) e = launch_fft_n(p, g, p.lam, p.twN, false);
-    if (e == cudaSuccess) e = launch_fft_s(p, g, p.lam, p.twS, S_FWD, false, nullptr);
-    if (e == cudaSuccess) e = launch_perm_lam(p, p.lam, p.lam_solve);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
-    cudaFree(psf_dev);
-    if (e != cudaSuccess) return fail(SR3D_ERR_CUDA, "plan setup: %s", cudaGetErrorString(e));
-    // separable PSF: the 1-D factor DFTs, whose products the class solve uses
-    std::vector<double> fm, fn, fs;
-    if (separable_factors(d->psf, d->p_m, d->p_n, d->p_s, fm, fn, fs)) {
-      TRY(dmalloc(p, &p.lamM1, (size_t)g.M * csz));
-      TRY(dmalloc(p, &p.lamN1, (size_t)g.N * csz));
-      TRY(dmalloc(p, &p.lamS1, (size_t)g.S * csz));
-      double* fdev = nullptr;
-      const size_t nf = fm.size() + fn.size() + fs.size();
-      CK(cudaMalloc(&fdev, nf * sizeof(double)));
-      std::vector<double> all(fm);
-      all.insert(all.end(), fn.begin(), fn.end());
-      all.insert(all.end(), fs.begin(), fs.end());
-      e = cudaMemcpyAsync(fdev, all.data(), nf * sizeof(double), cudaMemcpyHostToDevice, p.stream);
-      if (e == cudaSuccess) e = launch_dft_factor(p, p.lamM1, fdev, d->p_m, g.M);
-      if (e == cudaSuccess) e = launch_dft_factor(p, p.lamN1, fdev + fm.size(), d->p_n, g.N);
-      if (e == cudaSuccess) e = launch_dft_factor(p, p.lamS1, fdev + fm.size() + fn.size(), d->p_s, g.S);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
-      cudaFree(fdev);
-      if (e != cudaSuccess) return fail(SR3D_ERR_CUDA, "plan setup (separable PSF): %s", cudaGetErrorString(e));
-      p.sep_avail = true;
-    }
+    TRY(compute_lambda(p, d->psf, d->p_m, d->p_n, d->p_s));
     return SR3D_OK;
   };
   rc = body();
@@ -620,6 +634,24 @@ int sr3d_dual_init(sr3d_plan_t plan, const void* x, double lambda, double rho, v
   Plan& p = plan->p;
   LAUNCH(SR3D_K_OTHER, launch_dual_init(p, x, lambda / rho, d));
   return sync_plan(p);
+}
+
+int sr3d_set_psf(sr3d_plan_t plan, const double* psf, int p_m, int p_n, int p_s) {
+  if (!plan || !psf || p_m <= 0 || p_n <= 0 || p_s <= 0) return fail(SR3D_ERR_INVALID_ARG, "missing PSF");
+  Plan& p = plan->p;
+  if (p_m > p.hr.M || p_n > p.hr.N || p_s > p.hr.S) return fail(SR3D_ERR_INVALID_ARG, "PSF larger than the volume");
+  TRY(sync_plan(p));
+  const bool sep_before = p.sep_avail;
+  TRY(compute_lambda(p, psf, p_m, p_n, p_s));
+  if (p.sep_avail != sep_before) {  // captured solve arguments change with the separable path
+    if (p.iter_graph) {
+      cudaGraphExecDestroy(p.iter_graph);
+      p.iter_graph = nullptr;
+    }
+    drop_eval_graphs(p);
+    ++p.version;
+  }
+  return SR3D_OK;
 }
 
 int sr3d_set_tv(sr3d_plan_t plan, int kind) {

@@ -424,3 +424,53 @@ def test_cg_converges_to_the_closed_form(lib, dtype, tol, agree):
     _, k, rel, ok = plan.tikhonov_cg(yd, 1e-2, tol=1e-30, max_iters=3)  # NOT_CONVERGED: x still written
     assert not ok and k == 3 and rel > 1e-30
     plan.close()
+
+
+# ---------------------------------------------------------------------------
+# PSF replacement and the Gaussian PSF fit
+# ---------------------------------------------------------------------------
+
+def test_set_psf_equals_a_fresh_plan(lib):
+    """sr3d_set_psf recomputes Lambda in place: the same results, bit for bit,
+    as a plan created with that PSF (separable and non-separable PSFs)."""
+    import torch
+    dims, dec = (64, 32, 16), (2, 2, 2)
+    psf_a, xt, y = make_problem(dims, dec, sigma=(1.0, 1.0, 1.0), seed=111)
+    psf_b, _, _ = make_problem(dims, dec, sigma=(1.4, 0.7, 1.1), seed=112, asym=True)
+    plan = lib.Plan(dims, dec, psf_a, "f32")
+    yd = T(y, "f32")
+    plan.admm_tv(yd, plan.empty_hr(), 2e-3, 1e-2, 4, tau_init=1e-2)  # leaves graphs captured
+    for psf in (psf_b, psf_a):
+        plan.set_psf(psf)
+        fresh = lib.Plan(dims, dec, psf, "f32")
+        assert plan.separable() == fresh.separable()
+        assert torch.equal(plan.get_otf(), fresh.get_otf())
+        xa, xb = plan.empty_hr(), fresh.empty_hr()
+        plan.admm_tv(yd, xa, 2e-3, 1e-2, 4, tau_init=1e-2)
+        fresh.admm_tv(yd, xb, 2e-3, 1e-2, 4, tau_init=1e-2)
+        assert torch.equal(xa, xb)
+        fresh.close()
+    plan.close()
+
+
+def test_gaussian_psf_fit(lib):
+    """The fit's objective equals the oracle's at the same sigma, and on
+    noise-free data made with a known Gaussian, gain and offset it recovers
+    them."""
+    import torch
+    from paper_2010_15491_gb300 import psf_fit
+    dims, dec = (64, 64, 32), (2, 2, 2)
+    _, xt, _ = make_problem(dims, dec, seed=113, n_ell=20)
+    size = psf_fit.support((3.0, 3.0, 3.0), dims)
+    s_true = (1.3, 0.9, 1.7)
+    y = 2.0 * O.forward(xt, O.gaussian_psf_taps(s_true, size), dec) + 0.1
+    plan = lib.Plan(dims, dec, O.gaussian_psf_taps((1.0, 1.0, 1.0), size), "f64")
+    xd, yd = T(xt, "f64"), T(y, "f64")
+    for s in [(1.0, 1.0, 1.0), (2.0, 0.7, 1.2)]:
+        r, a, b = psf_fit.objective(plan, xd, yd, s, size)
+        ro, ao, bo = O.psf_fit_objective(s, size, xt, y, dec)
+        assert np.isclose(r, ro, rtol=1e-8) and np.isclose(a, ao, rtol=1e-10) and np.isclose(b, bo, rtol=1e-8, atol=1e-12)
+    res = psf_fit.fit_gaussian_psf(plan, xd, yd, sigma0=(1.0, 1.0, 1.0), bounds=(0.3, 3.0))
+    assert np.allclose(res["sigma"], s_true, rtol=1e-3), res
+    assert np.isclose(res["gain"], 2.0, rtol=1e-4) and np.isclose(res["offset"], 0.1, rtol=1e-3)
+    plan.close()

@@ -386,3 +386,28 @@ def test_cg_converges_to_the_dense_solution_and_error_decreases():
     assert np.allclose(r["x"], xd, atol=1e-10)
     # and it matches the closed form of eq. 12 used by the fast path
     assert np.allclose(r["x"], O.tikhonov(y, psf, dec, tau, xbar), atol=1e-10)
+
+
+# ---------------------------------------------------------------------------
+# Gaussian PSF fit objective
+# ---------------------------------------------------------------------------
+
+def test_gaussian_taps_match_the_input_generator():
+    from synth import gaussian_psf
+    s, size = (1.3, 0.9, 1.7), (9, 7, 11)
+    assert np.allclose(O.gaussian_psf_taps(s, size), gaussian_psf(s, size), rtol=1e-14, atol=0)
+
+
+def test_psf_fit_objective_is_zero_at_the_truth_and_grows_away():
+    rng = np.random.default_rng(41)
+    shape, dec = (8, 16, 16), (2, 2, 2)
+    x = rng.random(shape)
+    size, s_true = (9, 9, 7), (1.2, 0.8, 1.5)
+    y = 2.0 * O.forward(x, O.gaussian_psf_taps(s_true, size), dec) + 0.1
+    r0, a, b = O.psf_fit_objective(s_true, size, x, y, dec)
+    assert r0 <= 1e-24 * (y ** 2).sum() and np.isclose(a, 2.0) and np.isclose(b, 0.1)
+    for ax in range(3):
+        for f in (0.9, 1.1):
+            s = list(s_true)
+            s[ax] *= f
+            assert O.psf_fit_objective(s, size, x, y, dec)[0] > 1e3 * max(r0, 1e-30)
