@@ -229,9 +229,9 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
 // -n halo row of the rho region, warp 1 the -m halo column; x halo rows come
 // through warps 0 and 7, halo columns through warp 1.  Same algebra, modes
 // and statistics as k_tv; the statistics of a thread's four voxels are summed
-// in FP32 (sqrtf for ||g||) and those four-term sums accumulated in FP64
-// (FP64 arithmetic is slow on this GPU; a four-term FP32 sum is exact to a
-// few ulps).  Shared rows are padded so that m0 sits at column 4 (16-byte
+// in FP32 (sqrtf for ||g||) and accumulated over its planes in compensated
+// FP32 (Kahan), then reduced across the CTA in FP64 (FP64 arithmetic is slow
+// on this GPU).  Shared rows are padded so that m0 sits at column 4 (16-byte
 // aligned); column 3 is m0-1 and column 132 is m0+128.
 // ---------------------------------------------------------------------------
 constexpr int V4M = 128;
@@ -302,7 +302,16 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
     }
   };
 
-  double q[NQ] = {0, 0, 0, 0, 0, 0};
+  // per-thread statistics: compensated (Kahan) FP32 sums over the thread's
+  // planes, converted to FP64 once for the CTA reduction (FP64 arithmetic is
+  // slow on this GPU)
+  float qs[NQ] = {0, 0, 0, 0, 0, 0}, qc[NQ] = {0, 0, 0, 0, 0, 0};
+  auto kadd = [&](int k, float v) {
+    const float y = v - qc[k];
+    const float t = qs[k] + y;
+    qc[k] = (t - qs[k]) - y;
+    qs[k] = t;
+  };
   float4 r2prev = make_float4(0, 0, 0, 0), u2prev = r2prev, e2prev = r2prev;
   fetch_x(s0 - 1, xs);
   fetch_x(s0, xs + XP);
@@ -376,10 +385,10 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
         }
       }
       if (STATS && interior && own_plane) {
-        q[0] += f0;
-        q[1] += f1;
-        q[2] += f2;
-        q[3] += f3;
+        kadd(0, f0);
+        kadd(1, f1);
+        kadd(2, f2);
+        kadd(3, f3);
       }
       if (MODE != 1 && interior && own_plane) {
         const long long gi = pl + o_in;
@@ -443,7 +452,7 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
             pv[i] = psi_v;
             f5 += ltd * ltd;
           }
-          q[5] += f5;
+          kadd(5, f5);
           if (MODE != 1) {
             const float4 old = ld4(psi + gi);
             float f4s = 0.f;
@@ -452,7 +461,7 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
               const float dl = pv[i] - f4(old, i);
               f4s += dl * dl;
             }
-            q[4] += f4s;
+            kadd(4, f4s);
           }
           st4(psi + gi, make_float4(pv[0], pv[1], pv[2], pv[3]));
         }
@@ -472,7 +481,7 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
-      const double v = warp_sum_d(q[k]);
+      const double v = warp_sum_d((double)qs[k] - (double)qc[k]);
       if (lane == 0) red[k][warp] = v;
     }
     __syncthreads();
