@@ -5,12 +5,15 @@
 //
 // Activations and gradients are BF16, channels last ([voxel][channel]);
 // master weights, Adam moments and reductions are FP32 / FP64.  Every 3x3x3
-// convolution is an implicit GEMM on the tensor cores (mma.sync m16n8k16 BF16
-// with FP32 accumulation): rows are voxels, columns output channels, and the
-// reduction runs over (tap, input channel) in chunks of 16 staged per warp in
-// shared memory and read with ldmatrix.  The data gradient is the same kernel
-// with flipped, transposed weights; the weight gradient is a second GEMM
-// (channels x k over voxels) split over voxel groups.
+// convolution with 16-multiple input channels is an implicit GEMM on the
+// tensor cores: rows are voxels, columns output channels, the reduction runs
+// over (tap, input channel).  Two kernels compute it: k_conv3 (mma.sync
+// m16n8k16 BF16, FP32 accumulation; input brick + halo in shared memory, taps
+// read by ldmatrix) and k_conv3_tc (tcgen05.mma with TMEM accumulators, a
+// persistent CTA per row marching over s), chosen per layer shape.  The data
+// gradient is the same convolution with flipped, transposed weights; the
+// weight gradient is a third GEMM (channels x k over voxels) split over voxel
+// groups.  The first layer (one input channel) is a plain FP32 stencil.
 #include <cuda_bf16.h>
 #include <stdio.h>
 #include <string.h>
