@@ -20,7 +20,7 @@ constexpr int ct_radix(int n, int i) { return (ct_rem(n) > 1 && i == 0) ? ct_rem
 constexpr int ct_ns(int n, int i) { return i == 0 ? 1 : ct_ns(n, i - 1) * ct_radix(n, i - 1); }
 
 template <int N> __host__ __device__ constexpr bool ct_supported() {
-  return N == 128 || N == 256 || N == 512;
+  return N == 32 || N == 64 || N == 128 || N == 256 || N == 512;
 }
 
 // Shared-memory position of line element i: with PAD one spare slot follows

@@ -565,10 +565,10 @@ static void m_launch_shape(const Geometry& g, size_t csz, int& L, int& Hp, int& 
   smem = (size_t)L * Hp * csz;
 }
 
-// lengths with a compile-time plan (FP32 only)
+// lengths with a compile-time plan (FP32 only; the s pass takes 256)
 template <typename T> static int ct_len(int n, const FftAxis& f) {
   if (sizeof(T) != 4 || f.e != 16) return 0;
-  return (n == 128 || n == 256 || n == 512) ? n : 0;
+  return (n == 32 || n == 64 || n == 128 || n == 256 || n == 512) ? n : 0;
 }
 
 template <typename T, int EMAX, int NC>
@@ -615,6 +615,8 @@ static cudaError_t rfft_fwd_t(const Plan& p, const Geometry& g, const void* in, 
   if (fam3(g.fm)) return rfft_fwd_k<T, Emax<T>::p3, 0>(p, g, in, out, tw);
   if constexpr (sizeof(T) == 4) {
     switch (ct_len<T>(g.M / 2, g.fm)) {
+      case 32: return rfft_fwd_k<T, 16, 32>(p, g, in, out, tw);
+      case 64: return rfft_fwd_k<T, 16, 64>(p, g, in, out, tw);
       case 128: return rfft_fwd_k<T, 16, 128>(p, g, in, out, tw);
       case 256: return rfft_fwd_k<T, 16, 256>(p, g, in, out, tw);
       case 512: return rfft_fwd_k<T, 16, 512>(p, g, in, out, tw);
@@ -629,6 +631,8 @@ static cudaError_t rfft_inv_t(const Plan& p, const Geometry& g, const void* in, 
   if (fam3(g.fm)) return rfft_inv_k<T, Emax<T>::p3, 0>(p, g, in, out, tw, scale);
   if constexpr (sizeof(T) == 4) {
     switch (ct_len<T>(g.M / 2, g.fm)) {
+      case 32: return rfft_inv_k<T, 16, 32>(p, g, in, out, tw, scale);
+      case 64: return rfft_inv_k<T, 16, 64>(p, g, in, out, tw, scale);
       case 128: return rfft_inv_k<T, 16, 128>(p, g, in, out, tw, scale);
       case 256: return rfft_inv_k<T, 16, 256>(p, g, in, out, tw, scale);
       case 512: return rfft_inv_k<T, 16, 512>(p, g, in, out, tw, scale);
@@ -729,6 +733,8 @@ cudaError_t launch_fft_n(const Plan& p, const Geometry& g, void* spec, const voi
               : fft_n_e<double, Emax<double>::p2, 0>(p, g, spec, tw, inverse);
   if (f3) return fft_n_e<float, Emax<float>::p3, 0>(p, g, spec, tw, inverse);
   switch (ct_len<float>(g.N, g.fn)) {
+    case 64: return fft_n_e<float, 16, 64>(p, g, spec, tw, inverse);
+    case 128: return fft_n_e<float, 16, 128>(p, g, spec, tw, inverse);
     case 256: return fft_n_e<float, 16, 256>(p, g, spec, tw, inverse);
     case 512: return fft_n_e<float, 16, 512>(p, g, spec, tw, inverse);
   }
