@@ -50,11 +50,11 @@ STEP_BYTES = 80
 # valid while the kernel's sources hash to the recorded value
 NCU_TRAFFIC = {
     "tv": (502.2e6, ("kernels_tv.cu", "common.cuh"), "3cbcf7bfdb8f474b"),
-    "rfft_m_fwd": (87.3e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "4aa889e8daf20ca8"),
-    "fft_n_fwd": (80.4e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "4aa889e8daf20ca8"),
-    "fft_s": (111.4e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "4aa889e8daf20ca8"),
-    "fft_n_inv": (80.4e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "4aa889e8daf20ca8"),
-    "rfft_m_inv": (90.2e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "common.cuh"), "4aa889e8daf20ca8"),
+    "rfft_m_fwd": (87.3e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "fft_host.cuh", "common.cuh"), "4aa889e8daf20ca8"),
+    "fft_n_fwd": (80.4e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "fft_host.cuh", "common.cuh"), "4aa889e8daf20ca8"),
+    "fft_s": (111.4e6, ("kernels_fft_s.cu", "fft.cuh", "fft_ct.cuh", "fft_host.cuh", "common.cuh"), "4aa889e8daf20ca8"),
+    "fft_n_inv": (80.4e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "fft_host.cuh", "common.cuh"), "4aa889e8daf20ca8"),
+    "rfft_m_inv": (90.2e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "fft_host.cuh", "common.cuh"), "4aa889e8daf20ca8"),
 }
 
 

@@ -20,7 +20,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libsr3d.so")
 
-SOURCES = ["api.cu", "kernels_fft.cu", "kernels_tv.cu", "kernels_cg.cu", "unet.cu"]
+SOURCES = ["api.cu", "kernels_fft.cu", "kernels_fft_s.cu", "kernels_tv.cu", "kernels_cg.cu", "unet.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

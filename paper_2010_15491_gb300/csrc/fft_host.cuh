@@ -1,0 +1,44 @@
+// Host-side helpers shared by the FFT-pass translation units.
+#pragma once
+#include "internal.h"
+
+namespace sr3d {
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+template <typename K> static inline cudaError_t allow_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+static inline MAxis maxis(const Geometry& g) {
+  MAxis a;
+  a.M = g.M; a.H = g.M / 2; a.Ml = g.Ml; a.dr = g.dr; a.Ms = g.Ms; a.Mp = g.Mp; a.f = g.fm;
+  return a;
+}
+
+static inline LAxis laxis(int n, int nl, int dc, const FftAxis& f) {
+  LAxis a;
+  a.N = n; a.Nl = nl; a.dc = dc; a.f = f;
+  return a;
+}
+
+static inline bool fam3(const FftAxis& f) { return f.n % 3 == 0; }
+
+static inline void m_launch_shape(const Geometry& g, size_t csz, int& L, int& Hp, int& threads, size_t& smem) {
+  const int H = g.M / 2;
+  const int tpl = H / g.fm.e;
+  L = tpl >= 256 ? 1 : 256 / tpl;
+  Hp = H + (H >= 32 ? (int)(64 / csz) : 0);
+  threads = L * tpl;
+  smem = (size_t)L * Hp * csz;
+}
+
+// lengths with a compile-time plan (FP32 only; the s pass takes 256)
+template <typename T> static inline int ct_len(int n, const FftAxis& f) {
+  if (sizeof(T) != 4 || f.e != 16) return 0;
+  return (n == 32 || n == 64 || n == 128 || n == 256 || n == 512) ? n : 0;
+}
+
+}  // namespace sr3d
