@@ -474,3 +474,52 @@ def test_gaussian_psf_fit(lib):
     assert np.allclose(res["sigma"], s_true, rtol=1e-3), res
     assert np.isclose(res["gain"], 2.0, rtol=1e-4) and np.isclose(res["offset"], 0.1, rtol=1e-3)
     plan.close()
+
+
+@pytest.mark.slow
+def test_headline_error_curve(lib, tag):
+    """256^3 benchmark workload: relative L2 error of the FP32 iterate against
+    the FP64 oracle after 1, 2, 5 and 10 ADMM-TV iterations."""
+    from synth import HEADLINE_256 as W, noise_sigma
+    psf = W.psf()
+    x = W.phantom()
+    clean = O.forward(x, psf, W.dec)
+    y = clean + noise_sigma(clean, W.snr_db) * W.noise()
+    plan = lib.Plan(W.dims, W.dec, psf, "f32")
+    plan.autotune()
+    x0 = O.tikhonov(y, psf, W.dec, W.tau, O.nearest_neighbour(y, W.dec))
+    ks = (1, 2, 5, 10)
+    ref = {}
+    O.admm_tv(y, psf, W.dec, W.lam, W.mu, max(ks), x0,
+              callback=lambda i, xi, u, d: ref.__setitem__(i + 1, xi.copy()) if i + 1 in ks else None)
+    yd = T(y, "f32")
+    for k in ks:
+        xg = plan.empty_hr()
+        plan.admm_tv(yd, xg, W.lam, W.mu, k, tau_init=W.tau)
+        assert rel_l2(H(xg), ref[k], tag(f"x{k}")) < TOL["f32"], k
+    plan.close()
+
+
+@pytest.mark.slow
+def test_aniso512_tikhonov_optimality(lib):
+    """512 x 512 x 256, d = 1x1x4, sigma (1, 1, 2) (the anisotropic CBCT-like
+    workload at full size): the GPU Tikhonov solution satisfies the normal
+    equations of eq. 6, H^T D^T (D H x - y) + tau (x - xbar) = 0, evaluated
+    with the oracle's FP64 operators, to FP32 accuracy."""
+    import synth
+    W = synth.ANISO_512
+    psf = W.psf()
+    m, n, s = W.dims
+    lr = (s // W.dec[2], n // W.dec[1], m // W.dec[0])
+    # the property holds for any observation: a seeded smooth-plus-noise y
+    # instead of the 500-ellipsoid phantom keeps the host work to a few FFTs
+    y = 0.5 + 0.1 * synth.normal(W.seed, 5, int(np.prod(lr))).reshape(lr)
+    lam = O.otf(psf, (s, n, m))
+    plan = lib.Plan(W.dims, W.dec, psf, "f32")
+    xg = H(plan.tikhonov(T(y, "f32"), W.tau, xbar="nearest"))
+    plan.close()
+    xbar = O.nearest_neighbour(y, W.dec)
+    Ht = lambda v: np.real(np.fft.ifftn(np.conj(lam) * np.fft.fftn(v)))  # noqa: E731
+    rhs = Ht(O.zero_fill(y, W.dec)) + W.tau * xbar
+    r = Ht(O.zero_fill(O.forward(xg, psf, W.dec), W.dec)) + W.tau * xg - rhs
+    assert np.linalg.norm(r) <= 1e-5 * np.linalg.norm(rhs)
