@@ -523,6 +523,9 @@ def run_unet(args, rank, world, local_rank):
 
 
 WEIGHTS = os.path.join(ROOT, "paper_2010_15491_gb300", "weights", "unet_warmstart.npy")
+# the same network trained on targets after 1000 ADMM-TV iterations (closer to
+# convergence than the 300 of the recipe); reported beside it when present
+WEIGHTS_REF1000 = os.path.join(ROOT, "paper_2010_15491_gb300", "weights", "unet_warmstart_ref1000.npy")
 # forward multiply-adds per HR voxel of the warm-start U-Net: ten 3x3x3 layers
 # at full, 1/8 and 1/64 voxel density, plus the 1x1x1 head
 UNET_MACS = (27 * (1 * 16 + 16 * 16 + 48 * 16 + 16 * 16) + 27 * (16 * 32 + 32 * 32 + 96 * 32 + 32 * 32) / 8
@@ -554,6 +557,10 @@ def run_warmstart(args, rank, world, local_rank):
     plan.autotune()
     net = sr3d.UNet()
     net.set_params(np.load(WEIGHTS))
+    net2 = None
+    if os.path.exists(WEIGHTS_REF1000):
+        net2 = sr3d.UNet()
+        net2.set_params(np.load(WEIGHTS_REF1000))
     ys = [W.observe(plan, torch.from_numpy(f.result()).cuda(), w.snr_db, 90000 + j) for j, f in enumerate(futs)]
     pool.shutdown()
     tol, every, cap = 1e-4, 10, 5000
@@ -568,7 +575,9 @@ def run_warmstart(args, rank, world, local_rank):
     for _ in range(max(args.warmup, 1)):  # loads every kernel and graph once
         W.solve(plan, ys[0], w.lam, w.mu, w.tau, tol, 2 * every, eval_every=every)
         W.solve(plan, ys[0], w.lam, w.mu, w.tau, tol, 2 * every, eval_every=every, net=net)
-    cold, warm, warm_d0 = [], [], []
+    cold, warm, warm_d0, warm2 = [], [], [], []
+    if net2 is not None:
+        W.solve(plan, ys[0], w.lam, w.mu, w.tau, tol, 2 * every, eval_every=every, net=net2)
     with ClockSampler(torch.cuda.current_device()) as clk:
         for y in ys:
             (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every))
@@ -578,6 +587,10 @@ def run_warmstart(args, rank, world, local_rank):
             (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every, net=net,
                                                 dual=False))
             warm_d0.append((ms, st["iters"], st["converged"]))
+            if net2 is not None:
+                (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every,
+                                                    net=net2))
+                warm2.append((ms, st["iters"], st["converged"]))
     # parts of the warm start, on the first volume
     _, t_tik = timed(lambda: plan.tikhonov(ys[0], w.tau, xbar="nearest"))
     xt = plan.tikhonov(ys[0], w.tau, xbar="nearest")
@@ -602,7 +615,9 @@ def run_warmstart(args, rank, world, local_rank):
             "cold_ms": mean([c[0] for c in cold]), "cold_iters": [c[1] for c in cold],
             "warm_iters": [c[1] for c in warm], "warm_over_cold": mean([c[0] for c in warm]) / mean([c[0] for c in cold]),
             "ablation_warm_d0_zero": {"ms": mean([c[0] for c in warm_d0]), "iters": [c[1] for c in warm_d0]},
-            "converged": all(c[2] for c in cold + warm + warm_d0),
+            "warm_targets_1000": ({"ms": mean([c[0] for c in warm2]), "iters": [c[1] for c in warm2]}
+                                  if warm2 else None),
+            "converged": all(c[2] for c in cold + warm + warm_d0 + warm2),
             "warm_parts_ms": {"tikhonov": t_tik, "unet": t_net, "dual_init": t_dual},
             "unet_roofline": {"bound": "tensor", "achieved": unet_tflops, "peak": bf16, "unit": "TFLOP/s",
                               "frac": unet_tflops / bf16 if bf16 else None,
@@ -610,6 +625,8 @@ def run_warmstart(args, rank, world, local_rank):
             "clocks": clk.summary()}), flush=True)
     plan.close()
     net.close()
+    if net2 is not None:
+        net2.close()
 
 
 def main():
