@@ -299,7 +299,7 @@ def run_ours(args, w, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_desc(w), "voxels": w.voxels, "iters_per_step": w.iters,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2": "working set ~0.65 GB > L2; no flush"},
+                       "l2": "working set ~0.65 GB > L2; no flush", "schedule": plan.schedule()},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "kernels": kern}
     if world == 1 and not args.no_cpu_baseline:

@@ -176,6 +176,15 @@ int sr3d_tv_step(sr3d_plan_t plan, const void* x_dev, const void* d_in_dev, void
  * split the same work differently).  Errors: INVALID_ARG, CUDA, OOM. */
 int sr3d_autotune(sr3d_plan_t plan, int reps);
 
+/* The tile schedule the plan launches (the defaults, or the autotuner's
+ * choice).  tv_planes > 0 first sets the number of s planes each CTA of the
+ * TV kernel marches over (the last CTA along s takes the remainder; results
+ * do not depend on it); 0 only queries.  sched (if not NULL) receives
+ * sched[0] = m-slots per CTA of the n pass, sched[1] = m-slots per CTA of the
+ * s pass, sched[2] = TV planes per CTA.  Errors: INVALID_ARG (tv_planes
+ * negative or between 1 and 3). */
+int sr3d_schedule(sr3d_plan_t plan, int tv_planes, int sched[3]);
+
 /* Per-kernel accounting.  Kernel kinds: SR3D_K_TV (fused u/d/Theta step),
  * SR3D_K_RFFT_FWD / SR3D_K_RFFT_INV (real FFT along m), SR3D_K_FFTN_FWD /
  * SR3D_K_FFTN_INV (FFT along n), SR3D_K_FFTS (FFT along s, with the class

@@ -32,6 +32,7 @@ EXPORTED = [
     "sr3d_plan", "sr3d_destroy", "sr3d_forward", "sr3d_tikhonov", "sr3d_admm_tv", "sr3d_admm_tv_host",
     "sr3d_last_error", "sr3d_get_otf", "sr3d_fft3", "sr3d_xstep", "sr3d_tv_step", "sr3d_plan_info",
     "sr3d_profile", "sr3d_profile_read", "sr3d_tikhonov_noalloc", "sr3d_admm_tv_batched", "sr3d_autotune",
+    "sr3d_schedule",
     "sr3d_separable", "sr3d_set_tv", "sr3d_tikhonov_grad", "sr3d_tikhonov_cg", "sr3d_set_psf",
     "sr3d_dual_init", "sr3d_unet_param_count", "sr3d_unet_create", "sr3d_unet_destroy", "sr3d_unet_set_params",
     "sr3d_unet_get_params", "sr3d_unet_forward", "sr3d_unet_train_step", "sr3d_unet_read", "sr3d_unet_set_path",
@@ -91,6 +92,7 @@ def load() -> ctypes.CDLL:
         "sr3d_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "sr3d_tikhonov_noalloc": (i, [ctypes.POINTER(Desc), vp, vp, d, vp]),
         "sr3d_autotune": (i, [vp, i]),
+        "sr3d_schedule": (i, [vp, i, ctypes.POINTER(i)]),
         "sr3d_admm_tv_batched": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d), i]),
         "sr3d_dual_init": (i, [vp, vp, d, d, vp]),
@@ -236,6 +238,13 @@ class Plan:
     def autotune(self, reps: int = 3):
         """Times candidate tile schedules and keeps the fastest (cached per geometry)."""
         _check(load().sr3d_autotune(self._h, int(reps)))
+
+    def schedule(self, tv_planes: int = 0) -> dict:
+        """The tile schedule the plan launches (sr3d_schedule); tv_planes > 0
+        first sets the TV kernel's s planes per CTA."""
+        v = (ctypes.c_int * 3)()
+        _check(load().sr3d_schedule(self._h, int(tv_planes), v))
+        return {"n_pass_slots": v[0], "s_pass_slots": v[1], "tv_planes": v[2]}
 
     def profile(self, on: bool = True):
         """Resets the per-kernel accounting; with on=True also times every launch."""

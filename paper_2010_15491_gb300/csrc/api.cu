@@ -628,6 +628,30 @@ int sr3d_plan_info(sr3d_plan_t plan, int sizes[9], long long* bytes) {
   return SR3D_OK;
 }
 
+int sr3d_schedule(sr3d_plan_t plan, int tv_planes, int sched[3]) {
+  if (!plan) return fail(SR3D_ERR_INVALID_ARG, "NULL plan");
+  // at least 4 planes per CTA: the per-CTA partial sums are sized for that
+  if (tv_planes < 0 || (tv_planes > 0 && tv_planes < 4)) return fail(SR3D_ERR_INVALID_ARG, "tv_planes must be 0 or >= 4");
+  Plan& p = plan->p;
+  Geometry& g = p.hr;
+  if (tv_planes > 0 && tv_planes != g.ts_tv) {
+    TRY(sync_plan(p));
+    g.ts_tv = tv_planes;
+    if (p.iter_graph) {  // captured launches hold the old grid
+      cudaGraphExecDestroy(p.iter_graph);
+      p.iter_graph = nullptr;
+    }
+    drop_eval_graphs(p);
+    ++p.version;
+  }
+  if (sched) {
+    sched[0] = g.tw_n;
+    sched[1] = g.tw_s;
+    sched[2] = g.ts_tv > 0 ? g.ts_tv : tv_default_ts(g);
+  }
+  return SR3D_OK;
+}
+
 int sr3d_dual_init(sr3d_plan_t plan, const void* x, double lambda, double rho, void* d) {
   if (!plan || !x || !d) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
   if (!(rho > 0) || !(lambda > 0)) return fail(SR3D_ERR_INVALID_ARG, "need rho > 0 and lambda > 0");
@@ -1109,8 +1133,10 @@ extern "C" int sr3d_autotune(sr3d_plan_t plan, int reps) {
     // TV planes per CTA
     {
       float bt = 1e30f;
-      for (int ts : {4, 8, 16, 32}) {
-        if (ts > g.S) continue;
+      int cand[8];
+      const int nc = tv_ts_candidates(p, cand, 8);
+      for (int ci = 0; ci < nc; ++ci) {
+        const int ts = cand[ci];
         g.ts_tv = ts;
         float ms = 0;
         TRY(time_ms(p, reps, &ms, [&]() -> int {

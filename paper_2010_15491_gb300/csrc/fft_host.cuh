@@ -7,6 +7,9 @@ namespace sr3d {
 // ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
+// Opts a kernel in to more than 48 KB of dynamic shared memory.  The kernels
+// launched through it declare no static shared memory, so bytes is their
+// whole footprint.
 template <typename K> static inline cudaError_t allow_smem(K kernel, size_t bytes) {
   if (bytes <= 48 * 1024) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

@@ -151,6 +151,8 @@ cudaError_t launch_tv(const Plan& p, const void* x, const void* din, void* dout,
                       double thr, int mode, bool stats);
 long long tv_blocks(const Geometry& g);
 int tv_default_ts(const Geometry& g);
+// planes-per-CTA values for the autotuner to time (at most cap, into out)
+int tv_ts_candidates(const Plan& p, int* out, int cap);
 cudaError_t launch_finalize(const Plan& p, int hist_index, double lam_tv, double mu, double inv_nl,
                             bool with_data);
 cudaError_t launch_twiddle(const Plan& p, void* tw, int n);

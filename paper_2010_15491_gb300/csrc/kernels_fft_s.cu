@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(NC > 0 ? 256 : 512, NC > 0 ? 3 : 1) k_fft_s(cp
   if (MODE >= S_TIK_GEN && MODE <= S_FOLD) {
     double acc = solve_tile<T, MODE, STATS, DR_, DC_, DS_>(sm, TW, G, a0, b0, Ms, sv, tid, nthr);
     if (STATS) {
-      __shared__ double red[32];
+      double* red = reinterpret_cast<double*>(tws + (NC > 0 ? NC : 0));  // 32 slots after the tile (and twiddles)
       acc = warp_sum(acc);
       const int lane = tid & 31, warp = tid >> 5;
       if (lane == 0) red[warp] = acc;
@@ -353,6 +353,7 @@ static cudaError_t fft_s_k(const Plan& p, const Geometry& g, void* spec, const v
   const int TW = g.tw_s, G = g.g_s;
   size_t smem = (size_t)g.S * TW * G * sizeof(cplx<T>);
   if (NC > 0) smem += (size_t)NC * sizeof(cplx<T>);
+  if (STATS) smem += 32 * sizeof(double);  // the CTA's reduction slots
   dim3 grid((g.Ms + TW - 1) / TW, g.N / G);
   LAxis a = laxis(g.S, g.Sl, g.ds, g.fs);
   cudaError_t e;

@@ -511,6 +511,49 @@ int tv_default_ts(const Geometry& g) {
 
 static int tv_ts(const Geometry& g) { return g.ts_tv > 0 ? g.ts_tv : tv_default_ts(g); }
 
+// resident CTAs per SM of the plain ADMM-step TV kernel the plan launches
+template <typename T>
+static cudaError_t tv_per_sm(const Plan& p, int* per_sm) {
+  if (tv_vec4(p)) {
+    const size_t smem = tv4_smem(false);
+    cudaError_t e = cudaFuncSetAttribute(k_tv4<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tv4<0, false>, 32 * TN, smem);
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tv<T, 0, false>, TM * TN, 0);
+}
+
+int tv_ts_candidates(const Plan& p, int* out, int cap) {
+  const Geometry& g = p.hr;
+  int n = 0;
+  auto add = [&](int ts) {
+    if (ts < 4 || ts > g.S || n >= cap) return;
+    for (int i = 0; i < n; ++i)
+      if (out[i] == ts) return;
+    out[n++] = ts;
+  };
+  for (int ts : {4, 8, 16, 32}) add(ts);
+  // Every CTA marches over the same number of planes, so a partly filled last
+  // wave of CTAs holds the bandwidth of a few SMs for a whole CTA lifetime:
+  // add the plane counts whose grid fills 1..4 waves of resident CTAs.
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = p.dtype ? tv_per_sm<double>(p, &per_sm) : tv_per_sm<float>(p, &per_sm);
+  if (e != cudaSuccess || per_sm <= 0) {
+    cudaGetLastError();
+    return n;
+  }
+  const long long tiles = tv_vec4(p) ? (long long)(g.M / V4M) * (g.N / TN)
+                                     : (long long)((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN);
+  const long long slots = (long long)sms * per_sm;
+  for (int w = 1; w <= 4; ++w) {
+    const long long zmax = w * slots / tiles;  // CTAs along s that fit in w waves
+    if (zmax >= 1) add((int)((g.S + zmax - 1) / zmax));
+  }
+  return n;
+}
+
 long long tv_blocks(const Geometry& g) {
   // an upper bound covering both variants (the vectorised one has 4x fewer m
   // tiles) and every planes-per-CTA choice of at least 4
@@ -642,8 +685,10 @@ static long long tv_launch_blocks(const Plan& p) {
 
 cudaError_t launch_finalize(const Plan& p, int hist_index, double lam_tv, double mu, double inv_nl,
                             bool with_data) {
-  k_finalize<<<1, 256, 0, p.stream>>>(p.partial, tv_launch_blocks(p), p.partial_s, p.n_s_blocks, lam_tv, mu, inv_nl,
-                                      with_data ? 1 : 0, p.result, p.hist, hist_index, p.hcount, p.hist_cap);
+  // the partials of the CTAs the current schedules launch (the buffers hold
+  // the largest grid any schedule has used)
+  k_finalize<<<1, 256, 0, p.stream>>>(p.partial, tv_launch_blocks(p), p.partial_s, s_pass_blocks(p.hr), lam_tv, mu,
+                                      inv_nl, with_data ? 1 : 0, p.result, p.hist, hist_index, p.hcount, p.hist_cap);
   return cudaGetLastError();
 }
 

@@ -67,3 +67,49 @@ def test_autotuned_plans_keep_parity(lib):
         lib.admm_tv_batched([p], [yd], xs, [1e-3], [1e-2], [1e-2], 6)
         assert torch.equal(xs[0], x)
         p.close()
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_tv_planes_per_cta_leave_results_unchanged(lib, dtype):
+    """The TV kernel's planes per CTA (sr3d_schedule), including counts that do
+    not divide S, split the same per-voxel work differently: the iterate is
+    bit-identical and the statistics agree to reduction order.  The statistics
+    after a schedule change sum only the CTAs of the new grid."""
+    import torch
+    dims, dec = (128, 64, 48), (2, 2, 2)
+    psf, xt, y = make_problem(dims, dec, seed=61)
+    td = torch.float32 if dtype == "f32" else torch.float64
+    yd = torch.tensor(y, dtype=td, device="cuda")
+    p = lib.Plan(dims, dec, psf, dtype)
+    base = p.schedule()
+    assert base["tv_planes"] >= 4
+    runs = {}
+    for ts in (base["tv_planes"], 4, 5, 7, 37, 64, base["tv_planes"]):
+        assert p.schedule(ts)["tv_planes"] == ts
+        x = p.empty_hr()
+        st = p.admm_tv(yd, x, 1e-3, 1e-2, 12, tau_init=1e-2, eval_every=3, hist_len=8)
+        runs.setdefault(ts, []).append((x, st))
+    x0, st0 = runs[base["tv_planes"]][0]
+    for ts, rs in runs.items():
+        for x, st in rs:
+            assert torch.equal(x, x0), ts
+            assert st["evals"] == st0["evals"]
+            for a, b in zip(st["objective_hist"], st0["objective_hist"]):
+                assert abs(a - b) <= 1e-9 * abs(b), ts
+            for k in ("objective", "data_term", "tv_term", "primal", "dual"):
+                assert abs(st[k] - st0[k]) <= 1e-9 * abs(st0[k]) + 1e-300, (ts, k)
+    # the autotuner may change every schedule; statistics still match a fresh plan
+    p.autotune(2)
+    x = p.empty_hr()
+    st = p.admm_tv(yd, x, 1e-3, 1e-2, 12, tau_init=1e-2, eval_every=3)
+    q = lib.Plan(dims, dec, psf, dtype)
+    xq = q.empty_hr()
+    sq = q.admm_tv(yd, xq, 1e-3, 1e-2, 12, tau_init=1e-2, eval_every=3)
+    for k in ("objective", "data_term", "tv_term", "primal", "dual"):
+        assert abs(st[k] - sq[k]) <= 1e-6 * abs(sq[k]) + 1e-300, k
+    with pytest.raises(lib.Sr3dError):
+        p.schedule(3)
+    with pytest.raises(lib.Sr3dError):
+        p.schedule(-1)
+    p.close()
+    q.close()
