@@ -177,13 +177,16 @@ int sr3d_tv_step(sr3d_plan_t plan, const void* x_dev, const void* d_in_dev, void
 int sr3d_autotune(sr3d_plan_t plan, int reps);
 
 /* The tile schedule the plan launches (the defaults, or the autotuner's
- * choice).  tv_planes > 0 first sets the number of s planes each CTA of the
- * TV kernel marches over (the last CTA along s takes the remainder; results
- * do not depend on it); 0 only queries.  sched (if not NULL) receives
- * sched[0] = m-slots per CTA of the n pass, sched[1] = m-slots per CTA of the
- * s pass, sched[2] = TV planes per CTA.  Errors: INVALID_ARG (tv_planes
- * negative or between 1 and 3). */
-int sr3d_schedule(sr3d_plan_t plan, int tv_planes, int sched[3]);
+ * choice), and a way to set it.  Entries: [0] = m-slots per CTA of the n
+ * pass, [1] = m-slots per CTA of the s pass (a multiple of d_r), [2] = s
+ * planes each CTA of the TV kernel marches over (the last CTA along s takes
+ * the remainder).  set (may be NULL) gives new values, entries <= 0 keeping
+ * the current one; results do not depend on the schedule (it only splits the
+ * same work differently).  sched (may be NULL) receives the schedule in
+ * force.  Errors: INVALID_ARG (a width the pass's kernel or the plan's
+ * solve-order buffers cannot take, or fewer than 4 TV planes; nothing is
+ * changed), CUDA. */
+int sr3d_schedule(sr3d_plan_t plan, const int set[3], int sched[3]);
 
 /* Per-kernel accounting.  Kernel kinds: SR3D_K_TV (fused u/d/Theta step),
  * SR3D_K_RFFT_FWD / SR3D_K_RFFT_INV (real FFT along m), SR3D_K_FFTN_FWD /

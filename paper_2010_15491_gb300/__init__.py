@@ -92,7 +92,7 @@ def load() -> ctypes.CDLL:
         "sr3d_profile_read": (i, [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)]),
         "sr3d_tikhonov_noalloc": (i, [ctypes.POINTER(Desc), vp, vp, d, vp]),
         "sr3d_autotune": (i, [vp, i]),
-        "sr3d_schedule": (i, [vp, i, ctypes.POINTER(i)]),
+        "sr3d_schedule": (i, [vp, ctypes.POINTER(i), ctypes.POINTER(i)]),
         "sr3d_admm_tv_batched": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                      ctypes.POINTER(d), ctypes.POINTER(d), ctypes.POINTER(d), i]),
         "sr3d_dual_init": (i, [vp, vp, d, d, vp]),
@@ -239,11 +239,14 @@ class Plan:
         """Times candidate tile schedules and keeps the fastest (cached per geometry)."""
         _check(load().sr3d_autotune(self._h, int(reps)))
 
-    def schedule(self, tv_planes: int = 0) -> dict:
-        """The tile schedule the plan launches (sr3d_schedule); tv_planes > 0
-        first sets the TV kernel's s planes per CTA."""
+    def schedule(self, n_pass_slots: int = 0, s_pass_slots: int = 0, tv_planes: int = 0) -> dict:
+        """The tile schedule the plan launches (sr3d_schedule); positive
+        arguments first set the n-pass and s-pass tile widths (m-slots per
+        CTA) and the TV kernel's s planes per CTA."""
         v = (ctypes.c_int * 3)()
-        _check(load().sr3d_schedule(self._h, int(tv_planes), v))
+        req = (int(n_pass_slots), int(s_pass_slots), int(tv_planes))
+        setv = (ctypes.c_int * 3)(*req) if any(r > 0 for r in req) else None
+        _check(load().sr3d_schedule(self._h, setv, v))
         return {"n_pass_slots": v[0], "s_pass_slots": v[1], "tv_planes": v[2]}
 
     def profile(self, on: bool = True):

@@ -13,6 +13,7 @@
 #include <tuple>
 #include <string>
 #include <algorithm>
+#include <initializer_list>
 #include <vector>
 
 #include "internal.h"
@@ -628,21 +629,58 @@ int sr3d_plan_info(sr3d_plan_t plan, int sizes[9], long long* bytes) {
   return SR3D_OK;
 }
 
-int sr3d_schedule(sr3d_plan_t plan, int tv_planes, int sched[3]) {
+static int realloc_partials(Plan& p);
+
+// Tile widths the n pass and the s pass (with its class solve) accept for
+// this volume: the launch limits of their kernels and, for the s pass, the
+// solve-order buffers allocated with the plan.
+static bool tw_n_valid(const Geometry& g, size_t csz, int tw) {
+  const int tpl = g.N / g.fn.e;
+  const int cap = (g.Ms + 1) & ~1;
+  return tw >= 1 && tw <= 64 && tw <= cap && tw * tpl <= 256 && (size_t)tw * g.N * csz <= 96 * 1024 &&
+         (tw == 1 || tw % 2 == 0);
+}
+
+static bool tw_s_valid(const Plan& p, const Geometry& g, size_t csz, int tw) {
+  const int tpl = g.S / g.fs.e;
+  const int cap = ((g.Ms + 2 * g.dr - 1) / (2 * g.dr)) * (2 * g.dr);
+  if (tw < g.dr || tw % g.dr || tw > cap || (long long)tw * g.g_s * tpl > 512 ||
+      (size_t)tw * g.g_s * g.S * csz > 160 * 1024)
+    return false;
+  Geometry gc = g;
+  gc.tw_s = tw;
+  return solve_lam_elems(gc) <= p.lam_solve_cap && solve_yhat_elems(gc) <= p.yhat_solve_cap;
+}
+
+int sr3d_schedule(sr3d_plan_t plan, const int set[3], int sched[3]) {
   if (!plan) return fail(SR3D_ERR_INVALID_ARG, "NULL plan");
-  // at least 4 planes per CTA: the per-CTA partial sums are sized for that
-  if (tv_planes < 0 || (tv_planes > 0 && tv_planes < 4)) return fail(SR3D_ERR_INVALID_ARG, "tv_planes must be 0 or >= 4");
   Plan& p = plan->p;
   Geometry& g = p.hr;
-  if (tv_planes > 0 && tv_planes != g.ts_tv) {
-    TRY(sync_plan(p));
-    g.ts_tv = tv_planes;
-    if (p.iter_graph) {  // captured launches hold the old grid
-      cudaGraphExecDestroy(p.iter_graph);
-      p.iter_graph = nullptr;
+  const size_t csz = 2 * p.esz;
+  if (set) {
+    if (set[0] > 0 && !tw_n_valid(g, csz, set[0]))
+      return fail(SR3D_ERR_INVALID_ARG, "n-pass tile width %d does not fit this volume", set[0]);
+    if (set[1] > 0 && !tw_s_valid(p, g, csz, set[1]))
+      return fail(SR3D_ERR_INVALID_ARG, "s-pass tile width %d does not fit this volume", set[1]);
+    // at least 4 planes per CTA: the per-CTA partial sums are sized for that
+    if (set[2] > 0 && set[2] < 4) return fail(SR3D_ERR_INVALID_ARG, "TV planes per CTA must be >= 4");
+    const int tn = set[0] > 0 ? set[0] : g.tw_n, tws = set[1] > 0 ? set[1] : g.tw_s;
+    const int tv = set[2] > 0 ? set[2] : g.ts_tv;
+    if (tn != g.tw_n || tws != g.tw_s || tv != g.ts_tv) {
+      TRY(sync_plan(p));
+      g.tw_n = tn;
+      g.tw_s = tws;
+      g.ts_tv = tv;
+      TRY(realloc_partials(p));
+      CK(launch_perm_lam(p, p.lam, p.lam_solve));  // Lambda in the new solve order
+      if (p.iter_graph) {  // captured launches hold the old grids
+        cudaGraphExecDestroy(p.iter_graph);
+        p.iter_graph = nullptr;
+      }
+      drop_eval_graphs(p);
+      ++p.version;
+      TRY(sync_plan(p));
     }
-    drop_eval_graphs(p);
-    ++p.version;
   }
   if (sched) {
     sched[0] = g.tw_n;
@@ -1048,6 +1086,19 @@ static int time_ms(Plan& p, int reps, float* ms, const std::function<int()>& f) 
   return rc;
 }
 
+// Tile widths to time: the given ones, plus every multiple of step up to hi
+// whose tiles cover the ms m-slots with at most one step of padding (the
+// m-slot count of a half spectrum, (m_l / 2 + 1) d_r, is rarely a power of
+// two, and a nearly empty last tile costs a whole CTA lifetime per row).
+static std::vector<int> pad_candidates(std::initializer_list<int> base, int ms, int step, int hi) {
+  std::vector<int> out(base);
+  for (int tw = step; tw <= hi; tw += step) {
+    const int pad = (ms + tw - 1) / tw * tw - ms;
+    if (pad <= step && std::find(out.begin(), out.end(), tw) == out.end()) out.push_back(tw);
+  }
+  return out;
+}
+
 static int realloc_partials(Plan& p) {
   const long long ns = s_pass_blocks(p.hr);
   if (ns > p.n_s_blocks) {
@@ -1087,12 +1138,9 @@ extern "C" int sr3d_autotune(sr3d_plan_t plan, int reps) {
     CK(cudaMemsetAsync(p.theta, 0, (size_t)g.V() * p.esz, p.stream));
     // n pass tile width
     {
-      const int tpl = g.N / g.fn.e;
-      const int cap = (g.Ms + 1) & ~1;
       float bt = 1e30f;
-      for (int tw : {g.tw_n / 2, g.tw_n, g.tw_n * 2, g.tw_n * 4}) {
-        if (tw < 1 || tw > 64 || tw > cap || tw * tpl > 256 || (size_t)tw * g.N * csz > 96 * 1024) continue;
-        if (tw > 1 && tw % 2) continue;
+      for (int tw : pad_candidates({g.tw_n / 2, g.tw_n, g.tw_n * 2, g.tw_n * 4}, g.Ms, 2, 64)) {
+        if (!tw_n_valid(g, csz, tw)) continue;
         g.tw_n = tw;
         float ms = 0;
         TRY(time_ms(p, reps, &ms, [&]() -> int {
@@ -1106,17 +1154,12 @@ extern "C" int sr3d_autotune(sr3d_plan_t plan, int reps) {
     }
     // s pass (ADMM class solve) tile width; Lambda is re-permuted per candidate
     {
-      const int tpl = g.S / g.fs.e;
       const int cap = ((g.Ms + 2 * g.dr - 1) / (2 * g.dr)) * (2 * g.dr);
       float bt = 1e30f;
       const int tw0 = g.tw_s;
-      for (int tw : {tw0 / 2, tw0, tw0 * 2}) {
+      for (int tw : pad_candidates({tw0 / 2, tw0, tw0 * 2}, g.Ms, g.dr, cap)) {
         tw = (tw / g.dr) * g.dr;
-        if (tw < g.dr || tw > cap || (long long)tw * g.g_s * tpl > 512 || (size_t)tw * g.g_s * g.S * csz > 160 * 1024)
-          continue;
-        Geometry gc = g;
-        gc.tw_s = tw;
-        if (solve_lam_elems(gc) > p.lam_solve_cap || solve_yhat_elems(gc) > p.yhat_solve_cap) continue;
+        if (!tw_s_valid(p, g, csz, tw)) continue;
         g.tw_s = tw;
         TRY(realloc_partials(p));
         CK(launch_perm_lam(p, p.lam, p.lam_solve));
