@@ -49,19 +49,22 @@ STEP_BYTES = 80
 # kernel from one ncu capture of this workload (profiles/admm_tv_256_kernels_ncu.md),
 # valid while the kernel's sources hash to the recorded value
 NCU_TRAFFIC = {
-    "tv": (502.2e6, ("kernels_tv.cu", "common.cuh"), "3cbcf7bfdb8f474b"),
-    "rfft_m_fwd": (87.3e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "fft_host.cuh", "common.cuh"), "4aa889e8daf20ca8"),
-    "fft_n_fwd": (80.4e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "fft_host.cuh", "common.cuh"), "4aa889e8daf20ca8"),
-    "fft_s": (111.4e6, ("kernels_fft_s.cu", "fft.cuh", "fft_ct.cuh", "fft_host.cuh", "common.cuh"), "4aa889e8daf20ca8"),
-    "fft_n_inv": (80.4e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "fft_host.cuh", "common.cuh"), "4aa889e8daf20ca8"),
-    "rfft_m_inv": (90.2e6, ("kernels_fft.cu", "fft.cuh", "fft_ct.cuh", "fft_host.cuh", "common.cuh"), "4aa889e8daf20ca8"),
+    "tv": (499.0e6, ('kernels_tv.cu', 'common.cuh'), "bb1ce373cc693a5a"),
+    "rfft_m_fwd": (87.2e6, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
+    "fft_n_fwd": (80.2e6, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
+    "fft_s": (110.7e6, ('kernels_fft_s.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "eaa6dabc0f38b13d"),
+    "fft_n_inv": (80.4e6, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
+    "rfft_m_inv": (90.4e6, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
 }
+# the tile schedule (n-pass slots, s-pass slots, TV planes) the capture ran
+NCU_SCHEDULE = {"n_pass_slots": 16, "s_pass_slots": 6, "tv_planes": 37}
 
 
-def ncu_traffic(kind):
-    """Recorded DRAM bytes per launch of a loop kernel, or None if its sources changed."""
+def ncu_traffic(kind, schedule=None):
+    """Recorded DRAM bytes per launch of a loop kernel, or None if its sources
+    or the tile schedule differ from the capture's."""
     import hashlib
-    if kind not in NCU_TRAFFIC:
+    if kind not in NCU_TRAFFIC or (schedule is not None and schedule != NCU_SCHEDULE):
         return None
     nbytes, files, digest = NCU_TRAFFIC[kind]
     m = hashlib.sha256()
@@ -228,7 +231,12 @@ def run_ours(args, w, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     stream = torch.cuda.Stream()
     plan = sr3d.Plan(w.dims, w.dec, w.psf(), "f32", stream=stream)
-    plan.autotune()
+    if args.schedule:
+        # a fixed tile schedule instead of the autotuner (whose event timings
+        # mean nothing under a profiler that serialises launches)
+        plan.schedule(*(int(v) for v in args.schedule.split(",")))
+    else:
+        plan.autotune()
     with torch.cuda.stream(stream):
         y = make_inputs(w, plan, torch)
         x = plan.empty_hr()
@@ -288,7 +296,7 @@ def run_ours(args, w, rank, world, local_rank):
     per_launch_s = timed[dom]["ms_per_launch"] / 1e3
     achieved = ALG_BYTES[dom] * w.voxels / per_launch_s / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(dom),
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(dom, plan.schedule()),
                 "alg_bytes_per_launch": ALG_BYTES[dom] * w.voxels,
                 "step_frac": value / world * STEP_BYTES / (peak * 1e9)}
     if rank != 0:
@@ -476,7 +484,8 @@ def run_unet(args, rank, world, local_rank):
     theta = np.load(WEIGHTS) if os.path.exists(WEIGHTS) else W.init_params(3)
     net.set_params(theta)
     g = torch.Generator(device="cuda").manual_seed(5)
-    x = torch.rand((256, 256, 256), device="cuda", generator=g)
+    fshape = tuple(int(v) for v in args.unet_shape.split(","))
+    x = torch.rand(fshape, device="cuda", generator=g)
     x2 = torch.rand((128, 128, 128), device="cuda", generator=g)
     t2 = torch.rand((128, 128, 128), device="cuda", generator=g)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -506,15 +515,16 @@ def run_unet(args, rank, world, local_rank):
         torch.cuda.synchronize()
         trn = ev0.elapsed_time(ev1) / args.steps
         tf = 2 * UNET_MACS * x.numel() / (fwd * 1e-3) / 1e12
-        out[path] = {"forward_256_ms": fwd, "train_step_128_ms": trn, "forward_tflops": tf}
+        out[path] = {"forward_ms": fwd, "train_step_128_ms": trn, "forward_tflops": tf}
     net.set_path("tcgen05")
     if rank == 0:
         d = out["tcgen05"]
         print(json.dumps({
-            "metric": "U-Net forward TFLOP/s at 256³ (BF16 tensor cores)", "value": d["forward_tflops"],
+            "metric": "U-Net forward TFLOP/s (BF16 tensor cores)", "value": d["forward_tflops"],
             "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "warm-start U-Net 16/32/64 channels, forward 256^3, training step 128^3",
+            "config": {"workload": "warm-start U-Net 16/32/64 channels, forward " + "x".join(map(str, fshape[::-1]))
+                       + " (m x n x s), training step 128^3",
                        "flops_per_voxel": 2 * UNET_MACS},
             "roofline": {"bound": "tensor", "achieved": d["forward_tflops"], "peak": bf16, "unit": "TFLOP/s",
                          "frac": d["forward_tflops"] / bf16 if bf16 else None},
@@ -636,6 +646,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--schedule", default="",
+                    help="headline: fixed tile schedule n_slots,s_slots,tv_planes instead of the autotuner")
+    ap.add_argument("--unet-shape", default="256,256,256",
+                    help="--workload unet: forward volume s,n,m (a smaller case for profiling)")
     ap.add_argument("--workload", choices=["headline", "batch", "warmstart", "regularisers", "comparator", "unet"],
                     default="headline")
     args = ap.parse_args()
