@@ -47,26 +47,27 @@ ALG_BYTES = {"tv": 32, "rfft_m_fwd": 8, "fft_n_fwd": 8, "fft_s": 16, "fft_n_inv"
 STEP_BYTES = 80
 # DRAM bytes per launch (dram__bytes_read + dram__bytes_write) of each loop
 # kernel from one ncu capture of this workload (profiles/admm_tv_256_kernels_ncu.md),
-# valid while the kernel's sources hash to the recorded value
+# with the kernel's entry of the tile schedule in that capture; valid while the
+# plan runs that entry and the kernel's sources hash to the recorded value
 NCU_TRAFFIC = {
-    "tv": (499.0e6, ('kernels_tv.cu', 'common.cuh'), "bb1ce373cc693a5a"),
-    "rfft_m_fwd": (87.2e6, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
-    "fft_n_fwd": (80.2e6, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
-    "fft_s": (110.7e6, ('kernels_fft_s.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "eaa6dabc0f38b13d"),
-    "fft_n_inv": (80.4e6, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
-    "rfft_m_inv": (90.4e6, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
+    "tv": (499.0e6, {"tv_planes": 37}, ('kernels_tv.cu', 'common.cuh'), "bb1ce373cc693a5a"),
+    "rfft_m_fwd": (87.2e6, {"m_fwd_lines": 32}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
+    "fft_n_fwd": (80.2e6, {"n_pass_slots": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
+    "fft_s": (110.7e6, {"s_pass_slots": 6}, ('kernels_fft_s.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "eaa6dabc0f38b13d"),
+    "fft_n_inv": (80.4e6, {"n_pass_slots": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
+    "rfft_m_inv": (90.4e6, {"m_inv_lines": 32}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
 }
-# the tile schedule (n-pass slots, s-pass slots, TV planes) the capture ran
-NCU_SCHEDULE = {"n_pass_slots": 16, "s_pass_slots": 6, "tv_planes": 37}
 
 
 def ncu_traffic(kind, schedule=None):
     """Recorded DRAM bytes per launch of a loop kernel, or None if its sources
     or the tile schedule differ from the capture's."""
     import hashlib
-    if kind not in NCU_TRAFFIC or (schedule is not None and schedule != NCU_SCHEDULE):
+    if kind not in NCU_TRAFFIC:
         return None
-    nbytes, files, digest = NCU_TRAFFIC[kind]
+    nbytes, sched, files, digest = NCU_TRAFFIC[kind]
+    if schedule is not None and any(schedule.get(k) != v for k, v in sched.items()):
+        return None
     m = hashlib.sha256()
     for f in files:
         with open(os.path.join(ROOT, "paper_2010_15491_gb300", "csrc", f), "rb") as fh:
@@ -647,7 +648,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--schedule", default="",
-                    help="headline: fixed tile schedule n_slots,s_slots,tv_planes instead of the autotuner")
+                    help="headline: fixed tile schedule n_slots,s_slots,tv_planes[,m_fwd_lines,m_inv_lines] "
+                         "instead of the autotuner")
     ap.add_argument("--unet-shape", default="256,256,256",
                     help="--workload unet: forward volume s,n,m (a smaller case for profiling)")
     ap.add_argument("--workload", choices=["headline", "batch", "warmstart", "regularisers", "comparator", "unet"],

@@ -180,13 +180,14 @@ int sr3d_autotune(sr3d_plan_t plan, int reps);
  * choice), and a way to set it.  Entries: [0] = m-slots per CTA of the n
  * pass, [1] = m-slots per CTA of the s pass (a multiple of d_r), [2] = s
  * planes each CTA of the TV kernel marches over (the last CTA along s takes
- * the remainder).  set (may be NULL) gives new values, entries <= 0 keeping
- * the current one; results do not depend on the schedule (it only splits the
- * same work differently).  sched (may be NULL) receives the schedule in
- * force.  Errors: INVALID_ARG (a width the pass's kernel or the plan's
- * solve-order buffers cannot take, or fewer than 4 TV planes; nothing is
- * changed), CUDA. */
-int sr3d_schedule(sr3d_plan_t plan, const int set[3], int sched[3]);
+ * the remainder), [3] and [4] = lines per CTA of the forward and inverse m
+ * passes (whole warps, at most the default of 256 threads).  set (may be
+ * NULL) gives new values, entries <= 0 keeping the current one; results do
+ * not depend on the schedule (it only splits the same work differently).
+ * sched (may be NULL) receives the schedule in force.  Errors: INVALID_ARG
+ * (a value the pass's kernel or the plan's solve-order buffers cannot take,
+ * or fewer than 4 TV planes; nothing is changed), CUDA. */
+int sr3d_schedule(sr3d_plan_t plan, const int set[5], int sched[5]);
 
 /* Per-kernel accounting.  Kernel kinds: SR3D_K_TV (fused u/d/Theta step),
  * SR3D_K_RFFT_FWD / SR3D_K_RFFT_INV (real FFT along m), SR3D_K_FFTN_FWD /

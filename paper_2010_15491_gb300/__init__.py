@@ -239,15 +239,17 @@ class Plan:
         """Times candidate tile schedules and keeps the fastest (cached per geometry)."""
         _check(load().sr3d_autotune(self._h, int(reps)))
 
-    def schedule(self, n_pass_slots: int = 0, s_pass_slots: int = 0, tv_planes: int = 0) -> dict:
+    def schedule(self, n_pass_slots: int = 0, s_pass_slots: int = 0, tv_planes: int = 0, m_fwd_lines: int = 0,
+                 m_inv_lines: int = 0) -> dict:
         """The tile schedule the plan launches (sr3d_schedule); positive
         arguments first set the n-pass and s-pass tile widths (m-slots per
-        CTA) and the TV kernel's s planes per CTA."""
-        v = (ctypes.c_int * 3)()
-        req = (int(n_pass_slots), int(s_pass_slots), int(tv_planes))
-        setv = (ctypes.c_int * 3)(*req) if any(r > 0 for r in req) else None
+        CTA), the TV kernel's s planes per CTA and the m passes' lines per CTA."""
+        v = (ctypes.c_int * 5)()
+        req = (int(n_pass_slots), int(s_pass_slots), int(tv_planes), int(m_fwd_lines), int(m_inv_lines))
+        setv = (ctypes.c_int * 5)(*req) if any(r > 0 for r in req) else None
         _check(load().sr3d_schedule(self._h, setv, v))
-        return {"n_pass_slots": v[0], "s_pass_slots": v[1], "tv_planes": v[2]}
+        return {"n_pass_slots": v[0], "s_pass_slots": v[1], "tv_planes": v[2], "m_fwd_lines": v[3],
+                "m_inv_lines": v[4]}
 
     def profile(self, on: bool = True):
         """Resets the per-kernel accounting; with on=True also times every launch."""

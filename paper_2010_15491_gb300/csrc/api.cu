@@ -16,6 +16,7 @@
 #include <initializer_list>
 #include <vector>
 
+#include "fft_host.cuh"
 #include "internal.h"
 #include "sr3d.h"
 
@@ -652,7 +653,7 @@ static bool tw_s_valid(const Plan& p, const Geometry& g, size_t csz, int tw) {
   return solve_lam_elems(gc) <= p.lam_solve_cap && solve_yhat_elems(gc) <= p.yhat_solve_cap;
 }
 
-int sr3d_schedule(sr3d_plan_t plan, const int set[3], int sched[3]) {
+int sr3d_schedule(sr3d_plan_t plan, const int set[5], int sched[5]) {
   if (!plan) return fail(SR3D_ERR_INVALID_ARG, "NULL plan");
   Plan& p = plan->p;
   Geometry& g = p.hr;
@@ -664,13 +665,23 @@ int sr3d_schedule(sr3d_plan_t plan, const int set[3], int sched[3]) {
       return fail(SR3D_ERR_INVALID_ARG, "s-pass tile width %d does not fit this volume", set[1]);
     // at least 4 planes per CTA: the per-CTA partial sums are sized for that
     if (set[2] > 0 && set[2] < 4) return fail(SR3D_ERR_INVALID_ARG, "TV planes per CTA must be >= 4");
-    const int tn = set[0] > 0 ? set[0] : g.tw_n, tws = set[1] > 0 ? set[1] : g.tw_s;
-    const int tv = set[2] > 0 ? set[2] : g.ts_tv;
-    if (tn != g.tw_n || tws != g.tw_s || tv != g.ts_tv) {
+    for (int k = 3; k < 5; ++k)
+      if (set[k] > 0 && !m_lines_valid(g, set[k]))
+        return fail(SR3D_ERR_INVALID_ARG, "m-pass lines per CTA %d: need whole warps within 256 threads", set[k]);
+    const int v[5] = {g.tw_n, g.tw_s, g.ts_tv, g.lm_f, g.lm_i};
+    int w[5];
+    bool change = false;
+    for (int k = 0; k < 5; ++k) {
+      w[k] = set[k] > 0 ? set[k] : v[k];
+      change |= w[k] != v[k];
+    }
+    if (change) {
       TRY(sync_plan(p));
-      g.tw_n = tn;
-      g.tw_s = tws;
-      g.ts_tv = tv;
+      g.tw_n = w[0];
+      g.tw_s = w[1];
+      g.ts_tv = w[2];
+      g.lm_f = w[3];
+      g.lm_i = w[4];
       TRY(realloc_partials(p));
       CK(launch_perm_lam(p, p.lam, p.lam_solve));  // Lambda in the new solve order
       if (p.iter_graph) {  // captured launches hold the old grids
@@ -683,9 +694,15 @@ int sr3d_schedule(sr3d_plan_t plan, const int set[3], int sched[3]) {
     }
   }
   if (sched) {
+    int L, Hp, threads;
+    size_t smem;
     sched[0] = g.tw_n;
     sched[1] = g.tw_s;
     sched[2] = g.ts_tv > 0 ? g.ts_tv : tv_default_ts(g);
+    m_launch_shape(g, csz, g.lm_f, L, Hp, threads, smem);
+    sched[3] = L;
+    m_launch_shape(g, csz, g.lm_i, L, Hp, threads, smem);
+    sched[4] = L;
   }
   return SR3D_OK;
 }
@@ -1066,7 +1083,7 @@ int sr3d_admm_tv_host(sr3d_plan_t plan, const void* y_host, void* x_host, double
 // fastest and caches the choice per geometry for the process.
 // ---------------------------------------------------------------------------
 using TuneKey = std::tuple<int, int, int, int, int, int, int>;
-struct TuneVal { int tw_n, tw_s, ts_tv; };
+struct TuneVal { int tw_n, tw_s, ts_tv, lm_f, lm_i; };
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune;
 
@@ -1116,7 +1133,7 @@ extern "C" int sr3d_autotune(sr3d_plan_t plan, int reps) {
   Geometry& g = p.hr;
   const size_t csz = 2 * p.esz;
   const TuneKey key{g.M, g.N, g.S, g.dr, g.dc, g.ds, p.dtype};
-  TuneVal best{g.tw_n, g.tw_s, g.ts_tv};
+  TuneVal best{g.tw_n, g.tw_s, g.ts_tv, g.lm_f, g.lm_i};
   bool cached = false;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -1151,6 +1168,32 @@ extern "C" int sr3d_autotune(sr3d_plan_t plan, int reps) {
         if (ms < bt) { bt = ms; best.tw_n = tw; }
       }
       g.tw_n = best.tw_n;
+    }
+    // m passes: lines per CTA (whole warps), forward and inverse apart; at
+    // most eight values spread down from the default
+    {
+      std::vector<int> cand;
+      for (int L = 256; L >= 1; --L)
+        if (m_lines_valid(g, L)) cand.push_back(L);
+      const size_t stride = (cand.size() + 7) / 8;
+      float bf = 1e30f, bi = 1e30f;
+      for (size_t ci = 0; ci < cand.size(); ci += stride) {
+        const int L = cand[ci];
+        g.lm_f = g.lm_i = L;
+        float ms = 0;
+        TRY(time_ms(p, reps, &ms, [&]() -> int {
+          CK(launch_rfft_m_fwd(p, g, p.theta, p.spec, p.twM));
+          return SR3D_OK;
+        }));
+        if (ms < bf) { bf = ms; best.lm_f = L; }
+        TRY(time_ms(p, reps, &ms, [&]() -> int {
+          CK(launch_rfft_m_inv(p, g, p.spec, p.theta, p.twM, 1.0));
+          return SR3D_OK;
+        }));
+        if (ms < bi) { bi = ms; best.lm_i = L; }
+      }
+      g.lm_f = best.lm_f;
+      g.lm_i = best.lm_i;
     }
     // s pass (ADMM class solve) tile width; Lambda is re-permuted per candidate
     {
@@ -1195,6 +1238,8 @@ extern "C" int sr3d_autotune(sr3d_plan_t plan, int reps) {
   g.tw_n = best.tw_n;
   g.tw_s = best.tw_s;
   g.ts_tv = best.ts_tv;
+  g.lm_f = best.lm_f;
+  g.lm_i = best.lm_i;
   {
     Geometry gc = g;
     if (solve_lam_elems(gc) > p.lam_solve_cap || solve_yhat_elems(gc) > p.yhat_solve_cap)

@@ -29,13 +29,25 @@ static inline LAxis laxis(int n, int nl, int dc, const FftAxis& f) {
 
 static inline bool fam3(const FftAxis& f) { return f.n % 3 == 0; }
 
-static inline void m_launch_shape(const Geometry& g, size_t csz, int& L, int& Hp, int& threads, size_t& smem) {
+// Lines per CTA of the m passes: at most 256 threads (tpl per line); L_req > 0
+// (a schedule choice, checked by m_lines_valid) takes fewer lines.
+static inline void m_launch_shape(const Geometry& g, size_t csz, int L_req, int& L, int& Hp, int& threads,
+                                  size_t& smem) {
   const int H = g.M / 2;
   const int tpl = H / g.fm.e;
   L = tpl >= 256 ? 1 : 256 / tpl;
+  if (L_req > 0 && L_req < L) L = L_req;
   Hp = H + (H >= 32 ? (int)(64 / csz) : 0);
   threads = L * tpl;
   smem = (size_t)L * Hp * csz;
+}
+
+// A lines-per-CTA value the m-pass kernels take: at most the default, and
+// whole warps (the forward pass strides its stores over the CTA's warps).
+static inline bool m_lines_valid(const Geometry& g, int L) {
+  const int tpl = (g.M / 2) / g.fm.e;
+  const int lmax = tpl >= 256 ? 1 : 256 / tpl;
+  return L >= 1 && L <= lmax && (L * tpl) % 32 == 0;
 }
 
 // lengths with a compile-time plan (FP32 only; the s pass takes 256)

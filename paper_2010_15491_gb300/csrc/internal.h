@@ -58,6 +58,7 @@ struct Geometry {
   int g_s;            // s-pass tile height in n slots (multiple of dc)
   int tw_n;           // n-pass tile width
   int ts_tv;          // TV kernel: s planes per CTA (0 = default rule)
+  int lm_f, lm_i;     // m passes (forward, inverse): lines per CTA (0 = default rule)
   long long V() const { return (long long)M * N * S; }
   long long spec_elems() const { return (long long)S * N * Mp; }
 };

@@ -202,7 +202,7 @@ template <typename T, int EMAX, int NC>
 static cudaError_t rfft_fwd_k(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw) {
   int L, Hp, threads;
   size_t smem;
-  m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
+  m_launch_shape(g, sizeof(cplx<T>), g.lm_f, L, Hp, threads, smem);
   if (NC > 0) {
     Hp = ct_line_pitch<true>(NC);
     smem = (size_t)(L * Hp + 2 * NC) * sizeof(cplx<T>) + (size_t)g.Ms * sizeof(short2);  // + slot table
@@ -222,7 +222,7 @@ static cudaError_t rfft_inv_k(const Plan& p, const Geometry& g, const void* in, 
                               double scale) {
   int L, Hp, threads;
   size_t smem;
-  m_launch_shape(g, sizeof(cplx<T>), L, Hp, threads, smem);
+  m_launch_shape(g, sizeof(cplx<T>), g.lm_i, L, Hp, threads, smem);
   if (NC > 0) {
     Hp = ct_line_pitch<true>(NC);
     smem = (size_t)(L * Hp + 2 * NC + L * g.Mp) * sizeof(cplx<T>) + (size_t)(NC + 1) * sizeof(short2);

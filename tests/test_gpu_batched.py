@@ -72,9 +72,10 @@ def test_autotuned_plans_keep_parity(lib):
 @pytest.mark.parametrize("dtype", ["f32", "f64"])
 @pytest.mark.parametrize("dims", [(128, 64, 48), (256, 32, 64)])
 def test_schedules_leave_results_unchanged(lib, dtype, dims):
-    """Every tile width of the n and s passes and every TV plane count the
-    plan accepts (sr3d_schedule), including widths that do not divide the
-    m-slot count and plane counts that do not divide S, splits the same
+    """Every tile width of the n and s passes, every TV plane count and every
+    m-pass lines-per-CTA count the plan accepts (sr3d_schedule), including
+    widths that do not divide the m-slot count, plane counts that do not
+    divide S and line counts that do not divide N x S, splits the same
     per-element work differently: the iterate is bit-identical and the
     statistics agree to reduction order.  (256, 32, 64) has the 130 m-slots
     of a 256-long m axis at d_r = 2 and a compile-time s pass.  After a
@@ -110,21 +111,28 @@ def test_schedules_leave_results_unchanged(lib, dtype, dims):
         for k in ("objective", "data_term", "tv_term", "primal", "dual"):
             assert abs(st[k] - st0[k]) <= rtol * abs(st0[k]) + 1e-300, (tag, k)
 
-    accepted = {"n": [], "s": [], "tv": []}
-    for key, arg, widths in (("n", "n_pass_slots", (2, 6, 10, 12, 16, 22, 32, 34)),
-                             ("s", "s_pass_slots", (2, 4, 6, 8, 10, 12, 22)),
-                             ("tv", "tv_planes", (4, 5, 7, 37, 64))):
+    accepted = {}
+    for arg, widths in (("n_pass_slots", (2, 6, 10, 12, 16, 22, 32, 34)),
+                        ("s_pass_slots", (2, 4, 6, 8, 10, 12, 22)),
+                        ("tv_planes", (4, 5, 7, 37, 64)),
+                        ("m_fwd_lines", (3, 4, 8, 12, 16, 24, 40, 64)),
+                        ("m_inv_lines", (3, 4, 8, 12, 16, 24, 40, 64))):
+        accepted[arg] = []
         for w in widths:
+            prev = p.schedule()
             try:
                 sch = p.schedule(**{arg: w})
             except lib.Sr3dError:
+                assert p.schedule() == prev  # a rejected value changes nothing
                 continue
-            assert sch[{"n": "n_pass_slots", "s": "s_pass_slots", "tv": "tv_planes"}[key]] == w
-            accepted[key].append(w)
-            same((key, w))
-        p.schedule(n_pass_slots=base["n_pass_slots"], s_pass_slots=base["s_pass_slots"],
-                   tv_planes=base["tv_planes"])
-    assert len(accepted["n"]) >= 4 and len(accepted["s"]) >= 3 and len(accepted["tv"]) == 5, accepted
+            assert sch[arg] == w
+            accepted[arg].append(w)
+            same((arg, w))
+        p.schedule(**base)
+    assert p.schedule() == base
+    assert len(accepted["n_pass_slots"]) >= 4 and len(accepted["s_pass_slots"]) >= 3, accepted
+    assert len(accepted["tv_planes"]) == 5 and len(accepted["m_fwd_lines"]) >= 3, accepted
+    assert accepted["m_inv_lines"] == accepted["m_fwd_lines"], accepted
     same("restored")
     # the autotuner may change every schedule; statistics still match a fresh plan
     p.autotune(2)
@@ -134,7 +142,8 @@ def test_schedules_leave_results_unchanged(lib, dtype, dims):
     for k in ("objective", "data_term", "tv_term", "primal", "dual"):
         assert abs(st[k] - st0[k]) <= rtol * abs(st0[k]) + 1e-300, k
     before = p.schedule()
-    for bad in ({"tv_planes": 3}, {"s_pass_slots": 3}, {"n_pass_slots": 3}, {"n_pass_slots": 1000}):
+    for bad in ({"tv_planes": 3}, {"s_pass_slots": 3}, {"n_pass_slots": 3}, {"n_pass_slots": 1000},
+                {"m_fwd_lines": 3}, {"m_inv_lines": 1000}):
         with pytest.raises(lib.Sr3dError):
             p.schedule(**bad)
         assert p.schedule() == before
