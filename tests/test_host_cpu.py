@@ -61,3 +61,21 @@ def test_bench_unet_cost_counts_every_layer():
     density = [1, 1, 1 / 8, 1 / 8, 1 / 64, 1 / 64, 1 / 8, 1 / 8, 1, 1]
     macs = sum(27 * co * ci * f for (co, ci), f in zip(U.layer_shapes((c1, c2, c3)), density)) + c1
     assert bench.UNET_MACS == macs
+
+
+def test_bench_recorded_traffic_follows_sources_and_schedule():
+    """bench.py reports a kernel's recorded DRAM traffic only while the plan
+    runs the kernel's schedule entry of the capture and the kernel's sources
+    hash to the recorded value."""
+    import bench
+    for kind, (nbytes, sched, files, digest) in bench.NCU_TRAFFIC.items():
+        full = {"n_pass_slots": 0, "s_pass_slots": 0, "tv_planes": 0, "m_fwd_lines": 0, "m_inv_lines": 0}
+        full.update(sched)
+        other = dict(full)
+        key = next(iter(sched))
+        other[key] = sched[key] + 1
+        got = bench.ncu_traffic(kind, full)
+        assert got in (nbytes, None)  # None once the sources changed
+        assert bench.ncu_traffic(kind, other) is None
+    assert bench.ncu_traffic("tv", None) == bench.ncu_traffic("tv", {"tv_planes": 37})
+    assert bench.ncu_traffic("no_such_kernel") is None
