@@ -224,10 +224,12 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
 
 // ---------------------------------------------------------------------------
 // Vectorised variant for FP32 volumes with m_h a multiple of 128: a CTA of
-// 32 x 8 threads covers m in [m0, m0+128) x n in [n0, n0+8), each thread four
-// consecutive m voxels (float4 loads and stores).  Warp 0 also evaluates the
-// -n halo row of the rho region, warp 1 the -m halo column; x halo rows come
-// through warps 0 and 7, halo columns through warp 1.  Same algebra, modes
+// 32 x 9 threads covers m in [m0, m0+128) x n in [n0, n0+8); warps 0-7 own
+// the tile rows, each thread four consecutive m voxels (float4 loads and
+// stores).  Warp 8, the halo warp, copies the x and d halo rows and columns
+// and evaluates the -n halo row and the -m halo column of the rho region, so
+// that every warp evaluates about one row per plane (a tile warp that also
+// took the halo row held the others at the plane's barrier).  Same algebra, modes
 // and statistics as k_tv; the statistics of a thread's four voxels are summed
 // in FP32 (sqrtf for ||g||) and accumulated over its planes in compensated
 // FP32 (Kahan), then reduced across the CTA in FP64 (FP64 arithmetic is slow
@@ -255,7 +257,7 @@ __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_grou
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 template <int MODE, bool STATS>
-__global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const float* __restrict__ din,
+__global__ void __launch_bounds__(32 * (TN + 1), STATS ? 2 : 3) k_tv4(const float* __restrict__ x, const float* __restrict__ din,
                                              float* __restrict__ dout, float* __restrict__ theta,
                                              float* __restrict__ psi, int M, int N, int S, int TS, float thr,
                                              double* __restrict__ partial) {
@@ -267,38 +269,45 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
   float* rs = ds + 2 * 3 * RR * V4W;     // [NC][RR][V4W]
   constexpr int XP = XR * V4W, DP = 3 * RR * V4W, RP = RR * V4W;
   const int lm = threadIdx.x, ln = threadIdx.y, tid = ln * 32 + lm;
+  const bool halo_warp = ln == TN;
   const int m0 = blockIdx.x * V4M, n0 = blockIdx.y * TN, s0 = blockIdx.z * TS;
   const long long V = (long long)M * N * S;
   const long long P = (long long)M * N;
   const int s_end = min(S, s0 + TS);
   const int mc = 4 + 4 * lm;  // shared column of the thread's first voxel
-  const long long o_in = (long long)(n0 + ln) * M + m0 + 4 * lm;            // interior
-  const long long o_hr = (long long)((n0 - 1 + N) % N) * M + m0 + 4 * lm;  // row n0-1 (warp 0)
-  const long long o_xr = (long long)((n0 + TN) % N) * M + m0 + 4 * lm;     // row n0+8 (warp 7, x only)
-  // warp 1: lane < 10 -> x column m0-1 of row n0-1+lane; 10 <= lane < 20 -> column m0+128
-  const bool xcol = ln == 1 && lm < 20;
+  const long long o_in = (long long)(n0 + ln) * M + m0 + 4 * lm;            // interior (warps 0-7)
+  const long long o_hr = (long long)((n0 - 1 + N) % N) * M + m0 + 4 * lm;  // row n0-1 (halo warp)
+  const long long o_xr = (long long)((n0 + TN) % N) * M + m0 + 4 * lm;     // row n0+8 (halo warp, x only)
+  // halo warp: lane < 10 -> x column m0-1 of row n0-1+lane; 10 <= lane < 20 -> column m0+128
+  const bool xcol = halo_warp && lm < 20;
   const int xc_row = lm < 10 ? lm : lm - 10;
   const int xc_col = lm < 10 ? 3 : 4 + V4M;
   const long long o_xc = (long long)((n0 - 1 + xc_row + N) % N) * M + (lm < 10 ? (m0 - 1 + M) % M : (m0 + V4M) % M);
-  // warp 1: lane < RR -> d (and rho) column m0-1 of row n0-1+lane
-  const bool rcol = ln == 1 && lm < RR;
+  // halo warp: lane < RR -> d (and rho) column m0-1 of row n0-1+lane
+  const bool rcol = halo_warp && lm < RR;
   const long long o_rc = (long long)((n0 - 1 + lm + N) % N) * M + (m0 - 1 + M) % M;
   auto plane_of = [&](int s) -> long long { return (long long)((s + S) % S) * P; };
 
   auto fetch_x = [&](int s, float* buf) {
     const long long pl = plane_of(s);
-    cp16(buf + (ln + 1) * V4W + mc, x + pl + o_in);
-    if (ln == 0) cp16(buf + mc, x + pl + o_hr);
-    else if (ln == TN - 1) cp16(buf + (XR - 1) * V4W + mc, x + pl + o_xr);
-    if (xcol) cp4(buf + xc_row * V4W + xc_col, x + pl + o_xc);
+    if (!halo_warp) {
+      cp16(buf + (ln + 1) * V4W + mc, x + pl + o_in);
+    } else {
+      cp16(buf + mc, x + pl + o_hr);
+      cp16(buf + (XR - 1) * V4W + mc, x + pl + o_xr);
+      if (xcol) cp4(buf + xc_row * V4W + xc_col, x + pl + o_xc);
+    }
   };
   auto fetch_d = [&](int s, float* buf) {
     const long long pl = plane_of(s);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      cp16(buf + k * RP + (ln + 1) * V4W + mc, din + k * V + pl + o_in);
-      if (ln == 0) cp16(buf + k * RP + mc, din + k * V + pl + o_hr);
-      if (rcol) cp4(buf + k * RP + lm * V4W + 3, din + k * V + pl + o_rc);
+      if (!halo_warp) {
+        cp16(buf + k * RP + (ln + 1) * V4W + mc, din + k * V + pl + o_in);
+      } else {
+        cp16(buf + k * RP + mc, din + k * V + pl + o_hr);
+        if (rcol) cp4(buf + k * RP + lm * V4W + 3, din + k * V + pl + o_rc);
+      }
     }
   };
 
@@ -397,8 +406,11 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
         st4(dout + 2 * V + gi, make_float4(e2v[0], e2v[1], e2v[2], e2v[3]));
       }
     };
-    quad(ln + 1, true);
-    if (ln == 0) quad(0, false);
+    if (!halo_warp) {
+      quad(ln + 1, true);
+    } else {
+      quad(0, false);
+    }
     if (rcol) {
       // halo column m0-1 (shared column 3), row lm
       const int xr = lm;
@@ -409,8 +421,8 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
             e2);
     }
     __syncthreads();
-    // phase 2: Theta = L^T rho for the four interior voxels
-    {
+    // phase 2: Theta = L^T rho for the four interior voxels (tile warps)
+    if (!halo_warp) {
       const int row = (ln + 1) * V4W + mc;
       const int up = ln * V4W + mc;
       float4 own0, own1, own2, up1;
@@ -477,17 +489,17 @@ __global__ void __launch_bounds__(256) k_tv4(const float* __restrict__ x, const 
     cur = (cur + 1) % 3;
   }
   if (STATS) {
-    __shared__ double red[NQ][8];
+    __shared__ double red[NQ][TN];  // the tile warps' sums (the halo warp adds none)
     const int lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
       const double v = warp_sum_d((double)qs[k] - (double)qc[k]);
-      if (lane == 0) red[k][warp] = v;
+      if (lane == 0 && warp < TN) red[k][warp] = v;
     }
     __syncthreads();
     if (tid < NQ) {
       double v = 0;
-      for (int w = 0; w < 8; ++w) v += red[tid][w];
+      for (int w = 0; w < TN; ++w) v += red[tid][w];
       const long long b = ((long long)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
       partial[b * NQ + tid] = v;
     }
@@ -518,7 +530,7 @@ static cudaError_t tv_per_sm(const Plan& p, int* per_sm) {
     const size_t smem = tv4_smem(false);
     cudaError_t e = cudaFuncSetAttribute(k_tv4<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tv4<0, false>, 32 * TN, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tv4<0, false>, 32 * (TN + 1), smem);
   }
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tv<T, 0, false>, TM * TN, 0);
 }
@@ -579,7 +591,7 @@ static cudaError_t tv4_k(const Plan& p, const void* x, const void* din, void* do
   const Geometry& g = p.hr;
   const int ts = tv_ts(g);
   dim3 grid(g.M / V4M, g.N / TN, (g.S + ts - 1) / ts);
-  dim3 block(32, TN);
+  dim3 block(32, TN + 1);  // eight tile warps and the halo warp
   const size_t smem = tv4_smem(STATS);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_tv4<MODE, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
