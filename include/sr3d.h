@@ -93,7 +93,8 @@ int sr3d_plan(sr3d_plan_t* out, const sr3d_desc* desc);
 int sr3d_destroy(sr3d_plan_t plan);
 
 /* Degradation operator of eq. (1) without noise: y_dev = D H x_dev
- * (HR x in, LR y out).  Used to synthesise observations. */
+ * (HR x in, LR y out).  Used to synthesise observations.  Errors:
+ * INVALID_ARG (NULL arrays), CUDA. */
 int sr3d_forward(sr3d_plan_t plan, const void* x_dev, void* y_dev);
 
 /* Sentinel for xbar_dev: the prior xbar is the nearest-neighbour replication
@@ -168,12 +169,16 @@ int sr3d_xstep(sr3d_plan_t plan, const void* y_dev, const void* theta_dev, doubl
 int sr3d_tv_step(sr3d_plan_t plan, const void* x_dev, const void* d_in_dev, void* d_out_dev,
                  double lambda, double rho, void* theta_out_dev);
 
-/* Autotuner: times candidate tile schedules of the n pass, of the s pass with
- * its class solve, and of the TV kernel (reps launches each) on the plan's
- * own buffers, keeps the fastest and caches the choice per geometry (sizes,
- * decimation, dtype) for the process; a later plan of the same geometry only
- * applies the cached choice.  Results are unchanged (the schedules only
- * split the same work differently).  Errors: INVALID_ARG, CUDA, OOM. */
+/* Autotuner (not in the paper): times candidate tile schedules (reps launches
+ * each) on the plan's own buffers -- the n pass's and the s pass's tile
+ * widths (including widths that cover the m-slots with at most one step of
+ * padding), the m passes' lines per CTA, and the TV kernel's planes per CTA
+ * (including the counts whose grid fills whole waves of resident CTAs) --
+ * keeps the fastest and caches the choice per geometry (sizes, decimation,
+ * dtype) for the process; a later plan of the same geometry only applies the
+ * cached choice.  Results are unchanged (the schedules only split the same
+ * work differently); the work spectrum, Theta and dual buffers are
+ * overwritten.  Errors: INVALID_ARG, CUDA, OOM. */
 int sr3d_autotune(sr3d_plan_t plan, int reps);
 
 /* The tile schedule the plan launches (the defaults, or the autotuner's
@@ -263,8 +268,12 @@ long long sr3d_unet_param_count(void);
 /* Creates a network with all parameters zero (the identity map: out = x) on
  * `stream` (NULL = legacy default stream).  Activation buffers are
  * allocated on first use of a size and kept until the size changes.  The
- * handle is freed by sr3d_unet_destroy; a network is used by one host thread
- * at a time. */
+ * handle is freed by sr3d_unet_destroy (safe with NULL); a network is used by
+ * one host thread at a time.  Errors of every sr3d_unet_* call: INVALID_ARG
+ * (NULL arguments, a parameter or byte count that does not match, an unknown
+ * path or activation index, sr3d_unet_read before any forward pass),
+ * UNSUPPORTED_SIZE (m, n, s not positive multiples of 4), OOM, TIMEOUT (a
+ * bounded tcgen05 wait ran out), CUDA. */
 int sr3d_unet_create(sr3d_unet_t* out, void* stream);
 int sr3d_unet_destroy(sr3d_unet_t net);
 
@@ -312,10 +321,11 @@ int sr3d_unet_read(sr3d_unet_t net, int which, void* host, long long bytes);
 
 /* KKT-consistent initial dual for sr3d_admm_tv started at x (no counterpart in
  * the paper, which starts from d = 0): with g = Lx (periodic forward
- * differences, Section 3.2) and t = lambda / rho,
+ * differences, Sec. III-B) and t = lambda / rho,
  *   d_j = t g_j / max(||g_j||, t)   (j = voxel, ||.|| over the 3 directions),
  * written as d_dev[3][V] in the plan's dtype; x_dev is an HR volume of the
- * plan.  Pass d_dev to sr3d_admm_tv together with x_dev as x0. */
+ * plan.  Pass d_dev to sr3d_admm_tv together with x_dev as x0.  Errors:
+ * INVALID_ARG (NULL arrays, lambda or rho not positive), CUDA. */
 int sr3d_dual_init(sr3d_plan_t plan, const void* x_dev, double lambda, double rho, void* d_dev);
 
 /* Replaces the plan's PSF (host taps psf[p_s][p_n][p_m], each size at most the
@@ -371,12 +381,14 @@ int sr3d_tikhonov_cg(sr3d_plan_t plan, const void* y_dev, const void* xbar_dev, 
  * class solve of eq. 12 then forms Lambda from them instead of reading the
  * stored 3-D Lambda (4 bytes less HBM traffic per voxel in FP32).  use = 1
  * enables the path (the default), 0 disables it, -1 only queries; *active (if
- * not NULL) receives 1 when the path is in use.  Results agree with the stored
- * Lambda to rounding. */
+ * not NULL) receives 1 when the path is in use (enabled and the PSF
+ * separable).  Results agree with the stored Lambda to rounding.  Errors:
+ * INVALID_ARG (NULL plan), CUDA. */
 int sr3d_separable(sr3d_plan_t plan, int use, int* active);
 
 /* Plan facts for callers and tests: sizes[0..8] = m_h, n_h, s_h, m_l, n_l,
- * s_l, m-slots, m-pitch, dtype; bytes = device memory the plan holds. */
+ * s_l, m-slots, m-pitch, dtype; bytes (if not NULL) = device memory the plan
+ * holds.  Errors: INVALID_ARG (NULL plan or sizes). */
 int sr3d_plan_info(sr3d_plan_t plan, int sizes[9], long long* bytes);
 
 #ifdef __cplusplus
