@@ -170,7 +170,7 @@ int sr3d_tv_step(sr3d_plan_t plan, const void* x_dev, const void* d_in_dev, void
                  double lambda, double rho, void* theta_out_dev);
 
 /* Autotuner (not in the paper): times candidate tile schedules (reps launches
- * each) on the plan's own buffers -- the n pass's and the s pass's tile
+ * each after one warm-up launch; reps < 1 takes 10) on the plan's own buffers -- the n pass's and the s pass's tile
  * widths (including widths that cover the m-slots with at most one step of
  * padding), the m passes' lines per CTA, and the TV kernel's planes per CTA
  * (including the counts whose grid fills whole waves of resident CTAs) --

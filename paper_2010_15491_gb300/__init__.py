@@ -235,8 +235,9 @@ class Plan:
         _check(load().sr3d_separable(self._h, -1 if use is None else int(bool(use)), ctypes.byref(act)))
         return bool(act.value)
 
-    def autotune(self, reps: int = 3):
-        """Times candidate tile schedules and keeps the fastest (cached per geometry)."""
+    def autotune(self, reps: int = 10):
+        """Times candidate tile schedules (reps launches each) and keeps the
+        fastest (cached per geometry)."""
         _check(load().sr3d_autotune(self._h, int(reps)))
 
     def schedule(self, n_pass_slots: int = 0, s_pass_slots: int = 0, tv_planes: int = 0, m_fwd_lines: int = 0,

@@ -1143,7 +1143,7 @@ extern "C" int sr3d_autotune(sr3d_plan_t plan, int reps) {
       cached = true;
     }
   }
-  if (reps < 1) reps = 3;
+  if (reps < 1) reps = 10;  // a window of a few hundred microseconds per candidate
   const bool prof = p.prof_on;
   p.prof_on = false;
   struct Restore { Plan& p; bool on; ~Restore() { p.prof_on = on; } } restore{p, prof};
