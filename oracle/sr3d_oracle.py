@@ -6,17 +6,17 @@ TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
 baseline leg of bench.py may import this module.  The CUDA library never
 imports, links or calls it, and this module shares no code with it.
 
-It is deliberately plain: numpy arrays in float64 / complex128, numpy's FFT as
-a library primitive (pinned against an explicit DFT in the tests), and the
-paper's formulas written out in the paper's order.  Nothing is fused, tiled or
-reordered.
+It is deliberately plain: numpy arrays in float64 / complex128, scipy's FFT
+(pocketfft, threaded over the host's cores) as a library primitive (pinned
+against an explicit DFT in the tests), and the paper's formulas written out in
+the paper's order.  Nothing is fused, tiled or reordered.
 
 Conventions (readings of the paper where it is silent):
   * A volume with HR sizes (m_h, n_h, s_h) is an array of shape (s_h, n_h, m_h);
     m is the fastest axis ("lexicographic" ordering, Sec. II-A).
   * dec = (dr, dc, ds) decimates the m, n and s axes; r in eq. 9, 12 and
     Algorithm 1 is d = dr*dc*ds.
-  * The DFT is numpy's unnormalised forward transform.  Every formula below is
+  * The DFT is the unnormalised forward transform (fftn).  Every formula below is
     invariant under the choice between it and the paper's unitary F.
   * Lambda is the DFT of the PSF zero-padded to HR size with its centre tap
     (index floor(p/2)) moved to the origin: the eigenvalues of the circulant H.
@@ -34,15 +34,32 @@ Conventions (readings of the paper where it is silent):
 """
 from __future__ import annotations
 
+import os
+
 import numpy as np
+import scipy.fft as _sfft
 
 __all__ = [
     "otf", "blur", "decimate", "zero_fill", "forward", "nearest_neighbour",
     "fold", "replicate", "tikhonov", "grad", "grad_adj", "laplacian_symbol",
     "shrink", "shrink_aniso", "tv_term", "admm_xstep", "admm_tv", "objective", "augmented_lagrangian",
     "tikhonov_grad", "tikhonov_cg", "gaussian_psf_taps", "psf_fit_objective",
-    "psnr",
+    "psnr", "fftn", "ifftn", "FFT_WORKERS",
 ]
+
+# threads of the FFT primitive (the host's cores); the rest of the oracle is
+# single-threaded numpy
+FFT_WORKERS = os.cpu_count() or 1
+
+
+def fftn(a: np.ndarray) -> np.ndarray:
+    """Unnormalised forward 3D DFT X[k] = sum_n a[n] exp(-2 pi i k.n / N) (library primitive)."""
+    return _sfft.fftn(a, workers=FFT_WORKERS)
+
+
+def ifftn(a: np.ndarray) -> np.ndarray:
+    """Inverse of fftn: the conjugate-exponent sum scaled by 1/N (library primitive)."""
+    return _sfft.ifftn(a, workers=FFT_WORKERS)
 
 
 def _lr_shape(shape, dec):
@@ -74,12 +91,12 @@ def otf(psf: np.ndarray, shape) -> np.ndarray:
         raise ValueError("PSF larger than the volume")
     big[:ps, :pn, :pm] = psf
     big = np.roll(big, (-(ps // 2), -(pn // 2), -(pm // 2)), axis=(0, 1, 2))
-    return np.fft.fftn(big)
+    return fftn(big)
 
 
 def blur(x: np.ndarray, lam: np.ndarray) -> np.ndarray:
     """H x = F^H Lambda F x (eq. 2): cyclic convolution."""
-    return np.real(np.fft.ifftn(lam * np.fft.fftn(x)))
+    return np.real(ifftn(lam * fftn(x)))
 
 
 def decimate(z: np.ndarray, dec) -> np.ndarray:
@@ -150,13 +167,13 @@ def tikhonov(y: np.ndarray, psf: np.ndarray, dec, tau: float, xbar=None) -> np.n
     d = dr * dc * ds
     lam = otf(psf, shape)
     # F k with k = H^H D^H y + 2 lambda xbar (eq. 7)
-    Fk = np.conj(lam) * np.fft.fftn(zero_fill(y, dec))
+    Fk = np.conj(lam) * fftn(zero_fill(y, dec))
     if xbar is not None:
-        Fk = Fk + tau * np.fft.fftn(xbar)
+        Fk = Fk + tau * fftn(xbar)
     # eq. (12): x = k/(2l) - 1/(2l) F^H Lam_^H (2l r I + Lam_ Lam_^H)^-1 Lam_ F k
     inner = fold(lam * Fk, dec) / (tau * d + fold(np.abs(lam) ** 2, dec))
     X = Fk / tau - np.conj(lam) * replicate(inner, dec) / tau
-    return np.real(np.fft.ifftn(X))
+    return np.real(ifftn(X))
 
 
 # ---------------------------------------------------------------------------
@@ -225,7 +242,7 @@ def admm_xstep(y: np.ndarray, lam: np.ndarray, theta: np.ndarray, mu: float, dec
     dr, dc, ds = dec
     d = dr * dc * ds
     # F k = Lambda^H F D^H y + mu F Theta
-    Fk = np.conj(lam) * np.fft.fftn(zero_fill(y, dec)) + mu * np.fft.fftn(theta)
+    Fk = np.conj(lam) * fftn(zero_fill(y, dec)) + mu * fftn(theta)
     sym = laplacian_symbol(shape)
     gamma = np.zeros_like(sym)
     nz = sym > 0
@@ -245,7 +262,7 @@ def admm_xstep(y: np.ndarray, lam: np.ndarray, theta: np.ndarray, mu: float, dec
     sol = np.linalg.solve(A, np.array([Fk[i] for i in idx]))
     for i, v in zip(idx, sol):
         X[i] = v
-    return np.real(np.fft.ifftn(X))
+    return np.real(ifftn(X))
 
 
 def objective(x: np.ndarray, y: np.ndarray, psf: np.ndarray, dec, lam_tv: float, aniso: bool = False) -> float:
@@ -300,8 +317,8 @@ def tikhonov_cg(y: np.ndarray, psf: np.ndarray, dec, tau: float, xbar=None, iter
     sampling mask.  Stops after `iters` iterations or when ||r|| <= tol ||b||.
     Returns x, the iterations run and the residual norms ||r_k||."""
     lam = otf(psf, _hr_shape(y.shape, dec))
-    H = lambda v: np.real(np.fft.ifftn(lam * np.fft.fftn(v)))  # noqa: E731
-    Ht = lambda v: np.real(np.fft.ifftn(np.conj(lam) * np.fft.fftn(v)))  # noqa: E731
+    H = lambda v: np.real(ifftn(lam * fftn(v)))  # noqa: E731
+    Ht = lambda v: np.real(ifftn(np.conj(lam) * fftn(v)))  # noqa: E731
     A = lambda v: Ht(zero_fill(decimate(H(v), dec), dec)) + tau * v  # noqa: E731
     b = Ht(zero_fill(y, dec))
     if xbar is not None:

@@ -38,8 +38,10 @@ def test_fft_is_the_unnormalised_dft(shape):
     x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
     Fs, Fn, Fm = (dft_matrix(n) for n in shape)
     ref = np.einsum("ai,bj,ck,ijk->abc", Fs, Fn, Fm, x)
-    assert np.allclose(np.fft.fftn(x), ref, atol=1e-11)
-    assert np.allclose(np.fft.ifftn(ref), x, atol=1e-12)
+    assert np.allclose(O.fftn(x), ref, atol=1e-11)
+    assert np.allclose(O.ifftn(ref), x, atol=1e-12)
+    # the real-input path the oracle takes for volumes
+    assert np.allclose(O.fftn(x.real), np.einsum("ai,bj,ck,ijk->abc", Fs, Fn, Fm, x.real), atol=1e-11)
     # Parseval for the unnormalised transform
     assert np.isclose((np.abs(ref) ** 2).sum(), x.size * (np.abs(x) ** 2).sum())
 
@@ -411,3 +413,39 @@ def test_psf_fit_objective_is_zero_at_the_truth_and_grows_away():
             s = list(s_true)
             s[ax] *= f
             assert O.psf_fit_objective(s, size, x, y, dec)[0] > 1e3 * max(r0, 1e-30)
+
+
+# ---------------------------------------------------------------------------
+# the nearest-neighbour prior of eq. (5): every HR voxel copies the LR voxel of
+# its dr x dc x ds block, checked voxel by voxel (a swap of two axes' factors
+# must fail the check)
+# ---------------------------------------------------------------------------
+
+def _nearest_agrees(fn):
+    dec = (2, 1, 3)  # (dr, dc, ds) on (m, n, s): three different factors
+    y = np.random.default_rng(14).standard_normal((2, 3, 4))  # LR (s, n, m)
+    dr, dc, ds = dec
+    ref = np.zeros((2 * ds, 3 * dc, 4 * dr))
+    for s in range(ref.shape[0]):
+        for n in range(ref.shape[1]):
+            for m in range(ref.shape[2]):
+                ref[s, n, m] = y[s // ds, n // dc, m // dr]
+    got = fn(y, dec)
+    return got.shape == ref.shape and np.array_equal(got, ref)
+
+
+def test_nearest_neighbour_prior_copies_each_lr_voxel_to_its_block():
+    assert _nearest_agrees(O.nearest_neighbour)
+
+
+def test_nearest_neighbour_checker_rejects_planted_mistakes():
+    def swap_m_s(y, dec):
+        dr, dc, ds = dec
+        return O.nearest_neighbour(y, (ds, dc, dr))
+
+    def tiled(y, dec):
+        dr, dc, ds = dec
+        return np.tile(y, (ds, dc, dr))
+
+    assert not _nearest_agrees(swap_m_s)
+    assert not _nearest_agrees(tiled)
