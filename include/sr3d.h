@@ -92,6 +92,17 @@ int sr3d_plan(sr3d_plan_t* out, const sr3d_desc* desc);
 /* Frees the plan and everything it owns (safe with NULL). */
 int sr3d_destroy(sr3d_plan_t plan);
 
+/* Cap on the device memory any one plan may hold, process-wide (bytes <= 0:
+ * no cap, the default).  A plan whose buffers would pass it fails as if
+ * cudaMalloc had failed: sr3d_plan returns SR3D_ERR_OOM and frees everything
+ * it had allocated; an entry point that allocates lazily (the ADMM dual and
+ * residual buffers of the first sr3d_admm_tv, the CG vectors, the host-buffer
+ * staging of sr3d_admm_tv_host) returns SR3D_ERR_OOM and the plan stays
+ * usable.  For budgeting several plans on one device, and for testing the
+ * out-of-memory path without exhausting the device.  Not in the paper.
+ * Always returns SR3D_OK. */
+int sr3d_set_plan_memory_limit(long long bytes);
+
 /* Degradation operator of eq. (1) without noise: y_dev = D H x_dev
  * (HR x in, LR y out).  Used to synthesise observations.  Errors:
  * INVALID_ARG (NULL arrays), CUDA. */
@@ -218,22 +229,26 @@ int sr3d_profile(sr3d_plan_t plan, int on);
 int sr3d_profile_read(sr3d_plan_t plan, double ms[SR3D_NKINDS], long long launches[SR3D_NKINDS]);
 
 /* Allocation-free Tikhonov solve (no counterpart in the paper: an
- * interface for callers that cannot allocate device memory once running,
- * such as real-time reconstruction loops with a fixed memory budget or code
- * inside CUDA stream capture, where cudaMalloc is not allowed).  Same result
- * as sr3d_plan + sr3d_tikhonov + sr3d_destroy for the descriptor `desc`
- * (desc->stream NULL = the legacy default stream), but every piece of work
- * memory is carved from one file-scope device array of SR3D_NOALLOC_BYTES
- * (8 MiB), held by every GPU that loads the library until the process exits;
- * the call makes no cudaMalloc/cudaFree and no allocating library call.
- * The work memory is about 8 bytes per HR voxel in FP32 (16 in FP64), so
- * volumes up to about 2^19 HR voxels in FP32 (e.g. 128 x 64 x 64) or 2^18 in
- * FP64 fit; larger ones fail with SR3D_ERR_UNSUPPORTED_SIZE.
- * The first call on a device looks up the array's device address (make it
- * before any stream capture).  All calls share the array and every call
- * overwrites it, so calls that overlap on the GPU (other streams, other host
- * threads) race; serialise them.  Inputs and outputs are the caller's device
- * arrays as in sr3d_tikhonov. */
+ * interface for callers that may not allocate device memory once running --
+ * a reconstruction loop whose device-memory budget is fixed at start-up, or a
+ * plug-in inside a host application that owns the device's memory pool --
+ * where a cudaMalloc can fail, or stall the whole device while it
+ * synchronises).  Same result as sr3d_plan + sr3d_tikhonov + sr3d_destroy for
+ * the descriptor `desc` (desc->stream NULL = the legacy default stream), but
+ * every piece of work memory is carved from one file-scope device array of
+ * SR3D_NOALLOC_BYTES (8 MiB), held by every GPU that loads the library until
+ * the process exits; the call makes no cudaMalloc/cudaFree and no allocating
+ * library call.  The work memory is about 8 bytes per HR voxel in FP32 (16 in
+ * FP64), so volumes up to about 2^19 HR voxels in FP32 (e.g. 128 x 64 x 64)
+ * or 2^18 in FP64 fit; larger ones fail with SR3D_ERR_UNSUPPORTED_SIZE
+ * before any work is queued.  The first call on a device looks up the
+ * array's device address (once per device, with that device current); make
+ * that first call before any stream capture.  The PSF is copied from host
+ * memory on the stream and the call returns after the result is complete.
+ * All calls share the array and every call overwrites it, so calls that
+ * overlap on the GPU (other streams, other host threads) race; serialise
+ * them.  Inputs and outputs are the caller's device arrays as in
+ * sr3d_tikhonov. */
 #define SR3D_NOALLOC_BYTES (8u << 20)
 int sr3d_tikhonov_noalloc(const sr3d_desc* desc, const void* y_dev, const void* xbar_dev, double tau,
                           void* x_dev);
@@ -309,6 +324,18 @@ int sr3d_unet_train_step(sr3d_unet_t net, int m, int n, int s, const float* x_de
 #define SR3D_UNET_PATH_MMA 1
 #define SR3D_UNET_PATH_TCGEN05_ALL 2
 int sr3d_unet_set_path(sr3d_unet_t net, int path);
+
+/* Test support for the bounded waits of the tcgen05 kernel: one CTA allocates
+ * tensor memory as that kernel does, waits with the same bounded wait,
+ * shortened to limit_cycles SM clock cycles (1 .. 2e9), on an mbarrier that
+ * nothing arrives on (no MMA issued, none in flight), sets the network's
+ * device error flag when the wait runs out, frees its tensor memory and
+ * returns; the call then reports SR3D_ERR_TIMEOUT exactly as a forward or
+ * training call would.  After a timeout of the real kernels the results of
+ * that launch, and of any later launch on the stream, are to be discarded;
+ * after this self-test the network stays usable.  Errors: INVALID_ARG,
+ * TIMEOUT (the expected outcome), CUDA. */
+int sr3d_unet_wait_selftest(sr3d_unet_t net, long long limit_cycles);
 
 /* Copies an activation of the last forward pass (sr3d_unet_forward or
  * sr3d_unet_train_step) to host memory, for inspection and layer-by-layer

@@ -36,6 +36,7 @@ EXPORTED = [
     "sr3d_separable", "sr3d_set_tv", "sr3d_tikhonov_grad", "sr3d_tikhonov_cg", "sr3d_set_psf",
     "sr3d_dual_init", "sr3d_unet_param_count", "sr3d_unet_create", "sr3d_unet_destroy", "sr3d_unet_set_params",
     "sr3d_unet_get_params", "sr3d_unet_forward", "sr3d_unet_train_step", "sr3d_unet_read", "sr3d_unet_set_path",
+    "sr3d_set_plan_memory_limit", "sr3d_unet_wait_selftest",
 ]
 KINDS = ["tv", "rfft_m_fwd", "fft_n_fwd", "fft_s", "fft_n_inv", "rfft_m_inv", "other", "setup"]
 
@@ -110,6 +111,8 @@ def load() -> ctypes.CDLL:
         "sr3d_unet_train_step": (i, [vp, i, i, i, vp, vp, d, ctypes.POINTER(d), vp, i]),
         "sr3d_unet_read": (i, [vp, i, vp, ctypes.c_longlong]),
         "sr3d_unet_set_path": (i, [vp, i]),
+        "sr3d_set_plan_memory_limit": (i, [ctypes.c_longlong]),
+        "sr3d_unet_wait_selftest": (i, [vp, ctypes.c_longlong]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -394,6 +397,11 @@ def tikhonov_noalloc(dims, dec, psf, y, tau: float, x, xbar=None, dtype: str = "
     return x
 
 
+def set_plan_memory_limit(nbytes: int):
+    """Cap on the device bytes any one plan may hold (sr3d_set_plan_memory_limit; 0 = none)."""
+    _check(load().sr3d_set_plan_memory_limit(int(nbytes)))
+
+
 def admm_tv_batched(plans, ys, xs, lams, rhos, taus, iters: int):
     """sr3d_admm_tv_batched: ADMM-TV on many volumes (one plan each, each plan
     created with its own stream), iterations of all volumes in one CUDA graph."""
@@ -462,6 +470,11 @@ class UNet:
         """Convolution kernels (sr3d_unet_set_path): "tcgen05" (default: tcgen05 where it is the
         faster kernel), "mma" (mma.sync everywhere) or "tcgen05_all" (tcgen05 wherever it applies)."""
         _check(load().sr3d_unet_set_path(self._h, {"tcgen05": 0, "mma": 1, "tcgen05_all": 2}[path]))
+
+    def wait_selftest(self, limit_cycles: int):
+        """Makes the bounded tensor-core wait run out on a barrier nothing
+        arrives on (sr3d_unet_wait_selftest); raises Sr3dError TIMEOUT."""
+        _check(load().sr3d_unet_wait_selftest(self._h, int(limit_cycles)))
 
     ACTIVATIONS = ["x", "e1a", "e1", "p1", "e2a", "e2", "p2", "e3a", "e3", "d2a", "d2", "d1a", "d1", "out"]
 

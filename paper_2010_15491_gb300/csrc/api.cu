@@ -13,6 +13,7 @@
 #include <tuple>
 #include <string>
 #include <algorithm>
+#include <atomic>
 #include <initializer_list>
 #include <vector>
 
@@ -165,7 +166,17 @@ static int validate_lengths(const Geometry& g, size_t csz) {
   return SR3D_OK;
 }
 
+// Cap on the device bytes one plan may hold (0 = none); see
+// sr3d_set_plan_memory_limit.  A plan that would pass it fails with
+// SR3D_ERR_OOM exactly as if cudaMalloc had failed.
+static std::atomic<long long> g_plan_mem_limit{0};
+
 static int dmalloc(Plan& p, void** ptr, size_t bytes) {
+  const long long cap = g_plan_mem_limit.load();
+  if (cap > 0 && p.bytes + (long long)bytes > cap) {
+    *ptr = nullptr;
+    return fail(SR3D_ERR_OOM, "plan memory limit: %lld bytes held + %zu requested > %lld", p.bytes, bytes, cap);
+  }
   cudaError_t e = cudaMalloc(ptr, bytes);
   if (e != cudaSuccess) {
     *ptr = nullptr;
@@ -576,6 +587,11 @@ int sr3d_plan(sr3d_plan_t* out, const sr3d_desc* d) {
   return SR3D_OK;
 }
 
+int sr3d_set_plan_memory_limit(long long bytes) {
+  g_plan_mem_limit.store(bytes > 0 ? bytes : 0);
+  return SR3D_OK;
+}
+
 int sr3d_destroy(sr3d_plan_t plan) {
   if (!plan) return SR3D_OK;
   cudaStreamSynchronize(plan->p.stream);
@@ -924,6 +940,7 @@ static int ensure_hist(Plan& p, int n) {
     cudaFree(p.hist);
     p.bytes -= (long long)p.hist_cap * sizeof(double);
     p.hist = nullptr;
+    p.hist_cap = 0;  // stays 0 if the allocation below fails
   }
   TRY(dmalloc(p, (void**)&p.hist, (size_t)n * sizeof(double)));
   p.hist_cap = n;
@@ -1118,11 +1135,15 @@ static std::vector<int> pad_candidates(std::initializer_list<int> base, int ms, 
 
 static int realloc_partials(Plan& p) {
   const long long ns = s_pass_blocks(p.hr);
-  if (ns > p.n_s_blocks) {
-    cudaFree(p.partial_s);
-    p.partial_s = nullptr;
-    TRY(dmalloc(p, (void**)&p.partial_s, (size_t)ns * sizeof(double)));
-    p.n_s_blocks = ns;
+  if (ns > p.n_s_blocks || !p.partial_s) {
+    if (p.partial_s) {
+      cudaFree(p.partial_s);
+      p.bytes -= (long long)p.n_s_blocks * sizeof(double);
+      p.partial_s = nullptr;
+    }
+    const long long n = ns > p.n_s_blocks ? ns : p.n_s_blocks;
+    TRY(dmalloc(p, (void**)&p.partial_s, (size_t)n * sizeof(double)));
+    p.n_s_blocks = n;
   }
   return SR3D_OK;
 }
@@ -1413,13 +1434,15 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
 // ---------------------------------------------------------------------------
 // Allocation-free Tikhonov solve.
 //
-// For callers that must not allocate device memory once they are running:
-// hard real-time reconstruction loops and embedded scanner software with a
-// fixed device-memory budget decided at start-up, and code that runs while a
-// CUDA stream is being captured, where cudaMalloc is not allowed.  All the
-// work memory (twiddle and symbol tables, Lambda, the LR spectrum, the HR
+// For callers that may not allocate device memory once they are running: a
+// reconstruction loop whose device-memory budget is fixed at start-up, or a
+// plug-in inside a host application that owns the device's memory pool.  All
+// the work memory (twiddle and symbol tables, Lambda, the LR spectrum, the HR
 // spectrum) lives in one file-scope device array of SR3D_NOALLOC_BYTES, so
-// every GPU that loads this library holds it until the process exits.
+// every GPU that loads this library holds it until the process exits.  The
+// first call on a device looks up the array's device address; it should come
+// before any stream capture.  Calls share the array: calls that overlap on the
+// GPU race.
 // ---------------------------------------------------------------------------
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SR3D_NOALLOC_BYTES];
 

@@ -384,8 +384,10 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-// bounded wait for the completion of phase `parity` of an mbarrier
-__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
+// bounded wait for the completion of phase `parity` of an mbarrier: false
+// once `limit` SM clock cycles have passed (the default is about one second)
+constexpr long long kWaitLimit = 2000000000LL;
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity, long long limit = kWaitLimit) {
   const long long t0 = clock64();
   while (true) {
     uint32_t ok;
@@ -395,7 +397,7 @@ __device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t parity) {
         : "r"(su32(bar)), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > 2000000000LL) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 
@@ -515,7 +517,10 @@ __global__ void __launch_bounds__(128, 1) k_conv3_tc(ConvIn in, const bf16* __re
     return true;
   };
 
-  int j = 0;
+  // The failure decision is CTA-wide (__syncthreads_or), so once any thread's
+  // completion wait runs out no thread issues further plane loads or MMAs.
+  int j = 0, last = -1;  // last = index of the last committed MMA batch
+  bool bad = false;
   for (int s = s0; s < s_end; ++s, ++j) {
     if (s + 1 < s_end) load_plane(s + 2);  // needed by line s+1; its slot held plane s-3, drained at step j-1
     cp_commit_();
@@ -536,15 +541,55 @@ __global__ void __launch_bounds__(128, 1) k_conv3_tc(ConvIn in, const bf16* __re
       }
       tc::commit(&bars[j & 1]);
     }
-    if (j >= 1) ok = ok && epilogue(j - 1, s - 1);
+    last = j;
+    bool mine = true;
+    if (j >= 1) mine = epilogue(j - 1, s - 1);
     cp_wait_<0>();
     tc::fence_async_smem();
     tc::fence_before();
-    __syncthreads();
+    bad = __syncthreads_or(!mine) != 0;
     tc::fence_after();
+    if (bad) break;
   }
-  if (j >= 1) ok = ok && epilogue(j - 1, s_end - 1);
-  if (!ok && lane == 0) atomicExch(err, 1);
+  if (!bad && j >= 1) {
+    const bool mine = epilogue(j - 1, s_end - 1);
+    bad = __syncthreads_or(!mine) != 0;
+  }
+  if (bad) {
+    // A completion wait ran out.  Before the accumulator columns are freed,
+    // one more bounded wait on the last commit, which covers every MMA this
+    // CTA issued; then the flag tells the host to discard this launch's output.
+    if (tid == 0 && last >= 0) tc::wait_bar(&bars[last & 1], (uint32_t)((last >> 1) & 1));
+    if (tid == 0) atomicExch(err, 1);
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
+// Self-test of the bounded completion wait and of the error path that follows
+// it: one CTA allocates TMEM as k_conv3_tc does, waits with the same bounded
+// wait, shortened to `limit` cycles, on an mbarrier that nothing arrives on
+// (no MMA is issued and none is in flight), sets *err when the wait runs out,
+// then frees its TMEM and returns.
+__global__ void __launch_bounds__(128, 1) k_wait_selftest(long long limit, int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(tc::su32(&tslot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::su32(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tslot;
+  if (threadIdx.x == 0 && !tc::wait_bar(&bar, 0u, limit)) atomicExch(err, 1);
   tc::fence_before();
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
@@ -1224,7 +1269,9 @@ static int check_dims(int m, int n, int s) {
   return SR3D_OK;
 }
 
-// waits for the stream; SR3D_ERR_TIMEOUT if a bounded wait of the tcgen05 kernel ran out
+// waits for the stream; SR3D_ERR_TIMEOUT if a bounded wait of the tcgen05
+// kernel ran out (the results of that launch, and of every later launch on the
+// stream, are then to be discarded)
 static int finish(sr3d_unet_s* u) {
   int h = 0;
   UCK(cudaMemcpyAsync(&h, u->err, sizeof(int), cudaMemcpyDeviceToHost, u->stream));
@@ -1272,6 +1319,14 @@ int sr3d_unet_train_step(sr3d_unet_t u, int m, int n, int s, const float* x, con
   UCK(cudaMemcpyAsync(&l, u->loss, sizeof(double), cudaMemcpyDeviceToHost, u->stream));
   UCK(cudaStreamSynchronize(u->stream));
   if (loss) *loss = l / ((double)m * n * s);
+  return finish(u);
+}
+
+int sr3d_unet_wait_selftest(sr3d_unet_t u, long long limit_cycles) {
+  if (!u || limit_cycles < 1 || limit_cycles > tc::kWaitLimit)
+    return ufail(SR3D_ERR_INVALID_ARG, "wait limit must be in [1, 2e9] cycles");
+  k_wait_selftest<<<1, 128, 0, u->stream>>>(limit_cycles, u->err);
+  UCK(cudaGetLastError());
   return finish(u);
 }
 
