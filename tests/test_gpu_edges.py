@@ -43,7 +43,7 @@ def test_delta_psf_and_smallest_s(lib, dtype):
     _, xt, _ = make_problem(dims, dec, seed=122)
     y = O.forward(xt, psf, dec) + 0.01 * np.random.default_rng(123).standard_normal((2, 8, 32))
     plan = lib.Plan(dims, dec, psf, dtype)
-    tol = 1e-5 if dtype == "f32" else 1e-11
+    tol = 1e-5 if dtype == "f32" else 1e-12
     for prior in (None, "nearest"):
         x = plan.tikhonov(T(y, dtype), 0.3, xbar=prior)
         xb = None if prior is None else O.nearest_neighbour(y, dec)
@@ -64,5 +64,5 @@ def test_zero_tv_weight(lib):
     x = plan.empty_hr()
     plan.admm_tv(T(y, "f64"), x, 0.0, 1e-2, 6, tau_init=1e-2)
     x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
-    assert rel_l2(H(x), O.admm_tv(y, psf, dec, 0.0, 1e-2, 6, x0)["x"]) < 1e-11
+    assert rel_l2(H(x), O.admm_tv(y, psf, dec, 0.0, 1e-2, 6, x0)["x"]) < 1e-12
     plan.close()

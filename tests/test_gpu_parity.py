@@ -1,7 +1,7 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances: FP32 plans must match the FP64 oracle within 1e-5 relative L2;
-FP64 plans within 1e-11.  Inputs are seeded synthetic phantoms; every expected
+FP64 plans within 1e-12.  Inputs are seeded synthetic phantoms; every expected
 value comes from oracle/.
 """
 import numpy as np
@@ -12,7 +12,7 @@ from tests._problems import make_problem, rel_l2
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f32": 1e-5, "f64": 1e-11}
+TOL = {"f32": 1e-5, "f64": 1e-12}
 
 # (dims (m, n, s), dec (dr, dc, ds), dtype): several tiles with ragged tails,
 # mixed radix (96, 48, 24, 12), anisotropic and no decimation.
@@ -177,13 +177,13 @@ def test_tolerance_stop_and_zero_iterations(lib):
     assert st["primal_rel"] < 1e-3 and st["dual_rel"] < 1e-3
     x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
     ref = O.admm_tv(y, psf, dec, 1e-3, 1e-2, st["iters"], x0, record=True)
-    assert rel_l2(H(x), ref["x"]) < 1e-10
+    assert rel_l2(H(x), ref["x"]) < TOL["f64"]
     rel_p = ref["hist"]["primal"][-1] / max(ref["hist"]["norm_Lx"][-1], ref["hist"]["norm_u"][-1])
     assert np.isclose(st["primal_rel"], rel_p, rtol=1e-6)
     # zero iterations returns the Tikhonov start
     x2 = plan.empty_hr()
     plan.admm_tv(T(y, "f64"), x2, 1e-3, 1e-2, 0, tau_init=1e-2)
-    assert rel_l2(H(x2), x0) < 1e-11
+    assert rel_l2(H(x2), x0) < TOL["f64"]
     plan.close()
 
 
@@ -279,7 +279,7 @@ def test_statistics_blocks_replayed_as_graphs_match_eager(lib, every, dtype):
     x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
     ref = O.admm_tv(y, psf, dec, 2e-3, 1e-2, 23, x0, record=True)
     its = [k for k in range(1, 24) if k % every == 0 or k == 23]
-    tol = 1e-5 if dtype == "f32" else 1e-10
+    tol = 1e-5 if dtype == "f32" else 1e-12
     assert np.allclose(sa["objective_hist"], [ref["hist"]["objective"][k - 1] for k in its], rtol=tol)
     plan.close()
 
@@ -473,30 +473,6 @@ def test_gaussian_psf_fit(lib):
     res = psf_fit.fit_gaussian_psf(plan, xd, yd, sigma0=(1.0, 1.0, 1.0), bounds=(0.3, 3.0))
     assert np.allclose(res["sigma"], s_true, rtol=1e-3), res
     assert np.isclose(res["gain"], 2.0, rtol=1e-4) and np.isclose(res["offset"], 0.1, rtol=1e-3)
-    plan.close()
-
-
-@pytest.mark.slow
-def test_headline_error_curve(lib, tag):
-    """256^3 benchmark workload: relative L2 error of the FP32 iterate against
-    the FP64 oracle after 1, 2, 5 and 10 ADMM-TV iterations."""
-    from synth import HEADLINE_256 as W, noise_sigma
-    psf = W.psf()
-    x = W.phantom()
-    clean = O.forward(x, psf, W.dec)
-    y = clean + noise_sigma(clean, W.snr_db) * W.noise()
-    plan = lib.Plan(W.dims, W.dec, psf, "f32")
-    plan.autotune()
-    x0 = O.tikhonov(y, psf, W.dec, W.tau, O.nearest_neighbour(y, W.dec))
-    ks = (1, 2, 5, 10)
-    ref = {}
-    O.admm_tv(y, psf, W.dec, W.lam, W.mu, max(ks), x0,
-              callback=lambda i, xi, u, d: ref.__setitem__(i + 1, xi.copy()) if i + 1 in ks else None)
-    yd = T(y, "f32")
-    for k in ks:
-        xg = plan.empty_hr()
-        plan.admm_tv(yd, xg, W.lam, W.mu, k, tau_init=W.tau)
-        assert rel_l2(H(xg), ref[k], tag(f"x{k}")) < TOL["f32"], k
     plan.close()
 
 

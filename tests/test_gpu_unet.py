@@ -234,7 +234,7 @@ def test_admm_from_network_output_and_dual(lib):
     d = p.dual_init(x, lam, rho)
     p.admm_tv(yd, x, lam, rho, 6, d=d)
     ref = O.admm_tv(y, psf, dec, lam, rho, 6, x0, d0=U.dual_from_x(x0, lam, rho))
-    assert rel_l2(x.cpu().numpy(), ref["x"]) < 1e-11
+    assert rel_l2(x.cpu().numpy(), ref["x"]) < 1e-12
     p.close()
 
 
