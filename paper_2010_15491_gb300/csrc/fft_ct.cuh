@@ -95,6 +95,17 @@ __device__ __forceinline__ void ct_run(const Ld& ld, const St& st, float2* line,
   }
 }
 
+// Stages I .. END-1 (END < number of stages): stage 0 reads through ld, every
+// stage writes the line in shared memory (barrier after each).
+template <int N, int I, int END, bool PAD, class Ld>
+__device__ __forceinline__ void ct_run_to(const Ld& ld, float2* line, int es, int tl, const float2* __restrict__ tws,
+                                          int twstep) {
+  if constexpr (I < END) {
+    ct_stage<N, I, I == 0, false, PAD>(ld, CtNone{}, line, es, tl, tws, twstep);
+    ct_run_to<N, I + 1, END, PAD>(ld, line, es, tl, tws, twstep);
+  }
+}
+
 // global -> global.  Every load precedes the first barrier and every store
 // follows it, so ld and st may alias.
 template <int N, bool PAD = false, class Ld, class St>

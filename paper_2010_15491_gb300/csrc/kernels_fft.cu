@@ -166,6 +166,156 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_inv(const cplx<T>* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// m passes with the real-FFT split in registers (FP32, compile-time lengths,
+// d_r = 1 or 2).  After the last radix-16 stage of the half-length transform
+// (length NC = M/2, TPL = NC/16 threads per line), thread tl holds Z[k] for
+// k = tl + TPL r, r < 16.  The split of the real transform pairs Z[g] with
+// Z[NC - g], which sits in lane (TPL - tl) mod TPL at r' = 15 - r (lane 0:
+// itself, r' = 16 - r), so one warp shuffle per pair replaces the shared-
+// memory round trip of the split:
+//   E = (Z[g] + conj Z[NC-g]) / 2,  O = -i (Z[g] - conj Z[NC-g]) / 2,
+//   X[g] = E + W^g O,  X[NC-g] = conj(E - W^g O)   (W = exp(-2 pi i / M)).
+// With d_r = 2 the slots 2g and 2g+1 hold X[g] and conj(X[NC-g]) (frequency
+// g + NC, conjugated), i.e. E + W^g O and E - W^g O: one 16-byte store per g,
+// and the inverse pass reads the same 16 bytes to form its inputs for g and
+// NC - g.  The inverse input set of thread tl (k = tl + TPL m) is the same
+// index set, so the first inverse stage runs from registers.
+// ---------------------------------------------------------------------------
+template <int NC, int DR>
+__global__ void __launch_bounds__(256, 2) k_rfft_m_fwd2(const float* __restrict__ in, long long nlines,
+                                                      float2* __restrict__ out, int Mp, int L, int Hp,
+                                                      const float2* __restrict__ twM) {
+  constexpr int TPL = NC / 16;
+  constexpr int NST = ct_nst(NC);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  float2* tws = sm + L * Hp;  // the M = 2 NC roots
+  ct_load_twiddles(tws, twM, 2 * NC);
+  const int l = threadIdx.x / TPL, tl = threadIdx.x % TPL;
+  const long long gl = (long long)blockIdx.x * L + l;
+  const bool ok = gl < nlines;
+  const float2* src = reinterpret_cast<const float2*>(in) + gl * NC;  // (x[2j], x[2j+1]) as one complex
+  float2* line = sm + l * Hp;
+  auto ld = [&](int j) -> float2 { return ok ? __ldg(&src[j]) : make_float2(0.f, 0.f); };
+  ct_run_to<NC, 0, NST - 1, true>(ld, line, 1, tl, tws, 2);
+  // last stage (radix 16, NS = TPL) into registers: v[r] = Z[tl + TPL r]
+  float2 v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    float2 a = line[ct_pos<true>(tl + r * TPL)];
+    if (r > 0) a = cmul(a, tws[tl * r * 2]);
+    v[r] = a;
+  }
+  Dft<16, float2, float>::run(v);
+  const int lane = threadIdx.x & 31;
+  const int partner = lane - tl + ((TPL - tl) & (TPL - 1));
+  float2* orow = out + gl * Mp;
+#pragma unroll
+  for (int r = 0; r <= 8; ++r) {
+    float2 zh;
+    if (r < 8) {
+      float2 recv;
+      recv.x = __shfl_sync(0xffffffffu, v[15 - r].x, partner);
+      recv.y = __shfl_sync(0xffffffffu, v[15 - r].y, partner);
+      zh = tl == 0 ? v[(16 - r) & 15] : recv;
+    } else {
+      zh = v[8];  // g = NC/2 (lane 0 only)
+    }
+    const int g = tl + TPL * r;
+    const float2 zc = conjc(zh);
+    const float2 e = (v[r] + zc) * 0.5f;
+    const float2 o = mul_mi(v[r] - zc) * 0.5f;
+    const float2 t = cmul(tws[r < 8 ? g : NC / 2], o);
+    if (ok && (r < 8 || tl == 0)) {
+      const float2 xp = e + t, xm = e - t;
+      if constexpr (DR == 2) {
+        reinterpret_cast<float4*>(orow)[g] = make_float4(xp.x, xp.y, xm.x, xm.y);
+      } else {
+        orow[g] = xp;
+        if (r < 8 || tl != 0) orow[NC - g] = conjc(xm);  // g = NC/2: the same slot
+      }
+    }
+  }
+}
+
+template <int NC, int DR>
+__global__ void __launch_bounds__(256, 2) k_rfft_m_inv2(const float2* __restrict__ in, long long nlines,
+                                                      float* __restrict__ out, int Mp, int L, int Hp,
+                                                      const float2* __restrict__ twM, float scale) {
+  constexpr int TPL = NC / 16;
+  constexpr int R0 = ct_radix(NC, 0);
+  constexpr int NB = 16 / R0;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  float2* tws = sm + L * Hp;
+  ct_load_twiddles(tws, twM, 2 * NC);
+  const int l = threadIdx.x / TPL, tl = threadIdx.x % TPL;
+  const long long gl = (long long)blockIdx.x * L + l;
+  const bool ok = gl < nlines;
+  const float2* row = in + gl * Mp;
+  // pairs g = tl + TPL m: X[g] and conj(X[NC - g])
+  float2 xk[9], xh[9];
+#pragma unroll
+  for (int m = 0; m <= 8; ++m) {
+    const int g = tl + TPL * m;
+    const bool act = ok && (m < 8 || tl == 0);
+    xk[m] = make_float2(0.f, 0.f);
+    xh[m] = make_float2(0.f, 0.f);
+    if (act) {
+      if constexpr (DR == 2) {
+        const float4 q4 = __ldg(reinterpret_cast<const float4*>(row) + g);
+        xk[m] = make_float2(q4.x, q4.y);
+        xh[m] = make_float2(q4.z, q4.w);
+      } else {
+        xk[m] = __ldg(&row[g]);
+        xh[m] = conjc(__ldg(&row[NC - g]));
+      }
+    }
+  }
+  // inverse inputs (the forward engine on conjugated data): z[m] = Zi[tl + TPL m]
+  float2 z[16];
+  const int lane = threadIdx.x & 31;
+  const int partner = lane - tl + ((TPL - tl) & (TPL - 1));
+#pragma unroll
+  for (int m = 0; m <= 8; ++m) {
+    const int g = tl + TPL * m;
+    const float2 e = xk[m] + xh[m];
+    const float2 o = cmulc(tws[m < 8 ? g : NC / 2], xk[m] - xh[m]);  // W^-g (X[g] - conj X[NC-g])
+    const float2 zg = conjc(e + mul_i(o));                           // input g
+    const float2 zp = e - mul_i(o);                                  // input NC - g
+    if (m < 8) {
+      z[m] = zg;
+      float2 recv;
+      recv.x = __shfl_sync(0xffffffffu, zp.x, partner);
+      recv.y = __shfl_sync(0xffffffffu, zp.y, partner);
+      if (tl != 0) z[15 - m] = recv;
+      else if (m >= 1) z[16 - m] = zp;
+    } else if (tl == 0) {
+      z[8] = zg;
+    }
+  }
+  // stage 0 (radix R0, no twiddles) from the registers: butterfly j = tl + u TPL
+  // takes inputs j + r NC/R0 = tl + TPL (u + r NB)
+  float2* line = sm + l * Hp;
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    float2 w[R0];
+#pragma unroll
+    for (int r = 0; r < R0; ++r) w[r] = z[u + r * NB];
+    Dft<R0, float2, float>::run(w);
+    const int j = tl + u * TPL;
+#pragma unroll
+    for (int r = 0; r < R0; ++r) line[ct_pos<true>(j * R0 + r)] = w[r];
+  }
+  __syncthreads();
+  float2* outc = reinterpret_cast<float2*>(out) + gl * NC;
+  auto st = [&](int j, float2 r) {
+    if (ok) outc[j] = make_float2(r.x * scale, -r.y * scale);
+  };
+  ct_run<NC, 1, false, true, true>(CtNone{}, st, line, 1, tl, tws, 2);
+}
+
+// ---------------------------------------------------------------------------
 // n pass: tile of TW m-slots x all N rows of one s plane.
 // ---------------------------------------------------------------------------
 template <typename T, int EMAX, bool INV, int NC>
@@ -237,10 +387,70 @@ static cudaError_t rfft_inv_k(const Plan& p, const Geometry& g, const void* in, 
   return cudaGetLastError();
 }
 
+template <int NC, int DR>
+static cudaError_t rfft_fwd2_k(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw) {
+  int L, Hp, threads;
+  size_t smem;
+  m_launch_shape(g, sizeof(float2), g.lm_f, L, Hp, threads, smem);
+  Hp = ct_line_pitch<true>(NC);
+  smem = (size_t)(L * Hp + 2 * NC) * sizeof(float2);
+  const long long nlines = (long long)g.S * g.N;
+  const unsigned blocks = (unsigned)((nlines + L - 1) / L);
+  cudaError_t e;
+  if ((e = allow_smem(k_rfft_m_fwd2<NC, DR>, smem)) != cudaSuccess) return e;
+  k_rfft_m_fwd2<NC, DR><<<blocks, threads, smem, p.stream>>>((const float*)in, nlines, (float2*)out, g.Mp, L, Hp,
+                                                           (const float2*)tw);
+  return cudaGetLastError();
+}
+
+template <int NC, int DR>
+static cudaError_t rfft_inv2_k(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw,
+                               double scale) {
+  int L, Hp, threads;
+  size_t smem;
+  m_launch_shape(g, sizeof(float2), g.lm_i, L, Hp, threads, smem);
+  Hp = ct_line_pitch<true>(NC);
+  smem = (size_t)(L * Hp + 2 * NC) * sizeof(float2);
+  const long long nlines = (long long)g.S * g.N;
+  const unsigned blocks = (unsigned)((nlines + L - 1) / L);
+  cudaError_t e;
+  if ((e = allow_smem(k_rfft_m_inv2<NC, DR>, smem)) != cudaSuccess) return e;
+  k_rfft_m_inv2<NC, DR><<<blocks, threads, smem, p.stream>>>((const float2*)in, nlines, (float*)out, g.Mp, L, Hp,
+                                                           (const float2*)tw, (float)scale);
+  return cudaGetLastError();
+}
+
+// the register-split m passes: FP32, compile-time half length, d_r 1 or 2
+template <int DR>
+static cudaError_t rfft2_fwd_len(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw) {
+  switch (ct_len<float>(g.M / 2, g.fm)) {
+    case 32: return rfft_fwd2_k<32, DR>(p, g, in, out, tw);
+    case 64: return rfft_fwd2_k<64, DR>(p, g, in, out, tw);
+    case 128: return rfft_fwd2_k<128, DR>(p, g, in, out, tw);
+    case 256: return rfft_fwd2_k<256, DR>(p, g, in, out, tw);
+    case 512: return rfft_fwd2_k<512, DR>(p, g, in, out, tw);
+  }
+  return cudaErrorNotSupported;
+}
+template <int DR>
+static cudaError_t rfft2_inv_len(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw,
+                                 double scale) {
+  switch (ct_len<float>(g.M / 2, g.fm)) {
+    case 32: return rfft_inv2_k<32, DR>(p, g, in, out, tw, scale);
+    case 64: return rfft_inv2_k<64, DR>(p, g, in, out, tw, scale);
+    case 128: return rfft_inv2_k<128, DR>(p, g, in, out, tw, scale);
+    case 256: return rfft_inv2_k<256, DR>(p, g, in, out, tw, scale);
+    case 512: return rfft_inv2_k<512, DR>(p, g, in, out, tw, scale);
+  }
+  return cudaErrorNotSupported;
+}
+
 template <typename T>
 static cudaError_t rfft_fwd_t(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw) {
   if (fam3(g.fm)) return rfft_fwd_k<T, Emax<T>::p3, 0>(p, g, in, out, tw);
   if constexpr (sizeof(T) == 4) {
+    if (ct_len<T>(g.M / 2, g.fm) > 0 && (g.dr == 1 || g.dr == 2))
+      return g.dr == 2 ? rfft2_fwd_len<2>(p, g, in, out, tw) : rfft2_fwd_len<1>(p, g, in, out, tw);
     switch (ct_len<T>(g.M / 2, g.fm)) {
       case 32: return rfft_fwd_k<T, 16, 32>(p, g, in, out, tw);
       case 64: return rfft_fwd_k<T, 16, 64>(p, g, in, out, tw);
@@ -257,6 +467,8 @@ static cudaError_t rfft_inv_t(const Plan& p, const Geometry& g, const void* in, 
                               double scale) {
   if (fam3(g.fm)) return rfft_inv_k<T, Emax<T>::p3, 0>(p, g, in, out, tw, scale);
   if constexpr (sizeof(T) == 4) {
+    if (ct_len<T>(g.M / 2, g.fm) > 0 && (g.dr == 1 || g.dr == 2))
+      return g.dr == 2 ? rfft2_inv_len<2>(p, g, in, out, tw, scale) : rfft2_inv_len<1>(p, g, in, out, tw, scale);
     switch (ct_len<T>(g.M / 2, g.fm)) {
       case 32: return rfft_inv_k<T, 16, 32>(p, g, in, out, tw, scale);
       case 64: return rfft_inv_k<T, 16, 64>(p, g, in, out, tw, scale);

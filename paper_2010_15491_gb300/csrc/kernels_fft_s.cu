@@ -347,6 +347,224 @@ __global__ void __launch_bounds__(NC > 0 ? 256 : 512, NC > 0 ? 3 : 1) k_fft_s(cp
   else fft_line_sg<T, EMAX>(line, st, rowlen, a.f, tl, tpl, twS, 1);
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident s pass of the ADMM x-update (Algorithm 1 step 5a) for
+// 256-point s lines in FP32 with the class shape DR x DC x DS fixed at compile
+// time.  Each 256-point transform is two radix-16 Stockham stages: after the
+// forward transform's second stage, thread tl of a line holds the
+// frequencies k = tl + 16 r (r < 16) in registers, so the DS members
+// k, k + 256/DS, ... of an aliasing class along s are in the same thread, and
+// those frequencies are exactly the inputs of the inverse transform's first
+// stage.  The class's DR x DC members in the (m, n) plane sit in QN = DR * DC
+// adjacent lanes of one warp (lane layout q + QN * (gm + GMc * tl), q = pm +
+// DR * pn), and the solve exchanges only per-class scalars by warp shuffles
+// (the dominant member, the Sherman-Morrison sums and the ratio).  Each
+// element crosses shared memory four times (one round trip per transform)
+// instead of going through a shared tile for the solve.  Same arithmetic as
+// solve_tile: B = conj(Lambda) Y + mu F Theta, the dominant member
+// (largest |Lambda|^2 w, ties to the lowest member index) kept out of the
+// sums, the zero-frequency class solved exactly.
+// ---------------------------------------------------------------------------
+template <bool STATS, int DR, int DC, int DS>
+__global__ void __launch_bounds__(256, 3) k_fft_s_admm256(float2* __restrict__ spec, int Ms, int Mp, int Nn, int TW,
+                                                        SolveArgs sv, const float2* __restrict__ twS, int nNl) {
+  constexpr int S = 256, QN = DR * DC, D = DR * DC * DS, RS = 16 / DS, SL = S / DS;
+  static_assert(QN == 1 || QN == 2 || QN == 4, "class members in the (m, n) plane: 1, 2 or 4 lanes");
+  static_assert(16 % DS == 0, "the s members of a class must share a thread");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  const int GMc = TW / DR;
+  const int rowlen = DC * TW;
+  const int tid = threadIdx.x;
+  const int q = tid % QN, rest = tid / QN;
+  const int gm = rest % GMc, tl = rest / GMc;
+  const int pm = q % DR, pn = q / DR;
+  const int t = gm * DR + pm;  // m-slot of the tile
+  const int a0 = blockIdx.x * TW;
+  const int jl = blockIdx.y;  // LR n frequency of the tile's class row (G = DC rows)
+  const bool cls_ok = a0 + gm * DR < Ms;  // whole classes: Ms and TW are multiples of DR
+  const long long plane = (long long)Nn * Mp;
+  float2* col = spec + (long long)(jl + pn * nNl) * Mp + a0 + t;
+  float2* line = sm + pn * TW + t;
+  float2* tws = sm + S * rowlen;
+  ct_load_twiddles(tws, twS, S);
+
+  float2 v[16];
+  // forward transform, stage 0: 16 loads in flight, radix 16
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = cls_ok ? col[(long long)(tl + 16 * r) * plane] : make_float2(0.f, 0.f);
+  Dft<16, float2, float>::run(v);
+#pragma unroll
+  for (int r = 0; r < 16; ++r) line[(16 * tl + r) * rowlen] = v[r];
+  __syncthreads();
+  // stage 1: twiddles, radix 16; v[r] = frequency tl + 16 r
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    float2 a = line[(tl + 16 * r) * rowlen];
+    if (r > 0) a = cmul(a, tws[tl * r]);
+    v[r] = a;
+  }
+  Dft<16, float2, float>::run(v);
+
+  // per-class solve
+  const int g = cls_ok ? a0 / DR + gm : 0;
+  const int km = g + pm * sv.Ml, kn = jl + pn * sv.Nl;
+  const float* __restrict__ symS = reinterpret_cast<const float*>(sv.symS);
+  const float2* __restrict__ lamS = reinterpret_cast<const float2*>(sv.lamS);
+  const float sMN = __ldg(&reinterpret_cast<const float*>(sv.symM)[km]) +
+                    __ldg(&reinterpret_cast<const float*>(sv.symN)[kn]);
+  float2 lmn = make_float2(0.f, 0.f);
+  if (sv.sep)
+    lmn = cmul(__ldg(&reinterpret_cast<const float2*>(sv.lamM)[km]), __ldg(&reinterpret_cast<const float2*>(sv.lamN)[kn]));
+  const long long bc = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+  const int ncls = GMc * sv.Sl;
+  const float2* __restrict__ lamc = reinterpret_cast<const float2*>(sv.lam) + bc * D * ncls;
+  const float2* __restrict__ yhc = reinterpret_cast<const float2*>(sv.yhat) + bc * ncls;
+  const float alpha = (float)sv.alpha;
+  const float dd = (float)D;
+  const int lane = tid & 31;
+  const int gbase = lane - q;  // first lane of this class's group
+  double acc = 0.0;
+#pragma unroll
+  for (int cr = 0; cr < RS; ++cr) {
+    const int is = tl + 16 * cr;  // LR s frequency of the class
+    const int c = gm + GMc * is;
+    const float2 Yc = cls_ok ? __ldg(&yhc[c]) : make_float2(0.f, 0.f);
+    const bool dc_cls = cls_ok && g == 0 && jl == 0 && is == 0;
+    float2 av[DS], bv[DS];
+    float wv[DS];
+    float best = -1.f;
+    int bidx = D;
+#pragma unroll
+    for (int ps = 0; ps < DS; ++ps) {
+      const int qq = q + QN * ps;
+      const int ks = is + ps * SL;
+      float2 a_ = make_float2(0.f, 0.f);
+      float w = 0.f;
+      if (cls_ok) {
+        a_ = sv.sep ? cmul(lmn, __ldg(&lamS[ks])) : __ldg(&lamc[(long long)qq * ncls + c]);
+        w = (dc_cls && qq == 0) ? 0.f : 1.f / (alpha * (sMN + __ldg(&symS[ks])));
+      }
+      av[ps] = a_;
+      wv[ps] = w;
+      bv[ps] = cmulc(a_, Yc) + v[cr + ps * RS] * alpha;  // B = conj(Lambda) Y + mu F Theta
+      const float key = (dc_cls && qq == 0) ? Lim<float>::big : norm2(a_) * w;
+      if (key > best) { best = key; bidx = qq; }
+    }
+    // the dominant member of the class: largest key, lowest member index on ties
+#pragma unroll
+    for (int o = 1; o < QN; o <<= 1) {
+      const float ok_ = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ok_ > best || (ok_ == best && oi < bidx)) { best = ok_; bidx = oi; }
+    }
+    // Sherman-Morrison sums over the other members
+    float Sp = 0.f;
+    float2 Tp = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int ps = 0; ps < DS; ++ps) {
+      if (q + QN * ps != bidx) {
+        Sp += norm2(av[ps]) * wv[ps];
+        Tp = Tp + cmul(av[ps], bv[ps]) * wv[ps];
+      }
+    }
+#pragma unroll
+    for (int o = 1; o < QN; o <<= 1) {
+      Sp += __shfl_xor_sync(0xffffffffu, Sp, o);
+      Tp.x += __shfl_xor_sync(0xffffffffu, Tp.x, o);
+      Tp.y += __shfl_xor_sync(0xffffffffu, Tp.y, o);
+    }
+    // the lane holding the dominant member forms its value and the ratio
+    const bool owner = (bidx % QN) == q;
+    const int bps = bidx / QN;
+    float2 as = av[0], bs = bv[0];
+    float ws = wv[0];
+#pragma unroll
+    for (int ps = 1; ps < DS; ++ps)
+      if (ps == bps) { as = av[ps]; bs = bv[ps]; ws = wv[ps]; }
+    float2 Xs, ratio;
+    if (dc_cls) {
+      const float inv = 1.f / norm2(as);
+      Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * inv;
+      ratio = cmul(bs, as) * inv;
+    } else {
+      const float iD = 1.f / (dd + Sp + norm2(as) * ws);
+      Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * (ws * iD);
+      ratio = (Tp + cmul(as, bs) * ws) * iD;
+    }
+    if (QN > 1) {
+      const int src = gbase + (bidx % QN);
+      ratio.x = __shfl_sync(0xffffffffu, ratio.x, src);
+      ratio.y = __shfl_sync(0xffffffffu, ratio.y, src);
+    }
+    float2 tsum = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int ps = 0; ps < DS; ++ps) {
+      const bool mine = owner && ps == bps;
+      const float2 X = mine ? Xs : (bv[ps] - cmulc(av[ps], ratio)) * wv[ps];
+      v[cr + ps * RS] = conjc(X);  // conjugated: the inverse runs through the forward engine
+      if (STATS) tsum = tsum + cmul(av[ps], X);
+    }
+    if (STATS) {
+#pragma unroll
+      for (int o = 1; o < QN; o <<= 1) {
+        tsum.x += __shfl_xor_sync(0xffffffffu, tsum.x, o);
+        tsum.y += __shfl_xor_sync(0xffffffffu, tsum.y, o);
+      }
+      if (cls_ok && q == 0) {
+        const float2 R = Yc - tsum * (1.f / (float)D);
+        const double wg = (g == 0 || 2 * g == sv.Ml) ? 1.0 : 2.0;
+        acc += wg * (double)norm2(R);
+      }
+    }
+  }
+  if (STATS) {
+    double* red = reinterpret_cast<double*>(tws + S);
+    acc = warp_sum(acc);
+    const int warp = tid >> 5;
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (warp == 0) {
+      double s_ = (lane < (int)((blockDim.x + 31) / 32)) ? red[lane] : 0.0;
+      s_ = warp_sum(s_);
+      if (lane == 0) sv.partial[bc] = s_;
+    }
+  }
+  // inverse transform, stage 0 from the registers: radix 16
+  Dft<16, float2, float>::run(v);
+  __syncthreads();  // every thread has read its forward stage-1 inputs
+#pragma unroll
+  for (int r = 0; r < 16; ++r) line[(16 * tl + r) * rowlen] = v[r];
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    float2 a = line[(tl + 16 * r) * rowlen];
+    if (r > 0) a = cmul(a, tws[tl * r]);
+    v[r] = a;
+  }
+  Dft<16, float2, float>::run(v);
+  // the store addresses are formed again here rather than kept live (in
+  // registers) from the loads through the whole solve
+  asm volatile("" : "+l"(col));
+  if (cls_ok) {
+#pragma unroll
+    for (int r = 0; r < 16; ++r) col[(long long)(tl + 16 * r) * plane] = conjc(v[r]);
+  }
+}
+
+template <bool STATS, int DR, int DC, int DS>
+static cudaError_t fft_s_admm256(const Plan& p, const Geometry& g, void* spec, const void* tw, const SolveArgs& sv) {
+  const int TW = g.tw_s;
+  size_t smem = (size_t)(256 * TW * DC + 256) * sizeof(float2);
+  if (STATS) smem += 32 * sizeof(double);
+  dim3 grid((g.Ms + TW - 1) / TW, g.N / DC);
+  cudaError_t e;
+  if ((e = allow_smem(k_fft_s_admm256<STATS, DR, DC, DS>, smem)) != cudaSuccess) return e;
+  k_fft_s_admm256<STATS, DR, DC, DS><<<grid, TW * DC * 16, smem, p.stream>>>((float2*)spec, g.Ms, g.Mp, g.N, TW, sv,
+                                                                          (const float2*)tw, g.Nl);
+  return cudaGetLastError();
+}
+
 template <typename T, int EMAX, int MODE, bool STATS, int NC, int DR_ = 0, int DC_ = 0, int DS_ = 0>
 static cudaError_t fft_s_k(const Plan& p, const Geometry& g, void* spec, const void* tw, const SolveArgs& sv) {
   const int tpl = g.S / g.fs.e;
@@ -375,11 +593,14 @@ static cudaError_t fft_s_e(const Plan& p, const Geometry& g, void* spec, const v
       if constexpr (sizeof(T) == 4 && EMAX == 16) {
         if (ct_len<T>(g.S, g.fs) == 256 && g.tw_s * g.g_s * (256 / 16) <= 256) {
           if (g.dr == 2 && g.dc == 2 && g.ds == 2)
-            return stats ? fft_s_k<T, EMAX, S_ADMM, true, 256, 2, 2, 2>(p, g, spec, tw, sv)
-                         : fft_s_k<T, EMAX, S_ADMM, false, 256, 2, 2, 2>(p, g, spec, tw, sv);
+            return stats ? fft_s_admm256<true, 2, 2, 2>(p, g, spec, tw, sv)
+                         : fft_s_admm256<false, 2, 2, 2>(p, g, spec, tw, sv);
           if (g.dr == 1 && g.dc == 1 && g.ds == 4)
-            return stats ? fft_s_k<T, EMAX, S_ADMM, true, 256, 1, 1, 4>(p, g, spec, tw, sv)
-                         : fft_s_k<T, EMAX, S_ADMM, false, 256, 1, 1, 4>(p, g, spec, tw, sv);
+            return stats ? fft_s_admm256<true, 1, 1, 4>(p, g, spec, tw, sv)
+                         : fft_s_admm256<false, 1, 1, 4>(p, g, spec, tw, sv);
+          if (g.dr == 2 && g.dc == 2 && g.ds == 1)
+            return stats ? fft_s_admm256<true, 2, 2, 1>(p, g, spec, tw, sv)
+                         : fft_s_admm256<false, 2, 2, 1>(p, g, spec, tw, sv);
           return stats ? fft_s_k<T, EMAX, S_ADMM, true, 256>(p, g, spec, tw, sv)
                        : fft_s_k<T, EMAX, S_ADMM, false, 256>(p, g, spec, tw, sv);
         }
