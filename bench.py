@@ -46,16 +46,16 @@ UNIT = "voxel·iters/s"
 ALG_BYTES = {"tv": 32, "rfft_m_fwd": 8, "fft_n_fwd": 8, "fft_s": 16, "fft_n_inv": 8, "rfft_m_inv": 8}
 STEP_BYTES = 80
 # DRAM bytes per launch (dram__bytes_read + dram__bytes_write) of each loop
-# kernel from one ncu capture of this workload (profiles/admm_tv_256_kernels_ncu.md),
+# kernel from one ncu capture of this workload (its summary is kept under profiles/),
 # with the kernel's entry of the tile schedule in that capture; valid while the
 # plan runs that entry and the kernel's sources hash to the recorded value
 NCU_TRAFFIC = {
-    "tv": (499.0e6, {"tv_planes": 37}, ('kernels_tv.cu', 'common.cuh'), "bb1ce373cc693a5a"),
-    "rfft_m_fwd": (87.2e6, {"m_fwd_lines": 32}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
-    "fft_n_fwd": (80.2e6, {"n_pass_slots": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
-    "fft_s": (110.7e6, {"s_pass_slots": 6}, ('kernels_fft_s.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "eaa6dabc0f38b13d"),
-    "fft_n_inv": (80.4e6, {"n_pass_slots": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
-    "rfft_m_inv": (90.4e6, {"m_inv_lines": 32}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "e956c0f045557a4a"),
+    "tv": (497.55e6, {"tv_planes": 37}, ('kernels_tv.cu', 'common.cuh'), "6a977b8b3326bd08"),
+    "rfft_m_fwd": (83.57e6, {"m_fwd_lines": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "6f2096cce7b6697b"),
+    "fft_n_fwd": (77.31e6, {"n_pass_slots": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "6f2096cce7b6697b"),
+    "fft_s": (87.11e6, {"s_pass_slots": 8}, ('kernels_fft_s.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "8affab26f1711313"),
+    "fft_n_inv": (77.36e6, {"n_pass_slots": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "6f2096cce7b6697b"),
+    "rfft_m_inv": (85.58e6, {"m_inv_lines": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "6f2096cce7b6697b"),
 }
 
 
@@ -155,6 +155,11 @@ def make_inputs(w, plan, torch):
     return y
 
 
+def _oracle_cores():
+    import oracle as O
+    return int(O.FFT_WORKERS)
+
+
 def cpu_baseline(w, y_host, iters=5):
     """The FP64 oracle as it stands, timed on this host for `iters` ADMM-TV iterations."""
     import oracle as O
@@ -163,9 +168,90 @@ def cpu_baseline(w, y_host, iters=5):
     t = time.perf_counter()
     O.admm_tv(y_host, psf, w.dec, w.lam, w.mu, iters, x0)
     dt = time.perf_counter() - t
-    return {"value": w.voxels * iters / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    return {"value": w.voxels * iters / dt, "unit": UNIT, "cores": _oracle_cores(), "kind": "oracle",
             "sample": f"{iters} ADMM-TV iterations of the same 256^3 workload (Tikhonov start untimed), "
-                      f"{dt:.1f} s; numpy FFT, single thread; host has {os.cpu_count()} cores"}
+                      f"{dt:.1f} s; FFTs threaded over {_oracle_cores()} host cores, the rest single-threaded "
+                      f"numpy; host has {os.cpu_count()} cores"}
+
+
+def _oracle_problem(w, smooth=False):
+    """y for workload w: the seeded phantom through the oracle's forward model,
+    or (smooth=True, for timing only: the oracle's cost does not depend on the
+    values) a seeded smooth field plus noise of the LR shape."""
+    import numpy as np
+    import oracle as O
+    from synth import noise_sigma, normal
+    psf = w.psf()
+    if smooth:
+        m, n, s_ = w.lr_dims
+        return psf, 0.5 + 0.1 * normal(w.seed, 5, m * n * s_).reshape((s_, n, m))
+    clean = O.forward(w.phantom(), psf, w.dec)
+    return psf, clean + noise_sigma(clean, w.snr_db) * w.noise()
+
+
+def _time_oracle_iters(w, psf, y, iters, budget_s):
+    """Tikhonov start (untimed), then up to `iters` ADMM-TV iterations of the
+    oracle, stopping early once `budget_s` seconds have passed; (iterations, s)."""
+    import numpy as np
+    import oracle as O
+    x0 = O.tikhonov(y, psf, w.dec, w.tau, O.nearest_neighbour(y, w.dec))
+    lam = O.otf(psf, x0.shape)
+    x, u, d = x0, O.grad(x0), np.zeros((3,) + x0.shape)
+    t0 = time.perf_counter()
+    k = 0
+    while k < iters:
+        x = O.admm_xstep(y, lam, O.grad_adj(u - d), w.mu, w.dec)
+        g = O.grad(x)
+        u = O.shrink(g + d, w.lam / w.mu)
+        d = d + g - u
+        k += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return k, time.perf_counter() - t0
+
+
+def cpu_baselines_other_configs():
+    """The oracle on the other configurations of the benchmark set: the 32^3
+    FP64 problem in full (Tikhonov + 20 iterations, timed end to end), the
+    512x512x256 anisotropic volume and the ragged batch for a bounded number
+    of iterations, per iteration and extrapolated to the configuration's
+    iteration count."""
+    import oracle as O
+    import synth
+    out = {}
+    w = synth.SMALL_FP64
+    psf, y = _oracle_problem(w)
+    t0 = time.perf_counter()
+    x0 = O.tikhonov(y, psf, w.dec, w.tau, O.nearest_neighbour(y, w.dec))
+    O.admm_tv(y, psf, w.dec, w.lam, w.mu, w.iters, x0)
+    dt = time.perf_counter() - t0
+    out["hr32_d2_fp64"] = {"value": w.voxels * w.iters / dt, "unit": UNIT, "seconds": dt, "iters": w.iters,
+                           "extrapolated": False, "sample": "the whole run: Tikhonov start + 20 iterations"}
+    w = synth.ANISO_512
+    psf, y = _oracle_problem(w, smooth=True)
+    k, dt = _time_oracle_iters(w, psf, y, 5, 45.0)
+    out["hr512x512x256_d114"] = {"value": w.voxels * k / dt, "unit": UNIT, "seconds_per_iter": dt / k, "iters": k,
+                                 "extrapolated_seconds": w.iters * dt / k + 0.0, "extrapolated": True,
+                                 "sample": f"{k} of 200 iterations (Tikhonov start untimed) on a seeded smooth "
+                                           "observation of the workload's shape"}
+    ws = synth.batch_workloads()
+    tot_vox, tot_s, vols = 0, 0.0, 0
+    for wi in ws[:8]:
+        psf, y = _oracle_problem(wi, smooth=True)
+        k, dt = _time_oracle_iters(wi, psf, y, 5, 20.0)
+        tot_vox += wi.voxels * k
+        tot_s += dt
+        vols += 1
+    rate = tot_vox / tot_s
+    all_vox_iters = sum(wi.voxels for wi in ws) * ws[0].iters
+    out["batch64_ragged"] = {"value": rate, "unit": UNIT, "extrapolated": True,
+                             "extrapolated_seconds": all_vox_iters / rate,
+                             "sample": f"5 iterations of each of the first {vols} of the 64 volumes "
+                                       "(seeded smooth observations); rate applied to all 64 x 50 iterations"}
+    for v in out.values():
+        v["cores"] = _oracle_cores()
+        v["kind"] = "oracle"
+    return out
 
 
 def run_reference(args, w, rank):
@@ -201,8 +287,9 @@ def run_reference(args, w, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(w), "step": "one ADMM-TV iteration of the FP64 oracle"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed iterations at 256^3, numpy single thread"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": _oracle_cores(), "kind": "oracle",
+                             "sample": f"{args.steps} timed iterations at 256^3; FFTs threaded over "
+                                       f"{_oracle_cores()} host cores, the rest single-threaded numpy"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -223,7 +310,10 @@ def whole_job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-def run_ours(args, w, rank, world, local_rank):
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
+
+
+def run_ours(args, w, rank, world, local_rank, pool_futs=None):
     import torch
     import torch.distributed as dist
     from paper_2010_15491_gb300.build import build
@@ -287,6 +377,50 @@ def run_ours(args, w, rank, world, local_rank):
            "h2d_bytes_per_step": yh.numel() * yh.element_size(),
            "d2h_bytes_per_step": xh.numel() * xh.element_size()}
 
+    # the same solve with the FP64 objective and residual reductions on
+    # (statistics every 10th and every iteration; fixed iteration count)
+    stats_on = {}
+    for every in (10, 1):
+        for _ in range(2):
+            plan.admm_tv(y, x, w.lam, w.mu, w.iters, tau_init=w.tau, eval_every=every)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.admm_tv(y, x, w.lam, w.mu, w.iters, tau_init=w.tau, eval_every=every)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1e3
+        stats_on[f"eval_every_{every}"] = {"value": w.voxels * w.iters * args.steps / t, "unit": UNIT,
+                                           "ms_per_step": 1e3 * t / args.steps}
+    # cuFFT (through torch.fft, a library comparator only) on the same 256^3
+    # real volume: one R2C and one C2R 3D transform
+    cufft = None
+    if rank == 0:
+        with torch.cuda.stream(stream):
+            xr = torch.randn(plan.hr_shape, device="cuda", dtype=torch.float32)
+            for _ in range(3):
+                X = torch.fft.rfftn(xr)
+                torch.fft.irfftn(X, s=xr.shape)
+            torch.cuda.synchronize()
+            reps = 20
+            ev0.record(stream)
+            for _ in range(reps):
+                X = torch.fft.rfftn(xr)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            r2c = ev0.elapsed_time(ev1) / reps
+            ev0.record(stream)
+            for _ in range(reps):
+                torch.fft.irfftn(X, s=xr.shape)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            c2r = ev0.elapsed_time(ev1) / reps
+            del xr, X
+        cufft = {"r2c_ms": r2c, "c2r_ms": c2r, "pair_ms": r2c + c2r,
+                 "note": "cuFFT through torch.fft.rfftn / irfftn on a 256^3 FP32 volume (natural layout), timed "
+                         "only as a library comparator; the library's five loop passes (kernels_ms_per_iteration) "
+                         "do the same two transforms plus the class solve of eq. 12 in the s pass"}
+
     peak, peak_src = peaks()
     kern = {}
     for k, (kms, n) in prof.items():
@@ -299,7 +433,27 @@ def run_ours(args, w, rank, world, local_rank):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src, "traffic": ncu_traffic(dom, plan.schedule()),
                 "alg_bytes_per_launch": ALG_BYTES[dom] * w.voxels,
-                "step_frac": value / world * STEP_BYTES / (peak * 1e9)}
+                "step_frac": value / world * STEP_BYTES / (peak * 1e9),
+                "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
+                "step_frac_of_nominal": value / world * STEP_BYTES / (NOMINAL_HBM_GBS * 1e9),
+                "nominal_peak": NOMINAL_HBM_GBS}
+    if cufft is not None:
+        cufft["ours_fft_passes_ms"] = sum(kern[k]["ms_per_launch"] for k in
+                                          ("rfft_m_fwd", "fft_n_fwd", "fft_s", "fft_n_inv", "rfft_m_inv")
+                                          if k in kern and kern[k]["ms_per_launch"])
+    warm = None
+    if rank == 0 and pool_futs is not None:
+        import numpy as np
+        from paper_2010_15491_gb300 import warmstart as W
+        pool, futs = pool_futs
+        if os.path.exists(WEIGHTS):
+            net = sr3d.UNet()
+            net.set_params(np.load(WEIGHTS))
+            ys = [W.observe(plan, torch.from_numpy(f.result()).cuda(), w.snr_db, sd) for sd, f in zip(WARM_SEEDS, futs)]
+            warm = warm_cold(plan, net, ys, w)
+            net.close()
+            del ys
+        pool.shutdown()
     if rank != 0:
         plan.close()
         return
@@ -310,9 +464,13 @@ def run_ours(args, w, rank, world, local_rank):
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "working set ~0.65 GB > L2; no flush", "schedule": plan.schedule()},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-            "kernels": kern}
+            "kernels": kern, "stats_on": stats_on, "cufft": cufft}
+    if warm is not None:
+        line["warm_start"] = {"metric": "wall-clock to relative primal and dual residuals < 1e-4 at 256^3 "
+                                        "(held-out phantoms 90000-90004)", **warm}
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, y.double().cpu().numpy())
+        line["cpu_baseline"]["other_configs"] = cpu_baselines_other_configs()
     print(json.dumps(line), flush=True)
     plan.close()
 
@@ -543,18 +701,87 @@ UNET_MACS = (27 * (1 * 16 + 16 * 16 + 48 * 16 + 16 * 16) + 27 * (16 * 32 + 32 * 
              + 27 * (32 * 64 + 64 * 64) / 64 + 16)
 
 
-def run_warmstart(args, rank, world, local_rank):
+def warm_cold(plan, net, ys, w, net2=None, ablation=False):
+    """Wall-clock to relative primal and dual residuals below 1e-4 (checked
+    every 10 iterations) for each observation in ys: cold (the paper's start:
+    Tikhonov, d0 = 0) against warm (Tikhonov, U-Net, consistent dual), host
+    clock around synchronous calls.  Optionally the d0 = 0 ablation and a
+    second network."""
+    import torch
+    from paper_2010_15491_gb300 import warmstart as W
+    tol, every, cap = 1e-4, 10, 5000
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        return out, 1e3 * (time.perf_counter() - t0)
+
+    # loads every kernel and graph once
+    W.solve(plan, ys[0], w.lam, w.mu, w.tau, tol, 2 * every, eval_every=every)
+    W.solve(plan, ys[0], w.lam, w.mu, w.tau, tol, 2 * every, eval_every=every, net=net)
+    if net2 is not None:
+        W.solve(plan, ys[0], w.lam, w.mu, w.tau, tol, 2 * every, eval_every=every, net=net2)
+    res = {"cold": [], "warm": [], "warm_d0": [], "warm2": []}
+    for y in ys:
+        (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every))
+        res["cold"].append((ms, st["iters"], st["converged"]))
+        (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every, net=net))
+        res["warm"].append((ms, st["iters"], st["converged"]))
+        if ablation:
+            (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every, net=net,
+                                                dual=False))
+            res["warm_d0"].append((ms, st["iters"], st["converged"]))
+        if net2 is not None:
+            (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every,
+                                                net=net2))
+            res["warm2"].append((ms, st["iters"], st["converged"]))
+    # parts of the warm start, on the first volume
+    _, t_tik = timed(lambda: plan.tikhonov(ys[0], w.tau, xbar="nearest"))
+    xt = plan.tikhonov(ys[0], w.tau, xbar="nearest")
+    for _ in range(2):
+        net.forward(xt)
+    _, t_net = timed(lambda: net.forward(xt))
+    _, t_dual = timed(lambda: plan.dual_init(xt, w.lam, w.mu))
+    mean = lambda v: float(sum(v) / len(v))  # noqa: E731
+    out = {"warm_ms": mean([c[0] for c in res["warm"]]), "cold_ms": mean([c[0] for c in res["cold"]]),
+           "warm_iters": [c[1] for c in res["warm"]], "cold_iters": [c[1] for c in res["cold"]],
+           "converged": all(c[2] for v in res.values() for c in v),
+           "warm_parts_ms": {"tikhonov": t_tik, "unet": t_net, "dual_init": t_dual},
+           "tol": tol, "check_every": every, "volumes": len(ys)}
+    out["warm_over_cold"] = out["warm_ms"] / out["cold_ms"]
+    out["unet_share_of_warm"] = t_net / out["warm_ms"]
+    if ablation:
+        out["ablation_warm_d0_zero"] = {"ms": mean([c[0] for c in res["warm_d0"]]),
+                                        "iters": [c[1] for c in res["warm_d0"]]}
+    if net2 is not None:
+        out["warm_targets_1000"] = {"ms": mean([c[0] for c in res["warm2"]]), "iters": [c[1] for c in res["warm2"]]}
+    out["unet_tflops"] = 2 * UNET_MACS * w.voxels / (t_net * 1e-3) / 1e12
+    return out
+
+
+WARM_SEEDS = [90000 + j for j in range(5)]  # held-out phantoms (never used for training)
+
+
+def start_phantoms(w, seeds):
+    """Phantoms of the held-out seeds on host worker processes (spawned before any GPU call)."""
+    from paper_2010_15491_gb300 import warmstart as W
+    pool = W.phantom_pool(len(seeds))
+    return pool, [pool.submit(W._phantom, (w.dims[0], w.n_ellipsoids, sd, w.field)) for sd in seeds]
+
+
+def run_warmstart(args, rank, world, local_rank, pool_futs=None):
     """--workload warmstart: wall-clock to relative primal and dual residuals
     below 1e-4 at 256^3 on five held-out phantoms (seeds 90000 + j), cold
     (Tikhonov start, d0 = 0) against warm (Tikhonov, U-Net, consistent dual),
-    both checked every 10 iterations.  Warm time includes the Tikhonov solve,
+    both checked every 10 iterations, with the d0 = 0 ablation and the network
+    trained on 1000-iteration targets.  Warm time includes the Tikhonov solve,
     the U-Net inference and the dual initialisation."""
     import numpy as np
     from paper_2010_15491_gb300 import warmstart as W
     from synth import HEADLINE_256 as w
-    n_vol = 5
-    pool = W.phantom_pool(n_vol)  # host workers start before the first GPU call
-    futs = [pool.submit(W._phantom, (w.dims[0], w.n_ellipsoids, 90000 + j, w.field)) for j in range(n_vol)]
+    pool, futs = pool_futs if pool_futs else start_phantoms(w, WARM_SEEDS)
     import torch
     from paper_2010_15491_gb300.build import build
     import paper_2010_15491_gb300 as sr3d
@@ -572,67 +799,25 @@ def run_warmstart(args, rank, world, local_rank):
     if os.path.exists(WEIGHTS_REF1000):
         net2 = sr3d.UNet()
         net2.set_params(np.load(WEIGHTS_REF1000))
-    ys = [W.observe(plan, torch.from_numpy(f.result()).cuda(), w.snr_db, 90000 + j) for j, f in enumerate(futs)]
+    ys = [W.observe(plan, torch.from_numpy(f.result()).cuda(), w.snr_db, sd) for sd, f in zip(WARM_SEEDS, futs)]
     pool.shutdown()
-    tol, every, cap = 1e-4, 10, 5000
-
-    def timed(fn):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        out = fn()
-        torch.cuda.synchronize()
-        return out, 1e3 * (time.perf_counter() - t0)
-
-    for _ in range(max(args.warmup, 1)):  # loads every kernel and graph once
-        W.solve(plan, ys[0], w.lam, w.mu, w.tau, tol, 2 * every, eval_every=every)
-        W.solve(plan, ys[0], w.lam, w.mu, w.tau, tol, 2 * every, eval_every=every, net=net)
-    cold, warm, warm_d0, warm2 = [], [], [], []
-    if net2 is not None:
-        W.solve(plan, ys[0], w.lam, w.mu, w.tau, tol, 2 * every, eval_every=every, net=net2)
     with ClockSampler(torch.cuda.current_device()) as clk:
-        for y in ys:
-            (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every))
-            cold.append((ms, st["iters"], st["converged"]))
-            (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every, net=net))
-            warm.append((ms, st["iters"], st["converged"]))
-            (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every, net=net,
-                                                dual=False))
-            warm_d0.append((ms, st["iters"], st["converged"]))
-            if net2 is not None:
-                (_, st), ms = timed(lambda: W.solve(plan, y, w.lam, w.mu, w.tau, tol, cap, eval_every=every,
-                                                    net=net2))
-                warm2.append((ms, st["iters"], st["converged"]))
-    # parts of the warm start, on the first volume
-    _, t_tik = timed(lambda: plan.tikhonov(ys[0], w.tau, xbar="nearest"))
-    xt = plan.tikhonov(ys[0], w.tau, xbar="nearest")
-    for _ in range(2):
-        net.forward(xt)
-    _, t_net = timed(lambda: net.forward(xt))
-    _, t_dual = timed(lambda: plan.dual_init(xt, w.lam, w.mu))
+        r = warm_cold(plan, net, ys, w, net2=net2, ablation=True)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     bf16 = None
     if os.path.exists(peaks_path):
         with open(peaks_path) as f:
             bf16 = json.load(f).get("bf16_tflops")
-    unet_tflops = 2 * UNET_MACS * w.voxels / (t_net * 1e-3) / 1e12
-    mean = lambda v: float(sum(v) / len(v))  # noqa: E731
     if rank == 0:
         print(json.dumps({
-            "metric": "ADMM-TV wall-clock to relative residuals < 1e-4 at 256³, learned warm start", "value":
-            mean([c[0] for c in warm]), "unit": "ms", "n_gpus": 1, "steps": n_vol, "warmup": max(args.warmup, 1),
+            "metric": "ADMM-TV wall-clock to relative residuals < 1e-4 at 256³, learned warm start",
+            "value": r["warm_ms"], "unit": "ms", "n_gpus": 1, "steps": len(ys), "warmup": 1,
             "higher_is_better": False, "vs_baseline": None, "dtype": "f32 (U-Net bf16)", "data": "synthetic",
             "config": {"workload": "hr256_d2_fp32 recipe, held-out phantom seeds 90000-90004; tol 1e-4, residuals "
                                    "checked every 10 iterations", "timing": "host clock around synchronous calls"},
-            "cold_ms": mean([c[0] for c in cold]), "cold_iters": [c[1] for c in cold],
-            "warm_iters": [c[1] for c in warm], "warm_over_cold": mean([c[0] for c in warm]) / mean([c[0] for c in cold]),
-            "ablation_warm_d0_zero": {"ms": mean([c[0] for c in warm_d0]), "iters": [c[1] for c in warm_d0]},
-            "warm_targets_1000": ({"ms": mean([c[0] for c in warm2]), "iters": [c[1] for c in warm2]}
-                                  if warm2 else None),
-            "converged": all(c[2] for c in cold + warm + warm_d0 + warm2),
-            "warm_parts_ms": {"tikhonov": t_tik, "unet": t_net, "dual_init": t_dual},
-            "unet_roofline": {"bound": "tensor", "achieved": unet_tflops, "peak": bf16, "unit": "TFLOP/s",
-                              "frac": unet_tflops / bf16 if bf16 else None,
-                              "flops_per_voxel": 2 * UNET_MACS},
+            **{k: v for k, v in r.items() if k != "warm_ms"},
+            "unet_roofline": {"bound": "tensor", "achieved": r["unet_tflops"], "peak": bf16, "unit": "TFLOP/s",
+                              "frac": r["unet_tflops"] / bf16 if bf16 else None, "flops_per_voxel": 2 * UNET_MACS},
             "clocks": clk.summary()}), flush=True)
     plan.close()
     net.close()
@@ -647,6 +832,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-warm-start", action="store_true",
+                    help="headline: skip the warm- against cold-start measurement")
     ap.add_argument("--schedule", default="",
                     help="headline: fixed tile schedule n_slots,s_slots,tv_planes[,m_fwd_lines,m_inv_lines] "
                          "instead of the autotuner")
@@ -662,6 +849,11 @@ def main():
     if args.impl == "reference":
         run_reference(args, w, rank)
         return
+    pool_futs = None
+    if rank == 0 and ((args.workload == "headline" and not args.no_warm_start) or args.workload == "warmstart"):
+        # held-out phantoms for the warm-start measurement, on host processes
+        # spawned before the first GPU call
+        pool_futs = start_phantoms(w, WARM_SEEDS)
     if world > 1:
         import torch
         import torch.distributed as dist
@@ -671,7 +863,7 @@ def main():
         run_batch(args, rank, world, local_rank)
     elif args.workload == "warmstart":
         if rank == 0:
-            run_warmstart(args, rank, world, local_rank)
+            run_warmstart(args, rank, world, local_rank, pool_futs)
     elif args.workload == "regularisers":
         if rank == 0:
             run_regularisers(args, rank, world, local_rank)
@@ -682,7 +874,7 @@ def main():
         if rank == 0:
             run_unet(args, rank, world, local_rank)
     else:
-        run_ours(args, w, rank, world, local_rank)
+        run_ours(args, w, rank, world, local_rank, pool_futs)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
