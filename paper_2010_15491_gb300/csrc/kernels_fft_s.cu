@@ -358,13 +358,21 @@ __global__ void __launch_bounds__(NC > 0 ? 256 : 512, NC > 0 ? 3 : 1) k_fft_s(cp
 // stage.  The class's DR x DC members in the (m, n) plane sit in QN = DR * DC
 // adjacent lanes of one warp (lane layout q + QN * (gm + GMc * tl), q = pm +
 // DR * pn), and the solve exchanges only per-class scalars by warp shuffles
-// (the dominant member, the Sherman-Morrison sums and the ratio).  Each
-// element crosses shared memory four times (one round trip per transform)
-// instead of going through a shared tile for the solve.  Same arithmetic as
-// solve_tile: B = conj(Lambda) Y + mu F Theta, the dominant member
-// (largest |Lambda|^2 w, ties to the lowest member index) kept out of the
-// sums, the zero-frequency class solved exactly.
+// (the Sherman-Morrison sums of the other lanes' members, as the butterfly
+// delivers them).  Each element crosses shared memory four times (one round
+// trip per transform) instead of going through a shared tile for the solve.
+// Same system as solve_tile (B = conj(Lambda) Y + mu F Theta, the
+// zero-frequency class solved exactly), but every member is formed with its
+// own term kept out of the sums, so no member needs a dominant-member search.
 // ---------------------------------------------------------------------------
+// 1/x: the hardware approximation refined by one Newton-Raphson step
+// r <- r (2 - x r) (a few units in the last place; x normal and positive here)
+__device__ __forceinline__ float rcp_nr(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r * fmaf(-x, r, 2.0f);
+}
+
 template <bool STATS, int DR, int DC, int DS>
 __global__ void __launch_bounds__(256, 3) k_fft_s_admm256(float2* __restrict__ spec, int Ms, int Mp, int Nn, int TW,
                                                         SolveArgs sv, const float2* __restrict__ twS, int nNl) {
@@ -431,77 +439,80 @@ __global__ void __launch_bounds__(256, 3) k_fft_s_admm256(float2* __restrict__ s
     const int c = gm + GMc * is;
     const float2 Yc = cls_ok ? __ldg(&yhc[c]) : make_float2(0.f, 0.f);
     const bool dc_cls = cls_ok && g == 0 && jl == 0 && is == 0;
-    float2 av[DS], bv[DS];
-    float wv[DS];
-    float best = -1.f;
-    int bidx = D;
+    // members: Lambda a, mu s (den0), w = 1 / (mu s), B, key |a|^2 w, a B w
+    float2 av[DS], bv[DS], tv[DS];
+    float sv_[DS], wv[DS], kv[DS];
+    float Sown = 0.f;
+    float2 Town = make_float2(0.f, 0.f);
 #pragma unroll
     for (int ps = 0; ps < DS; ++ps) {
       const int qq = q + QN * ps;
       const int ks = is + ps * SL;
       float2 a_ = make_float2(0.f, 0.f);
-      float w = 0.f;
+      float mus = 1.f, w = 0.f;
       if (cls_ok) {
         a_ = sv.sep ? cmul(lmn, __ldg(&lamS[ks])) : __ldg(&lamc[(long long)qq * ncls + c]);
-        w = (dc_cls && qq == 0) ? 0.f : 1.f / (alpha * (sMN + __ldg(&symS[ks])));
+        mus = alpha * (sMN + __ldg(&symS[ks]));
+        w = (dc_cls && qq == 0) ? 0.f : rcp_nr(mus);  // Gamma / mu; singular at the zero frequency
       }
       av[ps] = a_;
+      sv_[ps] = mus;
       wv[ps] = w;
       bv[ps] = cmulc(a_, Yc) + v[cr + ps * RS] * alpha;  // B = conj(Lambda) Y + mu F Theta
-      const float key = (dc_cls && qq == 0) ? Lim<float>::big : norm2(a_) * w;
-      if (key > best) { best = key; bidx = qq; }
+      kv[ps] = norm2(a_) * w;
+      tv[ps] = cmul(a_, bv[ps]) * w;
+      Sown += kv[ps];
+      Town = Town + tv[ps];
     }
-    // the dominant member of the class: largest key, lowest member index on ties
-#pragma unroll
-    for (int o = 1; o < QN; o <<= 1) {
-      const float ok_ = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-      if (ok_ > best || (ok_ == best && oi < bidx)) { best = ok_; bidx = oi; }
-    }
-    // Sherman-Morrison sums over the other members
-    float Sp = 0.f;
-    float2 Tp = make_float2(0.f, 0.f);
-#pragma unroll
-    for (int ps = 0; ps < DS; ++ps) {
-      if (q + QN * ps != bidx) {
-        Sp += norm2(av[ps]) * wv[ps];
-        Tp = Tp + cmul(av[ps], bv[ps]) * wv[ps];
+    // sums over the members held by the other lanes of the class, without
+    // subtraction: the butterfly's received values are exactly those sums
+    float So = 0.f;
+    float2 To = make_float2(0.f, 0.f);
+    if (QN > 1) {
+      So = __shfl_xor_sync(0xffffffffu, Sown, 1);
+      To.x = __shfl_xor_sync(0xffffffffu, Town.x, 1);
+      To.y = __shfl_xor_sync(0xffffffffu, Town.y, 1);
+      if (QN > 2) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, Sown + So, 2);
+        const float t2x = __shfl_xor_sync(0xffffffffu, Town.x + To.x, 2);
+        const float t2y = __shfl_xor_sync(0xffffffffu, Town.y + To.y, 2);
+        So += s2;
+        To.x += t2x;
+        To.y += t2y;
       }
     }
-#pragma unroll
-    for (int o = 1; o < QN; o <<= 1) {
-      Sp += __shfl_xor_sync(0xffffffffu, Sp, o);
-      Tp.x += __shfl_xor_sync(0xffffffffu, Tp.x, o);
-      Tp.y += __shfl_xor_sync(0xffffffffu, Tp.y, o);
-    }
-    // the lane holding the dominant member forms its value and the ratio
-    const bool owner = (bidx % QN) == q;
-    const int bps = bidx / QN;
-    float2 as = av[0], bs = bv[0];
-    float ws = wv[0];
-#pragma unroll
-    for (int ps = 1; ps < DS; ++ps)
-      if (ps == bps) { as = av[ps]; bs = bv[ps]; ws = wv[ps]; }
-    float2 Xs, ratio;
-    if (dc_cls) {
-      const float inv = 1.f / norm2(as);
-      Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * inv;
-      ratio = cmul(bs, as) * inv;
-    } else {
-      const float iD = 1.f / (dd + Sp + norm2(as) * ws);
-      Xs = (bs * (dd + Sp) - cmulc(as, Tp)) * (ws * iD);
-      ratio = (Tp + cmul(as, bs) * ws) * iD;
-    }
-    if (QN > 1) {
-      const int src = gbase + (bidx % QN);
-      ratio.x = __shfl_sync(0xffffffffu, ratio.x, src);
-      ratio.y = __shfl_sync(0xffffffffu, ratio.y, src);
+    // Each member by Sherman-Morrison with itself kept out of the sums (no
+    // cancellation for any member):
+    //   X_p = (B_p (d + S_-p) - conj(Lambda_p) T_-p) / (mu s_p (d + S_-p) + |Lambda_p|^2).
+    // The zero-frequency class (Gamma singular at its member 0; one class in
+    // the volume) is solved exactly from member 0; its warp takes that branch.
+    float2 ratio0 = make_float2(0.f, 0.f);
+    const bool dc_warp = __any_sync(0xffffffffu, dc_cls);
+    if (dc_warp) {
+      float2 r = make_float2(0.f, 0.f);
+      if (dc_cls && q == 0) r = cmul(bv[0], av[0]) * (1.f / norm2(av[0]));  // B_0 / conj(Lambda_0)
+      if (QN > 1) {
+        r.x = __shfl_sync(0xffffffffu, r.x, gbase);
+        r.y = __shfl_sync(0xffffffffu, r.y, gbase);
+      }
+      ratio0 = r;
     }
     float2 tsum = make_float2(0.f, 0.f);
 #pragma unroll
     for (int ps = 0; ps < DS; ++ps) {
-      const bool mine = owner && ps == bps;
-      const float2 X = mine ? Xs : (bv[ps] - cmulc(av[ps], ratio)) * wv[ps];
+      float Sm = So;
+      float2 Tm = To;
+#pragma unroll
+      for (int o = 0; o < DS; ++o)
+        if (o != ps) {
+          Sm += kv[o];
+          Tm = Tm + tv[o];
+        }
+      float2 X = (bv[ps] * (dd + Sm) - cmulc(av[ps], Tm)) * rcp_nr(sv_[ps] * (dd + Sm) + norm2(av[ps]));
+      if (dc_warp && dc_cls) {
+        X = (q == 0 && ps == 0) ? (bv[0] * (dd + Sm) - cmulc(av[0], Tm)) * (1.f / norm2(av[0]))
+                                : (bv[ps] - cmulc(av[ps], ratio0)) * wv[ps];
+      }
       v[cr + ps * RS] = conjc(X);  // conjugated: the inverse runs through the forward engine
       if (STATS) tsum = tsum + cmul(av[ps], X);
     }
