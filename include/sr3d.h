@@ -399,6 +399,14 @@ int sr3d_tikhonov_grad(sr3d_plan_t plan, const void* y_dev, double tau, void* x_
 int sr3d_tikhonov_cg(sr3d_plan_t plan, const void* y_dev, const void* xbar_dev, double tau, double tol,
                      int max_iters, void* x_dev, int* iters, double* relres);
 
+/* The sums of the Gaussian PSF fit (Sec. IV estimates its PSF as a 3D
+ * Gaussian against an HR reference): with yh = D H x_dev (the plan's PSF) and
+ * y_dev an LR observation, moments[0..4] (host) receive, accumulated in FP64,
+ * sum yh, sum yh^2, sum y, sum y^2 and sum yh*y -- everything the closed-form
+ * gain a and offset b of min_{a,b} ||y - a yh - b||^2 and its residual need.
+ * Errors: INVALID_ARG (NULL arguments), OOM, CUDA. */
+int sr3d_psf_fit_moments(sr3d_plan_t plan, const void* x_dev, const void* y_dev, double moments[5]);
+
 /* Separable-PSF fast path.  When the PSF is an outer product of three 1-D
  * factors (a Gaussian, for instance, as in the experiments of Sec. IV), the
  * eigenvalues of eq. 2 factor as Lambda(k_m, k_n, k_s) = L_m(k_m) L_n(k_n)

@@ -36,7 +36,7 @@ EXPORTED = [
     "sr3d_separable", "sr3d_set_tv", "sr3d_tikhonov_grad", "sr3d_tikhonov_cg", "sr3d_set_psf",
     "sr3d_dual_init", "sr3d_unet_param_count", "sr3d_unet_create", "sr3d_unet_destroy", "sr3d_unet_set_params",
     "sr3d_unet_get_params", "sr3d_unet_forward", "sr3d_unet_train_step", "sr3d_unet_read", "sr3d_unet_set_path",
-    "sr3d_set_plan_memory_limit", "sr3d_unet_wait_selftest",
+    "sr3d_set_plan_memory_limit", "sr3d_unet_wait_selftest", "sr3d_psf_fit_moments",
 ]
 KINDS = ["tv", "rfft_m_fwd", "fft_n_fwd", "fft_s", "fft_n_inv", "rfft_m_inv", "other", "setup"]
 
@@ -113,6 +113,7 @@ def load() -> ctypes.CDLL:
         "sr3d_unet_set_path": (i, [vp, i]),
         "sr3d_set_plan_memory_limit": (i, [ctypes.c_longlong]),
         "sr3d_unet_wait_selftest": (i, [vp, ctypes.c_longlong]),
+        "sr3d_psf_fit_moments": (i, [vp, vp, vp, ctypes.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -305,6 +306,12 @@ class Plan:
                                       ctypes.byref(st) if st is not None else None)
         _check(rc, allow=(-9,))
         return self._stats_dict(st, hist, rc)
+
+    def psf_fit_moments(self, x, y):
+        """(sum yh, sum yh^2, sum y, sum y^2, sum yh y) in FP64 with yh = D H x (sr3d_psf_fit_moments)."""
+        m = (ctypes.c_double * 5)()
+        _check(load().sr3d_psf_fit_moments(self._h, self._hr(x), self._lr(y), m))
+        return tuple(m)
 
     def get_otf(self):
         """Lambda in natural half-spectrum layout, complex tensor (s, n, m/2+1)."""

@@ -193,7 +193,7 @@ static void free_plan(Plan& p) {
                   p.yhat_solve, p.yhat, p.spec,
                   p.theta, p.dbuf[0], p.dbuf[1], p.psi, p.xh, p.yh, p.partial, p.partial_s, p.result, p.hist,
                   p.lamM1, p.lamN1, p.lamS1, p.cg_buf[0], p.cg_buf[1], p.cg_buf[2], p.cg_buf[3],
-                  p.cg_partial, p.cg_scal};
+                  p.cg_partial, p.cg_scal, p.fit_lr, p.fit_partial};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p.iter_graph) cudaGraphExecDestroy(p.iter_graph);
@@ -878,6 +878,22 @@ int sr3d_forward(sr3d_plan_t plan, const void* x, void* y) {
   LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.lr, p.yhat, p.twSl, S_INV, false, nullptr));
   LAUNCH(SR3D_K_FFTN_INV, launch_fft_n(p, p.lr, p.yhat, p.twNl, true));
   LAUNCH(SR3D_K_RFFT_INV, launch_rfft_m_inv(p, p.lr, p.yhat, y, p.twMl, 1.0 / (double)p.lr.V()));
+  return sync_plan(p);
+}
+
+int sr3d_psf_fit_moments(sr3d_plan_t plan, const void* x, const void* y, double moments[5]) {
+  if (!plan || !x || !y || !moments) return fail(SR3D_ERR_INVALID_ARG, "NULL argument");
+  Plan& p = plan->p;
+  if (!p.fit_lr) TRY(dmalloc(p, &p.fit_lr, (size_t)p.lr.V() * p.esz));
+  if (!p.fit_partial) TRY(dmalloc(p, (void**)&p.fit_partial, (size_t)(5 * CG_BLOCKS + 5) * sizeof(double)));
+  TRY(hr_forward_partial(p, x));
+  SolveArgs sv = solve_args(p, 0, 1.0);
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, p.spec, p.twS, S_FOLD, false, &sv));
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.lr, p.yhat, p.twSl, S_INV, false, nullptr));
+  LAUNCH(SR3D_K_FFTN_INV, launch_fft_n(p, p.lr, p.yhat, p.twNl, true));
+  LAUNCH(SR3D_K_RFFT_INV, launch_rfft_m_inv(p, p.lr, p.yhat, p.fit_lr, p.twMl, 1.0 / (double)p.lr.V()));
+  LAUNCH(SR3D_K_OTHER, launch_fit_moments(p, p.fit_lr, y, p.fit_partial, p.fit_partial + 5 * CG_BLOCKS));
+  CK(cudaMemcpyAsync(moments, p.fit_partial + 5 * CG_BLOCKS, 5 * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
   return sync_plan(p);
 }
 

@@ -89,6 +89,8 @@ struct Plan {
   void* dbuf[2] = {nullptr, nullptr};  // ADMM dual, 3 V each
   void* psi = nullptr;                  // L^T u of the previous iteration
   void* xh = nullptr; void* yh = nullptr;  // staging for host-buffer calls
+  void* fit_lr = nullptr;        // DHx of the PSF fit (LR real)
+  double* fit_partial = nullptr; // its five FP64 sums: per-CTA partials, then the totals
   double* partial = nullptr;  // TV-kernel partial sums
   double* partial_s = nullptr;  // s-pass partial sums
   double* result = nullptr;   // finalize output (16 doubles)
@@ -172,6 +174,8 @@ cudaError_t launch_cg_ap(const Plan& p, void* w_ap, const void* pv, double tau);
 cudaError_t launch_cg_update(const Plan& p, void* x, void* r, const void* pv, const void* ap);
 cudaError_t launch_cg_dir(const Plan& p, const void* r, void* pv);
 cudaError_t launch_cg_reduce(const Plan& p, int slot, int copy_from, int copy_to);
+// partial: 5 * CG_BLOCKS doubles; out: 5 doubles (device)
+cudaError_t launch_fit_moments(const Plan& p, const void* yh, const void* y, double* partial, double* out);
 // KKT-consistent initial dual from x (unet.cu)
 cudaError_t launch_dual_init(const Plan& p, const void* x, double thr, void* d);
 // sets the calling thread's last-error text (api.cu) and returns code

@@ -141,7 +141,62 @@ __global__ void k_cg_reduce(const double* __restrict__ partial, double* __restri
   }
 }
 
+// The five sums of the Gaussian PSF fit's gain/offset least squares:
+// partial[k * gridDim.x + block] for k = 0..4 of sum yh, sum yh^2, sum y,
+// sum y^2, sum yh y (FP64 accumulation).
+template <typename T>
+__global__ void k_fit_moments(const T* __restrict__ yh, const T* __restrict__ y, long long n,
+                              double* __restrict__ partial) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0, a4 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double h = (double)yh[i], v = (double)y[i];
+    a0 += h;
+    a1 += h * h;
+    a2 += v;
+    a3 += v * v;
+    a4 += h * v;
+  }
+  cg_block_sum(a0, partial);
+  __syncthreads();
+  cg_block_sum(a1, partial + gridDim.x);
+  __syncthreads();
+  cg_block_sum(a2, partial + 2 * gridDim.x);
+  __syncthreads();
+  cg_block_sum(a3, partial + 3 * gridDim.x);
+  __syncthreads();
+  cg_block_sum(a4, partial + 4 * gridDim.x);
+}
+
+// out[k] = sum of row k of partial (nb entries each, fixed order), k < 5
+__global__ void k_fit_moments_final(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+  __shared__ double red[CG_THREADS];
+  for (int k = 0; k < 5; ++k) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nb; i += CG_THREADS) acc += partial[k * nb + i];
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int st = CG_THREADS / 2; st > 0; st >>= 1) {
+      if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) out[k] = red[0];
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_fit_moments(const Plan& p, const void* yh, const void* y, double* partial, double* out) {
+  const long long n = p.lr.V();
+  if (p.dtype)
+    k_fit_moments<double><<<CG_BLOCKS, CG_THREADS, 0, p.stream>>>((const double*)yh, (const double*)y, n, partial);
+  else
+    k_fit_moments<float><<<CG_BLOCKS, CG_THREADS, 0, p.stream>>>((const float*)yh, (const float*)y, n, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_fit_moments_final<<<1, CG_THREADS, 0, p.stream>>>(partial, CG_BLOCKS, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_zero_fill(const Plan& p, const void* y, void* z) {
   const Geometry& g = p.hr;

@@ -13,7 +13,8 @@ the decimation of the plan, and a gain a and offset b (the two scanners'
 intensity scales differ) solved in closed form for each sigma.  sigma is
 searched by cyclic golden-section line searches over log sigma, one axis at a
 time.  Each objective evaluation replaces the plan's PSF (sr3d_set_psf) and
-runs the forward model D H x (sr3d_forward) on the GPU.
+runs the forward model D H x and the sums of the gain/offset least squares
+(sr3d_psf_fit_moments) on the GPU.
 """
 from __future__ import annotations
 
@@ -41,13 +42,12 @@ def support(sigma_max: Sequence[float], dims: Sequence[int]) -> tuple:
 
 
 def objective(plan, x_ref, y, sigma, size):
-    """min over (a, b) of ||y - a D H_sigma x_ref - b||^2 and the minimising (a, b)."""
+    """min over (a, b) of ||y - a D H_sigma x_ref - b||^2 and the minimising (a, b).
+    The forward model and the five FP64 sums run in the library
+    (sr3d_set_psf, sr3d_psf_fit_moments); only the 2x2 solve is here."""
     plan.set_psf(gaussian_psf(sigma, size))
-    yh = plan.forward(x_ref).double()
-    yd = y.double()
-    n = yd.numel()
-    s1, s2 = float(yh.sum()), float((yh * yh).sum())
-    t1, t2, c = float(yd.sum()), float((yd * yd).sum()), float((yh * yd).sum())
+    s1, s2, t1, t2, c = plan.psf_fit_moments(x_ref, y)
+    n = int(np.prod(plan.lr_shape))
     det = n * s2 - s1 * s1
     if det <= 0:
         return float("inf"), 1.0, 0.0

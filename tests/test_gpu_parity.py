@@ -453,6 +453,21 @@ def test_set_psf_equals_a_fresh_plan(lib):
     plan.close()
 
 
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-12), ("f32", 1e-6)])
+def test_psf_fit_moments_equal_the_sums_of_the_oracle_forward_model(lib, dtype, tol):
+    """sr3d_psf_fit_moments: the five FP64 sums of the gain/offset least
+    squares, with yh = DHx formed in the library, against the oracle's DHx."""
+    dims, dec = (64, 32, 16), (2, 2, 2)
+    psf, xt, y = make_problem(dims, dec, seed=114, asym=True)
+    plan = lib.Plan(dims, dec, psf, dtype)
+    got = np.array(plan.psf_fit_moments(T(xt, dtype), T(y, dtype)))
+    yv = H(T(y, dtype))  # the observation as the GPU holds it
+    yh = O.forward(xt if dtype == "f64" else H(T(xt, dtype)), psf, dec)
+    ref = np.array([yh.sum(), (yh * yh).sum(), yv.sum(), (yv * yv).sum(), (yh * yv).sum()])
+    assert np.allclose(got, ref, rtol=tol, atol=tol * np.abs(ref).max()), (got, ref)
+    plan.close()
+
+
 def test_gaussian_psf_fit(lib):
     """The fit's objective equals the oracle's at the same sigma, and on
     noise-free data made with a known Gaussian, gain and offset it recovers
