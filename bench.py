@@ -465,6 +465,8 @@ def run_ours(args, w, rank, world, local_rank, pool_futs=None):
                        "l2": "working set ~0.65 GB > L2; no flush", "schedule": plan.schedule()},
             "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "kernels": kern, "stats_on": stats_on, "cufft": cufft}
+    if world == 1 and not args.no_other_configs:
+        line["other_configs"] = gpu_other_configs(sr3d, torch)
     if warm is not None:
         line["warm_start"] = {"metric": "wall-clock to relative primal and dual residuals < 1e-4 at 256^3 "
                                         "(held-out phantoms 90000-90004)", **warm}
@@ -473,6 +475,81 @@ def run_ours(args, w, rank, world, local_rank, pool_futs=None):
         line["cpu_baseline"]["other_configs"] = cpu_baselines_other_configs()
     print(json.dumps(line), flush=True)
     plan.close()
+
+
+def _smooth_y(w, plan, torch):
+    """A seeded smooth observation of the workload's LR shape on the device
+    (timing only: a fixed iteration count costs the same for any data)."""
+    from synth import normal
+    m, n, s_ = w.lr_dims
+    y = 0.5 + 0.1 * normal(w.seed, 5, m * n * s_).reshape((s_, n, m))
+    return torch.tensor(y, dtype=plan.tdtype, device="cuda")
+
+
+def gpu_other_configs(sr3d, torch, reps=3):
+    """The library on the other configurations of the benchmark set, CUDA
+    events on each plan's stream: the 32^3 FP64 problem (Tikhonov + 20
+    iterations, phantom data), the 512x512x256 anisotropic volume (Tikhonov +
+    200 iterations) and the ragged batch of 64 volumes (50 iterations each, one
+    graph; host clock around the synchronous call)."""
+    import synth
+    out = {}
+    for w, dtype, smooth in ((synth.SMALL_FP64, "f64", False), (synth.ANISO_512, "f32", True)):
+        st = torch.cuda.Stream()
+        plan = sr3d.Plan(w.dims, w.dec, w.psf(), dtype, stream=st)
+        plan.autotune()
+        with torch.cuda.stream(st):
+            if smooth:
+                y = _smooth_y(w, plan, torch)
+            else:
+                x_true = torch.tensor(w.phantom(), dtype=plan.tdtype, device="cuda")
+                y = plan.forward(x_true)
+                from synth import noise_sigma
+                y += torch.tensor(noise_sigma(y.double().cpu().numpy(), w.snr_db) * w.noise(), dtype=plan.tdtype,
+                                  device="cuda")
+            x = plan.empty_hr()
+        plan.admm_tv(y, x, w.lam, w.mu, w.iters, tau_init=w.tau)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            plan.admm_tv(y, x, w.lam, w.mu, w.iters, tau_init=w.tau)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[w.name] = {"value": w.voxels * w.iters / (ms * 1e-3), "unit": UNIT, "ms_per_solve": ms,
+                       "iters": w.iters, "dtype": dtype,
+                       "data": "seeded smooth observation" if smooth else "seeded phantom",
+                       "solve": f"LR spectrum + Tikhonov start (tau {w.tau:g}) + {w.iters} ADMM-TV iterations"}
+        plan.close()
+        del x, y
+    ws = synth.batch_workloads()
+    plans, ys, xs = [], [], []
+    for w in ws:
+        st = torch.cuda.Stream()
+        p = sr3d.Plan(w.dims, w.dec, w.psf(), "f32", stream=st)
+        p.autotune()  # cached per geometry
+        with torch.cuda.stream(st):
+            ys.append(_smooth_y(w, p, torch))
+            xs.append(p.empty_hr())
+        plans.append(p)
+    torch.cuda.synchronize()
+    lams, rhos, taus = [w.lam for w in ws], [w.mu for w in ws], [w.tau for w in ws]
+    iters = ws[0].iters
+    sr3d.admm_tv_batched(plans, ys, xs, lams, rhos, taus, iters)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        sr3d.admm_tv_batched(plans, ys, xs, lams, rhos, taus, iters)
+    torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / reps
+    vox = sum(w.voxels for w in ws)
+    out["batch64_ragged"] = {"value": vox * iters / sec, "unit": UNIT, "ms_per_solve": 1e3 * sec, "iters": iters,
+                             "volumes": len(ws), "voxels": vox, "dtype": "f32", "data": "seeded smooth observations",
+                             "solve": "LR spectra + Tikhonov starts + 50 ADMM-TV iterations per volume, one graph"}
+    for p in plans:
+        p.close()
+    return out
 
 
 def run_batch(args, rank, world, local_rank):
@@ -832,6 +909,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="headline: skip the GPU timings of the other configurations")
     ap.add_argument("--no-warm-start", action="store_true",
                     help="headline: skip the warm- against cold-start measurement")
     ap.add_argument("--schedule", default="",

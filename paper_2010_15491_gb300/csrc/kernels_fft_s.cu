@@ -373,10 +373,11 @@ __device__ __forceinline__ float rcp_nr(float x) {
   return r * fmaf(-x, r, 2.0f);
 }
 
-template <bool STATS, int DR, int DC, int DS>
-__global__ void __launch_bounds__(256, 3) k_fft_s_admm256(float2* __restrict__ spec, int Ms, int Mp, int Nn, int TW,
-                                                        SolveArgs sv, const float2* __restrict__ twS, int nNl) {
-  constexpr int S = 256, QN = DR * DC, D = DR * DC * DS, RS = 16 / DS, SL = S / DS;
+template <int S, bool STATS, int DR, int DC, int DS>
+__global__ void __launch_bounds__(256, 3) k_fft_s_admm_reg(float2* __restrict__ spec, int Ms, int Mp, int Nn, int TW,
+                                                         SolveArgs sv, const float2* __restrict__ twS, int nNl) {
+  constexpr int TPL = S / 16, NST = ct_nst(S), R0 = ct_radix(S, 0), NB = 16 / R0;
+  constexpr int QN = DR * DC, D = DR * DC * DS, RS = 16 / DS, SL = S / DS;
   static_assert(QN == 1 || QN == 2 || QN == 4, "class members in the (m, n) plane: 1, 2 or 4 lanes");
   static_assert(16 % DS == 0, "the s members of a class must share a thread");
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -398,17 +399,14 @@ __global__ void __launch_bounds__(256, 3) k_fft_s_admm256(float2* __restrict__ s
   ct_load_twiddles(tws, twS, S);
 
   float2 v[16];
-  // forward transform, stage 0: 16 loads in flight, radix 16
-#pragma unroll
-  for (int r = 0; r < 16; ++r) v[r] = cls_ok ? col[(long long)(tl + 16 * r) * plane] : make_float2(0.f, 0.f);
-  Dft<16, float2, float>::run(v);
-#pragma unroll
-  for (int r = 0; r < 16; ++r) line[(16 * tl + r) * rowlen] = v[r];
-  __syncthreads();
-  // stage 1: twiddles, radix 16; v[r] = frequency tl + 16 r
+  // forward transform: every stage but the last through shared memory (the
+  // first one loads straight from global memory, 16 loads in flight)
+  auto ld = [&](int j) -> float2 { return cls_ok ? col[(long long)j * plane] : make_float2(0.f, 0.f); };
+  ct_run_to<S, 0, NST - 1, false>(ld, line, rowlen, tl, tws, 1);
+  // last stage (radix 16, NS = TPL) into registers: v[r] = frequency tl + TPL r
 #pragma unroll
   for (int r = 0; r < 16; ++r) {
-    float2 a = line[(tl + 16 * r) * rowlen];
+    float2 a = line[(tl + TPL * r) * rowlen];
     if (r > 0) a = cmul(a, tws[tl * r]);
     v[r] = a;
   }
@@ -435,7 +433,7 @@ __global__ void __launch_bounds__(256, 3) k_fft_s_admm256(float2* __restrict__ s
   double acc = 0.0;
 #pragma unroll
   for (int cr = 0; cr < RS; ++cr) {
-    const int is = tl + 16 * cr;  // LR s frequency of the class
+    const int is = tl + TPL * cr;  // LR s frequency of the class
     const int c = gm + GMc * is;
     const float2 Yc = cls_ok ? __ldg(&yhc[c]) : make_float2(0.f, 0.f);
     const bool dc_cls = cls_ok && g == 0 && jl == 0 && is == 0;
@@ -541,39 +539,54 @@ __global__ void __launch_bounds__(256, 3) k_fft_s_admm256(float2* __restrict__ s
       if (lane == 0) sv.partial[bc] = s_;
     }
   }
-  // inverse transform, stage 0 from the registers: radix 16
-  Dft<16, float2, float>::run(v);
-  __syncthreads();  // every thread has read its forward stage-1 inputs
+  // inverse transform, stage 0 (radix R0, no twiddles) from the registers:
+  // butterfly j = tl + u TPL takes inputs j + r S/R0 = tl + TPL (u + r NB)
+  __syncthreads();  // every thread has read its forward last-stage inputs
 #pragma unroll
-  for (int r = 0; r < 16; ++r) line[(16 * tl + r) * rowlen] = v[r];
-  __syncthreads();
+  for (int u = 0; u < NB; ++u) {
+    float2 w[R0];
 #pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    float2 a = line[(tl + 16 * r) * rowlen];
-    if (r > 0) a = cmul(a, tws[tl * r]);
-    v[r] = a;
+    for (int r = 0; r < R0; ++r) w[r] = v[u + r * NB];
+    Dft<R0, float2, float>::run(w);
+    const int j = tl + u * TPL;
+#pragma unroll
+    for (int r = 0; r < R0; ++r) line[(j * R0 + r) * rowlen] = w[r];
   }
-  Dft<16, float2, float>::run(v);
+  __syncthreads();
   // the store addresses are formed again here rather than kept live (in
   // registers) from the loads through the whole solve
   asm volatile("" : "+l"(col));
-  if (cls_ok) {
-#pragma unroll
-    for (int r = 0; r < 16; ++r) col[(long long)(tl + 16 * r) * plane] = conjc(v[r]);
-  }
+  auto st = [&](int j, float2 x) {
+    if (cls_ok) col[(long long)j * plane] = conjc(x);
+  };
+  ct_run<S, 1, false, true, false>(CtNone{}, st, line, rowlen, tl, tws, 1);
 }
 
-template <bool STATS, int DR, int DC, int DS>
-static cudaError_t fft_s_admm256(const Plan& p, const Geometry& g, void* spec, const void* tw, const SolveArgs& sv) {
+template <int S, bool STATS, int DR, int DC, int DS>
+static cudaError_t fft_s_admm_reg(const Plan& p, const Geometry& g, void* spec, const void* tw, const SolveArgs& sv) {
   const int TW = g.tw_s;
-  size_t smem = (size_t)(256 * TW * DC + 256) * sizeof(float2);
+  size_t smem = (size_t)(S * TW * DC + S) * sizeof(float2);
   if (STATS) smem += 32 * sizeof(double);
   dim3 grid((g.Ms + TW - 1) / TW, g.N / DC);
   cudaError_t e;
-  if ((e = allow_smem(k_fft_s_admm256<STATS, DR, DC, DS>, smem)) != cudaSuccess) return e;
-  k_fft_s_admm256<STATS, DR, DC, DS><<<grid, TW * DC * 16, smem, p.stream>>>((float2*)spec, g.Ms, g.Mp, g.N, TW, sv,
-                                                                          (const float2*)tw, g.Nl);
+  if ((e = allow_smem(k_fft_s_admm_reg<S, STATS, DR, DC, DS>, smem)) != cudaSuccess) return e;
+  k_fft_s_admm_reg<S, STATS, DR, DC, DS><<<grid, TW * DC * (S / 16), smem, p.stream>>>(
+      (float2*)spec, g.Ms, g.Mp, g.N, TW, sv, (const float2*)tw, g.Nl);
   return cudaGetLastError();
+}
+
+// the register-resident ADMM s pass for the compile-time lengths and the class
+// shapes of the benchmark set (2x2x2, 2x2x1, 1x1x4); cudaErrorNotSupported otherwise
+template <int S>
+static cudaError_t fft_s_admm_reg_shape(const Plan& p, const Geometry& g, void* spec, const void* tw, bool stats,
+                                        const SolveArgs& sv) {
+  if (g.dr == 2 && g.dc == 2 && g.ds == 2)
+    return stats ? fft_s_admm_reg<S, true, 2, 2, 2>(p, g, spec, tw, sv) : fft_s_admm_reg<S, false, 2, 2, 2>(p, g, spec, tw, sv);
+  if (g.dr == 1 && g.dc == 1 && g.ds == 4)
+    return stats ? fft_s_admm_reg<S, true, 1, 1, 4>(p, g, spec, tw, sv) : fft_s_admm_reg<S, false, 1, 1, 4>(p, g, spec, tw, sv);
+  if (g.dr == 2 && g.dc == 2 && g.ds == 1)
+    return stats ? fft_s_admm_reg<S, true, 2, 2, 1>(p, g, spec, tw, sv) : fft_s_admm_reg<S, false, 2, 2, 1>(p, g, spec, tw, sv);
+  return cudaErrorNotSupported;
 }
 
 template <typename T, int EMAX, int MODE, bool STATS, int NC, int DR_ = 0, int DC_ = 0, int DS_ = 0>
@@ -602,33 +615,15 @@ static cudaError_t fft_s_e(const Plan& p, const Geometry& g, void* spec, const v
     case S_TIK_USER: return fft_s_k<T, EMAX, S_TIK_USER, false, 0>(p, g, spec, tw, sv);
     case S_ADMM:
       if constexpr (sizeof(T) == 4 && EMAX == 16) {
-        if (ct_len<T>(g.S, g.fs) == 256 && g.tw_s * g.g_s * (256 / 16) <= 256) {
-          if (g.dr == 2 && g.dc == 2 && g.ds == 2)
-            return stats ? fft_s_admm256<true, 2, 2, 2>(p, g, spec, tw, sv)
-                         : fft_s_admm256<false, 2, 2, 2>(p, g, spec, tw, sv);
-          if (g.dr == 1 && g.dc == 1 && g.ds == 4)
-            return stats ? fft_s_admm256<true, 1, 1, 4>(p, g, spec, tw, sv)
-                         : fft_s_admm256<false, 1, 1, 4>(p, g, spec, tw, sv);
-          if (g.dr == 2 && g.dc == 2 && g.ds == 1)
-            return stats ? fft_s_admm256<true, 2, 2, 1>(p, g, spec, tw, sv)
-                         : fft_s_admm256<false, 2, 2, 1>(p, g, spec, tw, sv);
-          return stats ? fft_s_k<T, EMAX, S_ADMM, true, 256>(p, g, spec, tw, sv)
-                       : fft_s_k<T, EMAX, S_ADMM, false, 256>(p, g, spec, tw, sv);
-        }
-        // shorter s lines (small volumes of the batched solve), fixed iterations
         const int sl = ct_len<T>(g.S, g.fs);
-        if (!stats && (sl == 64 || sl == 128) && g.tw_s * g.g_s * (sl / 16) <= 256) {
-          const bool c222 = g.dr == 2 && g.dc == 2 && g.ds == 2, c221 = g.dr == 2 && g.dc == 2 && g.ds == 1,
-                     c114 = g.dr == 1 && g.dc == 1 && g.ds == 4;
-          if (sl == 64) {
-            if (c222) return fft_s_k<T, EMAX, S_ADMM, false, 64, 2, 2, 2>(p, g, spec, tw, sv);
-            if (c221) return fft_s_k<T, EMAX, S_ADMM, false, 64, 2, 2, 1>(p, g, spec, tw, sv);
-            if (c114) return fft_s_k<T, EMAX, S_ADMM, false, 64, 1, 1, 4>(p, g, spec, tw, sv);
-          } else {
-            if (c222) return fft_s_k<T, EMAX, S_ADMM, false, 128, 2, 2, 2>(p, g, spec, tw, sv);
-            if (c221) return fft_s_k<T, EMAX, S_ADMM, false, 128, 2, 2, 1>(p, g, spec, tw, sv);
-            if (c114) return fft_s_k<T, EMAX, S_ADMM, false, 128, 1, 1, 4>(p, g, spec, tw, sv);
-          }
+        if ((sl == 64 || sl == 128 || sl == 256) && g.tw_s * g.g_s * (sl / 16) <= 256) {
+          const cudaError_t r = sl == 256   ? fft_s_admm_reg_shape<256>(p, g, spec, tw, stats, sv)
+                                : sl == 128 ? fft_s_admm_reg_shape<128>(p, g, spec, tw, stats, sv)
+                                            : fft_s_admm_reg_shape<64>(p, g, spec, tw, stats, sv);
+          if (r != cudaErrorNotSupported) return r;
+          if (sl == 256)
+            return stats ? fft_s_k<T, EMAX, S_ADMM, true, 256>(p, g, spec, tw, sv)
+                         : fft_s_k<T, EMAX, S_ADMM, false, 256>(p, g, spec, tw, sv);
         }
         if (g.dr == 2 && g.dc == 2 && g.ds == 1)
           return stats ? fft_s_k<T, EMAX, S_ADMM, true, 0, 2, 2, 1>(p, g, spec, tw, sv)
