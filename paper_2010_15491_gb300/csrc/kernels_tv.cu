@@ -223,10 +223,10 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
 }
 
 // ---------------------------------------------------------------------------
-// Vectorised variant for FP32 volumes with m_h a multiple of 128: a CTA of
-// 32 x 9 threads covers m in [m0, m0+128) x n in [n0, n0+8); warps 0-7 own
-// the tile rows, each thread four consecutive m voxels (float4 loads and
-// stores).  Warp 8, the halo warp, copies the x and d halo rows and columns
+// Vectorised variant for FP32 volumes whose m_h is a multiple of the tile
+// width W (128, else 96, else 64): a CTA of 32 x 9 threads covers m in
+// [m0, m0+W) x n in [n0, n0+8); warps 0-7 own the tile rows, lanes below W/4
+// four consecutive m voxels each (float4 loads and stores).  Warp 8, the halo warp, copies the x and d halo rows and columns
 // and evaluates the -n halo row and the -m halo column of the rho region, so
 // that every warp evaluates about one row per plane (a tile warp that also
 // took the halo row held the others at the plane's barrier).  Same algebra, modes
@@ -234,10 +234,9 @@ __global__ void __launch_bounds__(TM* TN) k_tv(const T* __restrict__ x, const T*
 // in FP32 (sqrtf for ||g||) and accumulated over its planes in compensated
 // FP32 (Kahan), then reduced across the CTA in FP64 (FP64 arithmetic is slow
 // on this GPU).  Shared rows are padded so that m0 sits at column 4 (16-byte
-// aligned); column 3 is m0-1 and column 132 is m0+128.
+// aligned); column 3 is m0-1 and column 4+W is m0+W.
 // ---------------------------------------------------------------------------
-constexpr int V4M = 128;
-constexpr int V4W = 136;  // padded row length (floats)
+constexpr int V4W = 136;  // padded row length (floats), for every tile width W <= 128
 
 __device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
@@ -256,8 +255,8 @@ __device__ __forceinline__ void cp4(float* dst, const float* src) {
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-template <int MODE, bool STATS>
-__global__ void __launch_bounds__(32 * (TN + 1), STATS ? 2 : 3) k_tv4(const float* __restrict__ x, const float* __restrict__ din,
+template <int W, int MODE, bool STATS>
+__global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restrict__ x, const float* __restrict__ din,
                                              float* __restrict__ dout, float* __restrict__ theta,
                                              float* __restrict__ psi, int M, int N, int S, int TS, float thr,
                                              double* __restrict__ partial) {
@@ -270,7 +269,9 @@ __global__ void __launch_bounds__(32 * (TN + 1), STATS ? 2 : 3) k_tv4(const floa
   constexpr int XP = XR * V4W, DP = 3 * RR * V4W, RP = RR * V4W;
   const int lm = threadIdx.x, ln = threadIdx.y, tid = ln * 32 + lm;
   const bool halo_warp = ln == TN;
-  const int m0 = blockIdx.x * V4M, n0 = blockIdx.y * TN, s0 = blockIdx.z * TS;
+  static_assert(W == 64 || W == 96 || W == 128, "tile width");
+  const bool act = W == 128 || lm < W / 4;  // lanes that own four voxels of a tile row (all at W = 128)
+  const int m0 = blockIdx.x * W, n0 = blockIdx.y * TN, s0 = blockIdx.z * TS;
   const long long V = (long long)M * N * S;
   const long long P = (long long)M * N;
   const int s_end = min(S, s0 + TS);
@@ -281,8 +282,8 @@ __global__ void __launch_bounds__(32 * (TN + 1), STATS ? 2 : 3) k_tv4(const floa
   // halo warp: lane < 10 -> x column m0-1 of row n0-1+lane; 10 <= lane < 20 -> column m0+128
   const bool xcol = halo_warp && lm < 20;
   const int xc_row = lm < 10 ? lm : lm - 10;
-  const int xc_col = lm < 10 ? 3 : 4 + V4M;
-  const long long o_xc = (long long)((n0 - 1 + xc_row + N) % N) * M + (lm < 10 ? (m0 - 1 + M) % M : (m0 + V4M) % M);
+  const int xc_col = lm < 10 ? 3 : 4 + W;
+  const long long o_xc = (long long)((n0 - 1 + xc_row + N) % N) * M + (lm < 10 ? (m0 - 1 + M) % M : (m0 + W) % M);
   // halo warp: lane < RR -> d (and rho) column m0-1 of row n0-1+lane
   const bool rcol = halo_warp && lm < RR;
   const long long o_rc = (long long)((n0 - 1 + lm + N) % N) * M + (m0 - 1 + M) % M;
@@ -291,10 +292,12 @@ __global__ void __launch_bounds__(32 * (TN + 1), STATS ? 2 : 3) k_tv4(const floa
   auto fetch_x = [&](int s, float* buf) {
     const long long pl = plane_of(s);
     if (!halo_warp) {
-      cp16(buf + (ln + 1) * V4W + mc, x + pl + o_in);
+      if (act) cp16(buf + (ln + 1) * V4W + mc, x + pl + o_in);
     } else {
-      cp16(buf + mc, x + pl + o_hr);
-      cp16(buf + (XR - 1) * V4W + mc, x + pl + o_xr);
+      if (act) {
+        cp16(buf + mc, x + pl + o_hr);
+        cp16(buf + (XR - 1) * V4W + mc, x + pl + o_xr);
+      }
       if (xcol) cp4(buf + xc_row * V4W + xc_col, x + pl + o_xc);
     }
   };
@@ -303,9 +306,9 @@ __global__ void __launch_bounds__(32 * (TN + 1), STATS ? 2 : 3) k_tv4(const floa
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       if (!halo_warp) {
-        cp16(buf + k * RP + (ln + 1) * V4W + mc, din + k * V + pl + o_in);
+        if (act) cp16(buf + k * RP + (ln + 1) * V4W + mc, din + k * V + pl + o_in);
       } else {
-        cp16(buf + k * RP + mc, din + k * V + pl + o_hr);
+        if (act) cp16(buf + k * RP + mc, din + k * V + pl + o_hr);
         if (rcol) cp4(buf + k * RP + lm * V4W + 3, din + k * V + pl + o_rc);
       }
     }
@@ -406,10 +409,9 @@ __global__ void __launch_bounds__(32 * (TN + 1), STATS ? 2 : 3) k_tv4(const floa
         st4(dout + 2 * V + gi, make_float4(e2v[0], e2v[1], e2v[2], e2v[3]));
       }
     };
-    if (!halo_warp) {
-      quad(ln + 1, true);
-    } else {
-      quad(0, false);
+    if (act) {
+      if (!halo_warp) quad(ln + 1, true);
+      else quad(0, false);
     }
     if (rcol) {
       // halo column m0-1 (shared column 3), row lm
@@ -422,7 +424,7 @@ __global__ void __launch_bounds__(32 * (TN + 1), STATS ? 2 : 3) k_tv4(const floa
     }
     __syncthreads();
     // phase 2: Theta = L^T rho for the four interior voxels (tile warps)
-    if (!halo_warp) {
+    if (!halo_warp && act) {
       const int row = (ln + 1) * V4W + mc;
       const int up = ln * V4W + mc;
       float4 own0, own1, own2, up1;
@@ -511,7 +513,13 @@ static size_t tv4_smem(bool stats) {
                           (size_t)(stats ? 6 : 3) * (TN + 1) * V4W);
 }
 
-static bool tv_vec4(const Plan& p) { return p.dtype == 0 && p.hr.M % V4M == 0 && p.hr.N % TN == 0; }
+// tile width of the vectorised kernel for this plan (0: the general kernel)
+static int tv4_width(const Plan& p) {
+  if (p.dtype != 0 || p.hr.N % TN != 0) return 0;
+  const int M = p.hr.M;
+  return M % 128 == 0 ? 128 : M % 96 == 0 ? 96 : M % 64 == 0 ? 64 : 0;
+}
+static bool tv_vec4(const Plan& p) { return tv4_width(p) > 0; }
 
 int tv_default_ts(const Geometry& g) {
   // planes per CTA: a few CTAs per SM while keeping the one-plane priming
@@ -527,10 +535,11 @@ static int tv_ts(const Geometry& g) { return g.ts_tv > 0 ? g.ts_tv : tv_default_
 template <typename T>
 static cudaError_t tv_per_sm(const Plan& p, int* per_sm) {
   if (tv_vec4(p)) {
+    // the three widths share the launch bounds and the shared-memory size
     const size_t smem = tv4_smem(false);
-    cudaError_t e = cudaFuncSetAttribute(k_tv4<0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tv4<128, 0, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tv4<0, false>, 32 * (TN + 1), smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tv4<128, 0, false>, 32 * (TN + 1), smem);
   }
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tv<T, 0, false>, TM * TN, 0);
 }
@@ -556,7 +565,7 @@ int tv_ts_candidates(const Plan& p, int* out, int cap) {
     cudaGetLastError();
     return n;
   }
-  const long long tiles = tv_vec4(p) ? (long long)(g.M / V4M) * (g.N / TN)
+  const long long tiles = tv_vec4(p) ? (long long)(g.M / tv4_width(p)) * (g.N / TN)
                                      : (long long)((g.M + TM - 1) / TM) * ((g.N + TN - 1) / TN);
   const long long slots = (long long)sms * per_sm;
   for (int w = 1; w <= 4; ++w) {
@@ -585,35 +594,42 @@ static cudaError_t tv_k(const Plan& p, const void* x, const void* din, void* dou
   return cudaGetLastError();
 }
 
-template <int MODE, bool STATS>
+template <int W, int MODE, bool STATS>
 static cudaError_t tv4_k(const Plan& p, const void* x, const void* din, void* dout, void* theta, void* psi,
                          double thr) {
   const Geometry& g = p.hr;
   const int ts = tv_ts(g);
-  dim3 grid(g.M / V4M, g.N / TN, (g.S + ts - 1) / ts);
+  dim3 grid(g.M / W, g.N / TN, (g.S + ts - 1) / ts);
   dim3 block(32, TN + 1);  // eight tile warps and the halo warp
   const size_t smem = tv4_smem(STATS);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_tv4<MODE, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_tv4<W, MODE, STATS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_tv4<MODE, STATS><<<grid, block, smem, p.stream>>>((const float*)x, (const float*)din, (float*)dout,
+  k_tv4<W, MODE, STATS><<<grid, block, smem, p.stream>>>((const float*)x, (const float*)din, (float*)dout,
                                                    (float*)theta, (float*)psi, g.M, g.N, g.S, ts, (float)thr,
                                                    p.partial);
   return cudaGetLastError();
+}
+
+template <int W>
+static cudaError_t tv4_w(const Plan& p, const void* x, const void* din, void* dout, void* theta, void* psi, double thr,
+                         int mode, bool stats) {
+  if (mode == 0)
+    return stats ? tv4_k<W, 0, true>(p, x, din, dout, theta, psi, thr) : tv4_k<W, 0, false>(p, x, din, dout, theta, psi, thr);
+  if (mode == 2)
+    return stats ? tv4_k<W, 2, true>(p, x, din, dout, theta, psi, thr) : tv4_k<W, 2, false>(p, x, din, dout, theta, psi, thr);
+  return stats ? tv4_k<W, 1, true>(p, x, din, dout, theta, psi, thr) : tv4_k<W, 1, false>(p, x, din, dout, theta, psi, thr);
 }
 
 template <typename T>
 static cudaError_t tv_t(const Plan& p, const void* x, const void* din, void* dout, void* theta, void* psi,
                         double thr, int mode, bool stats) {
   if (mode == 0 && p.tv_aniso) mode = 2;  // the plan's TV is anisotropic
-  if (tv_vec4(p)) {
-    if (mode == 0)
-      return stats ? tv4_k<0, true>(p, x, din, dout, theta, psi, thr) : tv4_k<0, false>(p, x, din, dout, theta, psi, thr);
-    if (mode == 2)
-      return stats ? tv4_k<2, true>(p, x, din, dout, theta, psi, thr) : tv4_k<2, false>(p, x, din, dout, theta, psi, thr);
-    return stats ? tv4_k<1, true>(p, x, din, dout, theta, psi, thr) : tv4_k<1, false>(p, x, din, dout, theta, psi, thr);
-  }
+  const int w = tv4_width(p);
+  if (w == 128) return tv4_w<128>(p, x, din, dout, theta, psi, thr, mode, stats);
+  if (w == 96) return tv4_w<96>(p, x, din, dout, theta, psi, thr, mode, stats);
+  if (w == 64) return tv4_w<64>(p, x, din, dout, theta, psi, thr, mode, stats);
   if (mode == 0)
     return stats ? tv_k<T, 0, true>(p, x, din, dout, theta, psi, thr)
                  : tv_k<T, 0, false>(p, x, din, dout, theta, psi, thr);
@@ -691,7 +707,7 @@ __global__ void k_finalize(const double* __restrict__ ptv, long long ntv, const 
 static long long tv_launch_blocks(const Plan& p) {
   const Geometry& g = p.hr;
   const int ts = tv_ts(g);
-  const long long mt = tv_vec4(p) ? g.M / V4M : (g.M + TM - 1) / TM;
+  const long long mt = tv_vec4(p) ? g.M / tv4_width(p) : (g.M + TM - 1) / TM;
   return mt * ((g.N + TN - 1) / TN) * ((g.S + ts - 1) / ts);
 }
 
