@@ -1297,14 +1297,33 @@ extern "C" int sr3d_autotune(sr3d_plan_t plan, int reps) {
 // ---------------------------------------------------------------------------
 // Batched solve of many volumes of uneven size and decimation.
 //
-// Every volume keeps its own plan and stream.  The per-volume set-up (LR
-// spectrum, Tikhonov start, initial Theta) is launched on the plans' streams;
-// the iterations run as one CUDA graph that forks from a capture stream into
-// one chain per volume (two ADMM iterations each) and joins back, replayed
-// iters/2 times.  Independent chains run concurrently, so many small volumes
-// fill the GPU together.  The graph is cached for repeated calls with the same
-// plans, buffers and parameters.
+// Every volume keeps its own plan and stream, and the per-volume set-up (LR
+// spectrum, Tikhonov start, initial Theta) is launched on the plans' streams.
+// Volumes that share a geometry, a tile schedule, lambda, rho, the TV kind and
+// a separable PSF (FP32) form a group: their iterates, duals, Theta, spectra,
+// solve-order LR spectra and separable Lambda tables are copied into buffers
+// that hold the group's volumes one after another, and each ADMM iteration of
+// the group is six launches (m, n, s passes with the class solve, n, m, TV)
+// over all of them; the m and n passes treat the volumes' planes as more
+// planes, the s pass and the TV kernel take the volume from their grid.  Other
+// volumes run their own six launches.  The iterations run as one CUDA graph
+// that forks from a capture stream into one chain per group or single volume
+// (two ADMM iterations each) and joins back, replayed iters/2 times, so the
+// chains run concurrently; the graph and the group buffers are cached for
+// repeated calls with the same plans, buffers and parameters.
 // ---------------------------------------------------------------------------
+struct BatchGroup {
+  std::vector<int> vols;         // volume indices of the call, in order
+  const sr3d_plan_s* lead = nullptr;
+  void* x = nullptr;             // B V reals
+  void* d[2] = {nullptr, nullptr};  // B 3V reals each
+  void* theta = nullptr;         // B V reals
+  void* spec = nullptr;          // B spectra
+  void* yhat = nullptr;          // B solve-order LR spectra
+  void* lam[3] = {nullptr, nullptr, nullptr};  // B M, B N, B S separable factors
+  int cur = 0;                   // which of d[] holds the current dual
+};
+
 struct BatchGraph {
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> key_ptr;
@@ -1312,9 +1331,96 @@ struct BatchGraph {
   std::vector<cudaEvent_t> ev;  // fork/join events
   cudaStream_t main = nullptr;
   long long launches[8] = {0};
+  // grouping of the last call and its buffers
+  std::vector<BatchGroup> groups;
+  std::vector<const void*> gkey_ptr;
+  std::vector<double> gkey_val;
 };
 static std::mutex g_batch_mu;
 static BatchGraph g_batch;
+
+static void free_groups() {
+  for (BatchGroup& G : g_batch.groups) {
+    void* bufs[] = {G.x, G.d[0], G.d[1], G.theta, G.spec, G.yhat, G.lam[0], G.lam[1], G.lam[2]};
+    for (void* q : bufs)
+      if (q) cudaFree(q);
+  }
+  g_batch.groups.clear();
+}
+
+// a volume that can join a group: FP32, separable PSF in use, vectorised TV
+static bool groupable(const Plan& p) { return p.dtype == SR3D_F32 && p.sep_avail && p.sep_on && tv_batchable(p); }
+
+// Groups of two or more volumes (see above); singletons are not listed.
+static int build_groups(int n, sr3d_plan_t* plans, const double* lambda, const double* rho) {
+  std::vector<bool> used(n, false);
+  std::vector<BatchGroup> out;
+  for (int i = 0; i < n; ++i) {
+    if (used[i] || !groupable(plans[i]->p)) continue;
+    const Plan& a = plans[i]->p;
+    BatchGroup G;
+    G.vols.push_back(i);
+    for (int j = i + 1; j < n; ++j) {
+      if (used[j] || !groupable(plans[j]->p)) continue;
+      const Plan& b = plans[j]->p;
+      const Geometry &ga = a.hr, &gb = b.hr;
+      if (ga.M == gb.M && ga.N == gb.N && ga.S == gb.S && ga.dr == gb.dr && ga.dc == gb.dc && ga.ds == gb.ds &&
+          ga.tw_n == gb.tw_n && ga.tw_s == gb.tw_s && ga.ts_tv == gb.ts_tv && ga.lm_f == gb.lm_f &&
+          ga.lm_i == gb.lm_i && a.tv_aniso == b.tv_aniso && lambda[i] == lambda[j] && rho[i] == rho[j])
+        G.vols.push_back(j);
+    }
+    if (G.vols.size() < 2) continue;
+    for (int v : G.vols) used[v] = true;
+    G.lead = plans[i];
+    out.push_back(G);
+  }
+  free_groups();
+  g_batch.groups = out;
+  for (BatchGroup& G : g_batch.groups) {
+    const Plan& p = G.lead->p;
+    const Geometry& g = p.hr;
+    const size_t B = G.vols.size(), csz = 2 * p.esz;
+    const size_t sizes[9] = {B * g.V() * p.esz, 3 * B * g.V() * p.esz, 3 * B * g.V() * p.esz, B * g.V() * p.esz,
+                             B * g.spec_elems() * csz, B * solve_yhat_elems(g) * csz, B * g.M * csz, B * g.N * csz,
+                             B * g.S * csz};
+    void** dst[9] = {&G.x, &G.d[0], &G.d[1], &G.theta, &G.spec, &G.yhat, &G.lam[0], &G.lam[1], &G.lam[2]};
+    for (int k = 0; k < 9; ++k) {
+      cudaError_t e = cudaMalloc(dst[k], sizes[k]);
+      if (e != cudaSuccess) {
+        *dst[k] = nullptr;
+        cudaGetLastError();
+        free_groups();
+        return fail(e == cudaErrorMemoryAllocation ? SR3D_ERR_OOM : SR3D_ERR_CUDA, "batched group buffers: %s",
+                    cudaGetErrorString(e));
+      }
+    }
+  }
+  return SR3D_OK;
+}
+
+// One ADMM iteration of a group (the six passes over all of its volumes) on
+// the lead plan's stream: dual d[cur] in, d[1 - cur] out.
+static int group_iteration(BatchGroup& G, double thr, double rho) {
+  Plan& p = const_cast<Plan&>(G.lead->p);
+  const int B = (int)G.vols.size();
+  Geometry gB = p.hr;  // the m and n passes see the volumes' planes as more planes
+  gB.S *= B;
+  SolveArgs sv = solve_args(p, 0, rho);
+  sv.yhat = G.yhat;
+  sv.lamM = G.lam[0];
+  sv.lamN = G.lam[1];
+  sv.lamS = G.lam[2];
+  sv.sep = 1;
+  sv.batch = B;
+  LAUNCH(SR3D_K_RFFT_FWD, launch_rfft_m_fwd(p, gB, G.theta, G.spec, p.twM));
+  LAUNCH(SR3D_K_FFTN_FWD, launch_fft_n(p, gB, G.spec, p.twN, false));
+  LAUNCH(SR3D_K_FFTS, launch_fft_s(p, p.hr, G.spec, p.twS, S_ADMM, false, &sv));
+  LAUNCH(SR3D_K_FFTN_INV, launch_fft_n(p, gB, G.spec, p.twN, true));
+  LAUNCH(SR3D_K_RFFT_INV, launch_rfft_m_inv(p, gB, G.spec, G.x, p.twM, 1.0 / (double)p.hr.V()));
+  LAUNCH(SR3D_K_TV, launch_tv_batched(p, B, G.x, G.d[G.cur], G.d[1 - G.cur], G.theta, thr));
+  G.cur = 1 - G.cur;
+  return SR3D_OK;
+}
 
 static int batch_events(size_t n) {
   while (g_batch.ev.size() < n + 1) {
@@ -1340,6 +1446,30 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
   }
   std::lock_guard<std::mutex> lk(g_batch_mu);
   TRY(batch_events((size_t)n));
+  // grouping (cached while the plans, their versions and parameters repeat)
+  {
+    std::vector<const void*> gp;
+    std::vector<double> gv;
+    for (int i = 0; i < n; ++i) {
+      gp.push_back(plans[i]);
+      gv.push_back((double)plans[i]->p.version);
+      gv.push_back(lambda[i]);
+      gv.push_back(rho[i]);
+    }
+    if (gp != g_batch.gkey_ptr || gv != g_batch.gkey_val) {
+      if (g_batch.exec) {
+        cudaGraphExecDestroy(g_batch.exec);
+        g_batch.exec = nullptr;
+      }
+      g_batch.gkey_ptr.clear();
+      TRY(build_groups(n, plans, lambda, rho));
+      g_batch.gkey_ptr = gp;
+      g_batch.gkey_val = gv;
+    }
+  }
+  std::vector<int> group_of(n, -1);
+  for (int k = 0; k < (int)g_batch.groups.size(); ++k)
+    for (int v : g_batch.groups[k].vols) group_of[v] = k;
   std::vector<void*> dcur(n), dnext(n);
   // set-up on every plan's stream, after whatever the stream holds
   for (int i = 0; i < n; ++i) {
@@ -1354,12 +1484,48 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
     CK(cudaMemsetAsync(dcur[i], 0, (size_t)3 * p.hr.V() * p.esz, p.stream));
     LAUNCH(SR3D_K_TV, launch_tv(p, x[i], dcur[i], nullptr, p.theta, p.psi, lambda[i] / rho[i], 1, false));
   }
-  auto eager_iteration = [&]() -> int {
-    for (int i = 0; i < n; ++i) {
-      Plan& p = plans[i]->p;
-      TRY(admm_iteration(p, x[i], dcur[i], dnext[i], lambda[i] / rho[i], rho[i]));
-      std::swap(dcur[i], dnext[i]);
+  // group members' state into the group buffers, on the lead's stream after
+  // each member's set-up
+  for (BatchGroup& G : g_batch.groups) {
+    Plan& L = const_cast<Plan&>(G.lead->p);
+    const Geometry& g = L.hr;
+    const size_t csz = 2 * L.esz, vb = (size_t)g.V() * L.esz;
+    for (size_t j = 0; j < G.vols.size(); ++j) {
+      Plan& p = plans[G.vols[j]]->p;
+      if (&p != &L) {
+        CK(cudaEventRecord(g_batch.ev[G.vols[j]], p.stream));
+        CK(cudaStreamWaitEvent(L.stream, g_batch.ev[G.vols[j]], 0));
+      }
+      unsigned char* xb = (unsigned char*)G.x + j * vb;
+      unsigned char* tb = (unsigned char*)G.theta + j * vb;
+      unsigned char* yb = (unsigned char*)G.yhat + j * (size_t)solve_yhat_elems(g) * csz;
+      CK(cudaMemcpyAsync(xb, x[G.vols[j]], vb, cudaMemcpyDeviceToDevice, L.stream));
+      CK(cudaMemcpyAsync(tb, p.theta, vb, cudaMemcpyDeviceToDevice, L.stream));
+      CK(cudaMemcpyAsync(yb, p.yhat_solve, (size_t)solve_yhat_elems(g) * csz, cudaMemcpyDeviceToDevice, L.stream));
+      CK(cudaMemcpyAsync((unsigned char*)G.lam[0] + j * g.M * csz, p.lamM1, g.M * csz, cudaMemcpyDeviceToDevice, L.stream));
+      CK(cudaMemcpyAsync((unsigned char*)G.lam[1] + j * g.N * csz, p.lamN1, g.N * csz, cudaMemcpyDeviceToDevice, L.stream));
+      CK(cudaMemcpyAsync((unsigned char*)G.lam[2] + j * g.S * csz, p.lamS1, g.S * csz, cudaMemcpyDeviceToDevice, L.stream));
     }
+    CK(cudaMemsetAsync(G.d[0], 0, 3 * G.vols.size() * vb, L.stream));
+    G.cur = 0;
+  }
+  // the chains: a group (its lead's index) or a single volume
+  std::vector<int> chain;
+  for (int i = 0; i < n; ++i)
+    if (group_of[i] < 0) chain.push_back(i);
+  for (const BatchGroup& G : g_batch.groups) chain.push_back(G.vols[0]);
+  auto chain_iteration = [&](int i) -> int {
+    if (group_of[i] >= 0) {
+      BatchGroup& G = g_batch.groups[group_of[i]];
+      return group_iteration(G, lambda[i] / rho[i], rho[i]);
+    }
+    Plan& p = plans[i]->p;
+    TRY(admm_iteration(p, x[i], dcur[i], dnext[i], lambda[i] / rho[i], rho[i]));
+    std::swap(dcur[i], dnext[i]);
+    return SR3D_OK;
+  };
+  auto eager_iteration = [&]() -> int {
+    for (int i : chain) TRY(chain_iteration(i));
     return SR3D_OK;
   };
   int it = 0;
@@ -1382,6 +1548,10 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
       kv.push_back(rho[i]);
       kv.push_back((double)plans[i]->p.version);
     }
+    for (const BatchGroup& G : g_batch.groups) {
+      kp.push_back(G.x);
+      kv.push_back((double)G.cur);
+    }
     if (!g_batch.exec || kp != g_batch.key_ptr || kv != g_batch.key_val) {
       if (g_batch.exec) {
         cudaGraphExecDestroy(g_batch.exec);
@@ -1394,12 +1564,13 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
       CK(cudaStreamBeginCapture(g_batch.main, cudaStreamCaptureModeThreadLocal));
       int rc = SR3D_OK;
       cudaError_t ec = cudaEventRecord(g_batch.ev[n], g_batch.main);
-      for (int i = 0; i < n && rc == SR3D_OK && ec == cudaSuccess; ++i) {
+      for (size_t c = 0; c < chain.size() && rc == SR3D_OK && ec == cudaSuccess; ++c) {
+        const int i = chain[c];
         Plan& p = plans[i]->p;
         ec = cudaStreamWaitEvent(p.stream, g_batch.ev[n], 0);
         if (ec != cudaSuccess) break;
-        rc = admm_iteration(p, x[i], dcur[i], dnext[i], lambda[i] / rho[i], rho[i]);
-        if (rc == SR3D_OK) rc = admm_iteration(p, x[i], dnext[i], dcur[i], lambda[i] / rho[i], rho[i]);
+        rc = chain_iteration(i);
+        if (rc == SR3D_OK) rc = chain_iteration(i);
         if (rc == SR3D_OK) ec = cudaEventRecord(g_batch.ev[i], p.stream);
         if (ec == cudaSuccess && rc == SR3D_OK) ec = cudaStreamWaitEvent(g_batch.main, g_batch.ev[i], 0);
       }
@@ -1442,6 +1613,16 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
   while (it < iters) {
     TRY(eager_iteration());
     ++it;
+  }
+  // the groups' iterates back to the callers' buffers
+  for (BatchGroup& G : g_batch.groups) {
+    Plan& L = const_cast<Plan&>(G.lead->p);
+    const size_t vb = (size_t)L.hr.V() * L.esz;
+    for (size_t j = 0; j < G.vols.size(); ++j)
+      CK(cudaMemcpyAsync(x[G.vols[j]], (unsigned char*)G.x + j * vb, vb, cudaMemcpyDeviceToDevice, L.stream));
+    CK(cudaEventRecord(g_batch.ev[G.vols[0]], L.stream));
+    for (size_t j = 1; j < G.vols.size(); ++j)
+      CK(cudaStreamWaitEvent(plans[G.vols[j]]->p.stream, g_batch.ev[G.vols[0]], 0));
   }
   for (int i = 0; i < n; ++i) TRY(sync_plan(plans[i]->p));
   return SR3D_OK;

@@ -46,6 +46,12 @@ struct SolveArgs {
   const void* lamS;
   int sep;
   const void* lam_nat;  // Lambda in the natural spectral layout (S_MUL, S_MULC)
+  // Batched ADMM s pass over `batch` volumes of one geometry stored one after
+  // another (spectrum, solve-order LR spectrum, separable tables of M, N, S
+  // entries each); batch <= 1: one volume.  batch_ny (tiles along n per
+  // volume) is set by the launcher.
+  int batch;
+  int batch_ny;
 };
 
 struct Geometry {
@@ -150,6 +156,12 @@ cudaError_t launch_perm_yhat(const Plan& p, const void* yh, void* out);
 
 // ---- launchers (kernels_tv.cu) ----
 // mode 0: ADMM step (shrink + dual update); mode 1: initial Theta = L^T (L x - d)
+// ADMM TV step (isotropic or anisotropic as the plan, no statistics) over
+// `batch` volumes of the plan's geometry stored one after another (x, theta:
+// V each; din, dout: 3V each); the vectorised kernel only (tv_batchable).
+cudaError_t launch_tv_batched(const Plan& p, int batch, const void* x, const void* din, void* dout, void* theta,
+                              double thr);
+bool tv_batchable(const Plan& p);
 cudaError_t launch_tv(const Plan& p, const void* x, const void* din, void* dout, void* theta, void* psi,
                       double thr, int mode, bool stats);
 long long tv_blocks(const Geometry& g);

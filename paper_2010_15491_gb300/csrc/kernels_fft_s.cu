@@ -59,7 +59,7 @@ __host__ __device__ __forceinline__ SolveTile solve_layout(int Ms, int TW, int G
 // thread's share of sum_i |Y_i - (1/d) sum_p Lambda_p X_p|^2 (STATS).
 template <typename T, int MODE, bool STATS, int DR_, int DC_, int DS_>
 __device__ __forceinline__ double solve_tile(cplx<T>* sm, int TW, int G, int a0, int b0, int Ms, const SolveArgs& sv,
-                                             int tid, int nthr) {
+                                             int tid, int nthr, int vb) {
   using C = cplx<T>;
   const int dr = DR_ > 0 ? DR_ : sv.dr, dc = DR_ > 0 ? DC_ : sv.dc, ds = DR_ > 0 ? DS_ : sv.ds;
   const int d = dr * dc * ds;
@@ -73,9 +73,10 @@ __device__ __forceinline__ double solve_tile(cplx<T>* sm, int TW, int G, int a0,
   const T* __restrict__ symN = reinterpret_cast<const T*>(sv.symN);
   const T* __restrict__ symS = reinterpret_cast<const T*>(sv.symS);
   // separable PSF: Lambda of a member is the product of three 1-D factor DFTs
-  const C* __restrict__ lamM = reinterpret_cast<const C*>(sv.lamM);
-  const C* __restrict__ lamN = reinterpret_cast<const C*>(sv.lamN);
-  const C* __restrict__ lamS = reinterpret_cast<const C*>(sv.lamS);
+  // the volume's separable tables (vb > 0 only in a batched ADMM s pass)
+  const C* __restrict__ lamM = reinterpret_cast<const C*>(sv.lamM) + (long long)vb * sv.M;
+  const C* __restrict__ lamN = reinterpret_cast<const C*>(sv.lamN) + (long long)vb * sv.N;
+  const C* __restrict__ lamS = reinterpret_cast<const C*>(sv.lamS) + (long long)vb * sv.S;
   const T alpha = (T)sv.alpha;
   const T ialpha = (T)(1.0 / sv.alpha);
   double acc = 0.0;
@@ -270,7 +271,11 @@ __global__ void __launch_bounds__(NC > 0 ? 256 : 512, NC > 0 ? 3 : 1) k_fft_s(cp
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int S = NC > 0 ? NC : a.N;
-  const int a0 = blockIdx.x * TW, b0 = blockIdx.y * G;
+  // volume of a batch (batched S_ADMM only; see SolveArgs::batch)
+  const int ny = sv.batch_ny > 0 ? sv.batch_ny : (int)gridDim.y;
+  const int vb = blockIdx.y / ny;
+  const int a0 = blockIdx.x * TW, b0 = (blockIdx.y - vb * ny) * G;
+  spec += (long long)vb * S * Nn * Mp;
   const int tv = min(TW, Ms - a0);
   const int nthr = blockDim.x, tid = threadIdx.x;
   const int rowlen = G * TW;
@@ -327,7 +332,7 @@ __global__ void __launch_bounds__(NC > 0 ? 256 : 512, NC > 0 ? 3 : 1) k_fft_s(cp
     __syncthreads();
   }
   if (MODE >= S_TIK_GEN && MODE <= S_FOLD) {
-    double acc = solve_tile<T, MODE, STATS, DR_, DC_, DS_>(sm, TW, G, a0, b0, Ms, sv, tid, nthr);
+    double acc = solve_tile<T, MODE, STATS, DR_, DC_, DS_>(sm, TW, G, a0, b0, Ms, sv, tid, nthr, vb);
     if (STATS) {
       double* red = reinterpret_cast<double*>(tws + (NC > 0 ? NC : 0));  // 32 slots after the tile (and twiddles)
       acc = warp_sum(acc);
@@ -390,9 +395,14 @@ __global__ void __launch_bounds__(256, 3) k_fft_s_admm_reg(float2* __restrict__ 
   const int pm = q % DR, pn = q / DR;
   const int t = gm * DR + pm;  // m-slot of the tile
   const int a0 = blockIdx.x * TW;
-  const int jl = blockIdx.y;  // LR n frequency of the tile's class row (G = DC rows)
+  // volume of a batch (sv.batch_ny tiles along n per volume, volumes one after
+  // another); the solve-order LR spectrum follows from the block index alone
+  const int ny = sv.batch_ny > 0 ? sv.batch_ny : (int)gridDim.y;
+  const int vb = blockIdx.y / ny;
+  const int jl = blockIdx.y - vb * ny;  // LR n frequency of the tile's class row (G = DC rows)
   const bool cls_ok = a0 + gm * DR < Ms;  // whole classes: Ms and TW are multiples of DR
   const long long plane = (long long)Nn * Mp;
+  spec += (long long)vb * S * plane;
   float2* col = spec + (long long)(jl + pn * nNl) * Mp + a0 + t;
   float2* line = sm + pn * TW + t;
   float2* tws = sm + S * rowlen;
@@ -416,12 +426,13 @@ __global__ void __launch_bounds__(256, 3) k_fft_s_admm_reg(float2* __restrict__ 
   const int g = cls_ok ? a0 / DR + gm : 0;
   const int km = g + pm * sv.Ml, kn = jl + pn * sv.Nl;
   const float* __restrict__ symS = reinterpret_cast<const float*>(sv.symS);
-  const float2* __restrict__ lamS = reinterpret_cast<const float2*>(sv.lamS);
+  const float2* __restrict__ lamS = reinterpret_cast<const float2*>(sv.lamS) + (long long)vb * S;
   const float sMN = __ldg(&reinterpret_cast<const float*>(sv.symM)[km]) +
                     __ldg(&reinterpret_cast<const float*>(sv.symN)[kn]);
   float2 lmn = make_float2(0.f, 0.f);
   if (sv.sep)
-    lmn = cmul(__ldg(&reinterpret_cast<const float2*>(sv.lamM)[km]), __ldg(&reinterpret_cast<const float2*>(sv.lamN)[kn]));
+    lmn = cmul(__ldg(&reinterpret_cast<const float2*>(sv.lamM)[(long long)vb * sv.M + km]),
+               __ldg(&reinterpret_cast<const float2*>(sv.lamN)[(long long)vb * sv.N + kn]));
   const long long bc = (long long)blockIdx.y * gridDim.x + blockIdx.x;
   const int ncls = GMc * sv.Sl;
   const float2* __restrict__ lamc = reinterpret_cast<const float2*>(sv.lam) + bc * D * ncls;
@@ -567,11 +578,14 @@ static cudaError_t fft_s_admm_reg(const Plan& p, const Geometry& g, void* spec, 
   const int TW = g.tw_s;
   size_t smem = (size_t)(S * TW * DC + S) * sizeof(float2);
   if (STATS) smem += 32 * sizeof(double);
-  dim3 grid((g.Ms + TW - 1) / TW, g.N / DC);
+  const int nb = sv.batch > 1 ? sv.batch : 1;
+  SolveArgs svb = sv;
+  svb.batch_ny = g.N / DC;
+  dim3 grid((g.Ms + TW - 1) / TW, (g.N / DC) * nb);
   cudaError_t e;
   if ((e = allow_smem(k_fft_s_admm_reg<S, STATS, DR, DC, DS>, smem)) != cudaSuccess) return e;
   k_fft_s_admm_reg<S, STATS, DR, DC, DS><<<grid, TW * DC * (S / 16), smem, p.stream>>>(
-      (float2*)spec, g.Ms, g.Mp, g.N, TW, sv, (const float2*)tw, g.Nl);
+      (float2*)spec, g.Ms, g.Mp, g.N, TW, svb, (const float2*)tw, g.Nl);
   return cudaGetLastError();
 }
 
@@ -596,12 +610,15 @@ static cudaError_t fft_s_k(const Plan& p, const Geometry& g, void* spec, const v
   size_t smem = (size_t)g.S * TW * G * sizeof(cplx<T>);
   if (NC > 0) smem += (size_t)NC * sizeof(cplx<T>);
   if (STATS) smem += 32 * sizeof(double);  // the CTA's reduction slots
-  dim3 grid((g.Ms + TW - 1) / TW, g.N / G);
+  const int nb = (MODE == S_ADMM && sv.batch > 1) ? sv.batch : 1;
+  SolveArgs svb = sv;
+  svb.batch_ny = g.N / G;
+  dim3 grid((g.Ms + TW - 1) / TW, (g.N / G) * nb);
   LAxis a = laxis(g.S, g.Sl, g.ds, g.fs);
   cudaError_t e;
   if ((e = allow_smem(k_fft_s<T, EMAX, MODE, STATS, NC, DR_, DC_, DS_>, smem)) != cudaSuccess) return e;
   k_fft_s<T, EMAX, MODE, STATS, NC, DR_, DC_, DS_><<<grid, TW * G * tpl, smem, p.stream>>>((cplx<T>*)spec, a, g.Ms, g.Mp, g.N, TW,
-                                                                          G, sv, (const cplx<T>*)tw, g.dc, g.Nl);
+                                                                          G, svb, (const cplx<T>*)tw, g.dc, g.Nl);
   return cudaGetLastError();
 }
 

@@ -259,7 +259,7 @@ template <int W, int MODE, bool STATS>
 __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restrict__ x, const float* __restrict__ din,
                                              float* __restrict__ dout, float* __restrict__ theta,
                                              float* __restrict__ psi, int M, int N, int S, int TS, float thr,
-                                             double* __restrict__ partial) {
+                                             double* __restrict__ partial, int zper) {
   constexpr int XR = TN + 2;  // x rows n0-1 .. n0+8
   constexpr int RR = TN + 1;  // rho / d rows n0-1 .. n0+7
   extern __shared__ __align__(16) float sm4[];
@@ -271,8 +271,15 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
   const bool halo_warp = ln == TN;
   static_assert(W == 64 || W == 96 || W == 128, "tile width");
   const bool act = W == 128 || lm < W / 4;  // lanes that own four voxels of a tile row (all at W = 128)
-  const int m0 = blockIdx.x * W, n0 = blockIdx.y * TN, s0 = blockIdx.z * TS;
   const long long V = (long long)M * N * S;
+  // volume of a batch (z blocks zper per volume, volumes one after another)
+  const int vb = blockIdx.z / zper;
+  x += vb * V;
+  din += 3 * vb * V;
+  dout += 3 * vb * V;
+  theta += vb * V;
+  psi += vb * V;
+  const int m0 = blockIdx.x * W, n0 = blockIdx.y * TN, s0 = (blockIdx.z - vb * zper) * TS;
   const long long P = (long long)M * N;
   const int s_end = min(S, s0 + TS);
   const int mc = 4 + 4 * lm;  // shared column of the thread's first voxel
@@ -608,8 +615,40 @@ static cudaError_t tv4_k(const Plan& p, const void* x, const void* din, void* do
   }
   k_tv4<W, MODE, STATS><<<grid, block, smem, p.stream>>>((const float*)x, (const float*)din, (float*)dout,
                                                    (float*)theta, (float*)psi, g.M, g.N, g.S, ts, (float)thr,
-                                                   p.partial);
+                                                   p.partial, (int)grid.z);
   return cudaGetLastError();
+}
+
+template <int W, int MODE>
+static cudaError_t tv4_batch_k(const Plan& p, int batch, const void* x, const void* din, void* dout, void* theta,
+                               double thr) {
+  const Geometry& g = p.hr;
+  const int ts = tv_ts(g);
+  const int zper = (g.S + ts - 1) / ts;
+  dim3 grid(g.M / W, g.N / TN, zper * batch);
+  dim3 block(32, TN + 1);
+  const size_t smem = tv4_smem(false);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_tv4<W, MODE, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  // theta doubles as the (unused) psi argument
+  k_tv4<W, MODE, false><<<grid, block, smem, p.stream>>>((const float*)x, (const float*)din, (float*)dout,
+                                                        (float*)theta, (float*)theta, g.M, g.N, g.S, ts, (float)thr,
+                                                        nullptr, zper);
+  return cudaGetLastError();
+}
+
+bool tv_batchable(const Plan& p) { return tv_vec4(p); }
+
+cudaError_t launch_tv_batched(const Plan& p, int batch, const void* x, const void* din, void* dout, void* theta,
+                              double thr) {
+  const int w = tv4_width(p);
+  const bool an = p.tv_aniso;
+  if (w == 128) return an ? tv4_batch_k<128, 2>(p, batch, x, din, dout, theta, thr) : tv4_batch_k<128, 0>(p, batch, x, din, dout, theta, thr);
+  if (w == 96) return an ? tv4_batch_k<96, 2>(p, batch, x, din, dout, theta, thr) : tv4_batch_k<96, 0>(p, batch, x, din, dout, theta, thr);
+  if (w == 64) return an ? tv4_batch_k<64, 2>(p, batch, x, din, dout, theta, thr) : tv4_batch_k<64, 0>(p, batch, x, din, dout, theta, thr);
+  return cudaErrorNotSupported;
 }
 
 template <int W>

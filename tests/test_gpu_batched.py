@@ -148,3 +148,84 @@ def test_schedules_leave_results_unchanged(lib, dtype, dims):
             p.schedule(**bad)
         assert p.schedule() == before
     p.close()
+
+
+# volumes that share a geometry, lambda and rho are solved as groups (one
+# launch per pass over the group's volumes); each keeps its own PSF and tau
+GROUPED = [((64, 64, 32), (2, 2, 2), 1.0, 1e-2), ((64, 64, 32), (2, 2, 2), 1.4, 3e-2),
+           ((64, 64, 32), (2, 2, 2), 0.8, 5e-3), ((96, 96, 64), (2, 2, 1), 1.2, 2e-2),
+           ((96, 96, 64), (2, 2, 1), 0.9, 1e-2), ((64, 32, 96), (2, 2, 2), 1.1, 1e-2),
+           ((64, 32, 96), (2, 2, 2), 1.6, 4e-2), ((128, 64, 64), (1, 1, 4), 1.0, 1e-2)]
+
+
+def test_grouped_volumes_equal_single_volume_solves(lib):
+    """Three groups (64x64x32 d222: 32-point s pass with the shared-tile
+    solve, 64-wide TV tiles; 96x96x64 d221: register-resident 64-point s pass,
+    96-wide TV tiles; 64x32x96 d222: 96-point s pass with the shared-tile
+    solve) and a single volume: every volume equals its
+    own single-plan solve bit for bit, on two calls (the second replays the
+    cached graph and group buffers), and a sample matches the oracle."""
+    import torch
+    plans, ys, xs, probs = [], [], [], []
+    for k, (dims, dec, sg, tau) in enumerate(GROUPED):
+        psf, xt, y = make_problem(dims, dec, sigma=(sg, 0.9 * sg, 1.1 * sg), seed=70 + k)
+        p = lib.Plan(dims, dec, psf, "f32", stream=torch.cuda.Stream())
+        assert p.separable()
+        plans.append(p)
+        ys.append(torch.tensor(y, dtype=torch.float32, device="cuda"))
+        xs.append(p.empty_hr())
+        probs.append((psf, y, dec, tau))
+    lams, rhos = [2e-3] * len(plans), [1e-2] * len(plans)
+    taus = [v[3] for v in GROUPED]
+    for rep in range(2):
+        for x in xs:
+            x.fill_(float("nan"))
+        lib.admm_tv_batched(plans, ys, xs, lams, rhos, taus, 9)
+        for k, p in enumerate(plans):
+            single = p.empty_hr()
+            p.admm_tv(ys[k], single, lams[k], rhos[k], 9, tau_init=taus[k])
+            assert torch.equal(single, xs[k]), (rep, k)
+    for k in (1, 4, 6):
+        psf, y, dec, tau = probs[k]
+        x0 = O.tikhonov(y, psf, dec, tau, O.nearest_neighbour(y, dec))
+        ref = O.admm_tv(y, psf, dec, lams[k], rhos[k], 9, x0)["x"]
+        assert rel_l2(xs[k].cpu().numpy(), ref) < 1e-5, k
+    for p in plans:
+        p.close()
+
+
+@pytest.mark.slow
+def test_full_ragged_batch_against_single_solves(lib):
+    """The 64-volume ragged draw of the batch benchmark (sizes 64^3,
+    96x96x64, 128^3, 128x128x96; d in 2x2x2, 2x2x1, 1x1x4; tau log-uniform,
+    sigma uniform; 50 iterations) on seeded smooth observations: every volume
+    equals its single-plan solve bit for bit, and three small volumes match
+    the oracle."""
+    import torch
+    import synth
+    ws = synth.batch_workloads()
+    plans, ys, xs, yh = [], [], [], []
+    for w in ws:
+        p = lib.Plan(w.dims, w.dec, w.psf(), "f32", stream=torch.cuda.Stream())
+        p.autotune(2)
+        m, n, s = w.lr_dims
+        y = 0.5 + 0.1 * synth.normal(w.seed, 5, m * n * s).reshape((s, n, m))
+        yh.append(y)
+        plans.append(p)
+        ys.append(torch.tensor(y, dtype=torch.float32, device="cuda"))
+        xs.append(p.empty_hr())
+    lams, rhos, taus = [w.lam for w in ws], [w.mu for w in ws], [w.tau for w in ws]
+    lib.admm_tv_batched(plans, ys, xs, lams, rhos, taus, ws[0].iters)
+    for k, p in enumerate(plans):
+        single = p.empty_hr()
+        p.admm_tv(ys[k], single, lams[k], rhos[k], ws[k].iters, tau_init=taus[k])
+        assert torch.equal(single, xs[k]), k
+    small = [k for k, w in enumerate(ws) if w.dims == (64, 64, 64)][:3]
+    for k in small:
+        w = ws[k]
+        psf = w.psf()
+        x0 = O.tikhonov(yh[k], psf, w.dec, w.tau, O.nearest_neighbour(yh[k], w.dec))
+        ref = O.admm_tv(yh[k], psf, w.dec, w.lam, w.mu, w.iters, x0)["x"]
+        assert rel_l2(xs[k].cpu().numpy(), ref) < 1e-5, k
+    for p in plans:
+        p.close()
