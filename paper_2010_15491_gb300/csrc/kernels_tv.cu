@@ -272,8 +272,9 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
   static_assert(W == 64 || W == 96 || W == 128, "tile width");
   const bool act = W == 128 || lm < W / 4;  // lanes that own four voxels of a tile row (all at W = 128)
   const long long V = (long long)M * N * S;
-  // volume of a batch (z blocks zper per volume, volumes one after another)
-  const int vb = blockIdx.z / zper;
+  // volume of a batch (z blocks zper per volume, volumes one after another;
+  // the statistics variants are never batched)
+  const int vb = STATS ? 0 : (int)(blockIdx.z / zper);
   x += vb * V;
   din += 3 * vb * V;
   dout += 3 * vb * V;
@@ -352,7 +353,7 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
 
     // one voxel of the rho region: shrink, dual, rho into shared row rr, column cc
     auto voxel = [&](int rr, int cc, float g0, float g1, float g2, float d0, float d1, float d2, float& u0,
-                     float& u1, float& u2, float& e0, float& e1, float& e2) {
+                     float& u1, float& u2, float& e0, float& e1, float& e2, bool store) {
       if (MODE == 1) {
         u0 = g0; u1 = g1; u2 = g2;
         e0 = d0; e1 = d1; e2 = d2;
@@ -367,6 +368,7 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
         u0 = v0 * sc; u1 = v1 * sc; u2 = v2 * sc;
         e0 = v0 - u0; e1 = v1 - u1; e2 = v2 - u2;
       }
+      if (!store) return;
       const int i = rr * V4W + cc;
       if (STATS) {
         rs[0 * RP + i] = u0; rs[1 * RP + i] = u1; rs[2 * RP + i] = u2;
@@ -375,16 +377,26 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
         rs[0 * RP + i] = u0 - e0; rs[1 * RP + i] = u1 - e1; rs[2 * RP + i] = u2 - e2;
       }
     };
+    // lanes of a tile row (all 32 at W = 128); the right x neighbour of a
+    // thread's last voxel and the left rho neighbour of its first are the
+    // next / previous lane's (shuffles instead of strided shared loads)
+    const unsigned amask = W == 128 ? 0xffffffffu : ((1u << (W / 4)) - 1u);
     // four voxels of shared row xr (x rows xr, xr+1; rho / d row xr), columns mc..mc+3
     auto quad = [&](int xr, bool interior) {
       const float4 a = lds4(xc + xr * V4W + mc);
-      const float a4 = xc[xr * V4W + mc + 4];
+      float a4;
+      if (STATS) {
+        a4 = xc[xr * V4W + mc + 4];  // (registers of the statistics variants at their limit)
+      } else {
+        a4 = __shfl_down_sync(amask, a.x, 1);
+        if (lm == W / 4 - 1) a4 = xc[xr * V4W + mc + 4];  // halo column m0 + W
+      }
       const float4 b = lds4(xc + (xr + 1) * V4W + mc);
       const float4 c = lds4(xn + xr * V4W + mc);
       const float4 dv0 = lds4(dd + 0 * RP + xr * V4W + mc);
       const float4 dv1 = lds4(dd + 1 * RP + xr * V4W + mc);
       const float4 dv2 = lds4(dd + 2 * RP + xr * V4W + mc);
-      float e0v[4], e1v[4], e2v[4];
+      float e0v[4], e1v[4], e2v[4], u0v[4], u1v[4], u2v[4];
       float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;  // the quad's partial sums (FP32, 4 terms)
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -393,7 +405,13 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
         const float g1 = f4(b, i) - xv;
         const float g2 = f4(c, i) - xv;
         float u0, u1, u2;
-        voxel(xr, mc + i, g0, g1, g2, f4(dv0, i), f4(dv1, i), f4(dv2, i), u0, u1, u2, e0v[i], e1v[i], e2v[i]);
+        // the statistics variants (six values per voxel, registers at their
+        // limit) store each voxel as it is formed; the step variants store
+        // the quad below
+        voxel(xr, mc + i, g0, g1, g2, f4(dv0, i), f4(dv1, i), f4(dv2, i), u0, u1, u2, e0v[i], e1v[i], e2v[i], STATS);
+        u0v[i] = u0;
+        u1v[i] = u1;
+        u2v[i] = u2;
         if (STATS && interior && own_plane) {
           const float gg = g0 * g0 + g1 * g1 + g2 * g2;
           f0 += MODE == 2 ? fabsf(g0) + fabsf(g1) + fabsf(g2) : sqrtf(gg);
@@ -402,6 +420,15 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
           f2 += gg;
           f3 += u0 * u0 + u1 * u1 + u2 * u2;
         }
+      }
+      // the quad's rho as one 16-byte store per component (conflict-free,
+      // where four scalar stores per component at a four-float lane stride
+      // were four-way bank conflicts)
+      if (!STATS) {
+        float* r = rs + xr * V4W + mc;
+        st4(r + 0 * RP, make_float4(u0v[0] - e0v[0], u0v[1] - e0v[1], u0v[2] - e0v[2], u0v[3] - e0v[3]));
+        st4(r + 1 * RP, make_float4(u1v[0] - e1v[0], u1v[1] - e1v[1], u1v[2] - e1v[2], u1v[3] - e1v[3]));
+        st4(r + 2 * RP, make_float4(u2v[0] - e2v[0], u2v[1] - e2v[1], u2v[2] - e2v[2], u2v[3] - e2v[3]));
       }
       if (STATS && interior && own_plane) {
         kadd(0, f0);
@@ -427,7 +454,7 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
       float u0, u1, u2, e0, e1, e2;
       voxel(xr, 3, xc[xr * V4W + 4] - xv, xc[(xr + 1) * V4W + 3] - xv, xn[xr * V4W + 3] - xv,
             dd[0 * RP + xr * V4W + 3], dd[1 * RP + xr * V4W + 3], dd[2 * RP + xr * V4W + 3], u0, u1, u2, e0, e1,
-            e2);
+            e2, true);
     }
     __syncthreads();
     // phase 2: Theta = L^T rho for the four interior voxels (tile warps)
@@ -436,7 +463,7 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
       const int up = ln * V4W + mc;
       float4 own0, own1, own2, up1;
       float4 u_0, u_1, u_2, e_0, e_1, e_2, uup1, eup1;
-      float left0;
+      float left0, ul = 0.f, el = 0.f;
       if (STATS) {
         u_0 = lds4(rs + 0 * RP + row); u_1 = lds4(rs + 1 * RP + row); u_2 = lds4(rs + 2 * RP + row);
         e_0 = lds4(rs + 3 * RP + row); e_1 = lds4(rs + 4 * RP + row); e_2 = lds4(rs + 5 * RP + row);
@@ -445,11 +472,14 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
         own1 = make_float4(u_1.x - e_1.x, u_1.y - e_1.y, u_1.z - e_1.z, u_1.w - e_1.w);
         own2 = make_float4(u_2.x - e_2.x, u_2.y - e_2.y, u_2.z - e_2.z, u_2.w - e_2.w);
         up1 = make_float4(uup1.x - eup1.x, uup1.y - eup1.y, uup1.z - eup1.z, uup1.w - eup1.w);
-        left0 = rs[0 * RP + row - 1] - rs[3 * RP + row - 1];
+        ul = rs[0 * RP + row - 1];
+        el = rs[3 * RP + row - 1];
+        left0 = ul - el;
       } else {
         own0 = lds4(rs + 0 * RP + row); own1 = lds4(rs + 1 * RP + row); own2 = lds4(rs + 2 * RP + row);
         up1 = lds4(rs + 1 * RP + up);
-        left0 = rs[0 * RP + row - 1];
+        left0 = __shfl_up_sync(amask, own0.w, 1);
+        if (lm == 0) left0 = rs[0 * RP + row - 1];  // halo column m0 - 1
       }
       if (own_plane) {
         float th[4];
@@ -461,7 +491,6 @@ __global__ void __launch_bounds__(32 * (TN + 1), 3) k_tv4(const float* __restric
         const long long gi = pl + o_in;
         st4(theta + gi, make_float4(th[0], th[1], th[2], th[3]));
         if (STATS) {
-          const float ul = rs[0 * RP + row - 1], el = rs[3 * RP + row - 1];
           float pv[4];
           float f5 = 0.f;
 #pragma unroll
