@@ -199,7 +199,10 @@ static void free_plan(Plan& p) {
   if (p.iter_graph) cudaGraphExecDestroy(p.iter_graph);
   for (auto& g : p.eval_graph)
     if (g) cudaGraphExecDestroy(g);
+  for (auto& g : p.tol_graph)
+    if (g) cudaGraphExecDestroy(g);
   if (p.hcount) cudaFree(p.hcount);
+  if (p.tolctl) cudaFree(p.tolctl);
   if (p.res_host) cudaFreeHost(p.res_host);
   if (p.own_stream && p.stream) cudaStreamDestroy(p.stream);
   for (int i = 0; i < 2 * p.prof_cap; ++i) cudaEventDestroy(p.prof_ev[i]);
@@ -403,19 +406,20 @@ static int admm_iteration(Plan& p, void* x, const void* din, void* dout, double 
 }
 
 static void drop_eval_graphs(Plan& p) {
-  for (auto& g : p.eval_graph)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  for (cudaGraphExec_t* gs : {p.eval_graph, p.tol_graph})
+    for (int i = 0; i < 2; ++i)
+      if (gs[i]) {
+        cudaGraphExecDestroy(gs[i]);
+        gs[i] = nullptr;
+      }
 }
 
 // One evaluation block: iterations 1..every, statistics kernels in the last
 // two (the dual residual needs L^T u of the iteration before), the finalize
-// (objective history indexed on the device) and the copy of its results to
-// pinned host memory.  d0 -> d1 -> d0 ... through the block.
+// (objective history indexed on the device) and, when to_host, the copy of
+// its results to pinned host memory.  d0 -> d1 -> d0 ... through the block.
 static int admm_eval_block(Plan& p, void* x, void* d0, void* d1, double thr, double rho, double lambda,
-                           int every) {
+                           int every, bool to_host = true) {
   void* a = d0;
   void* b = d1;
   for (int j = 1; j <= every; ++j) {
@@ -428,15 +432,14 @@ static int admm_eval_block(Plan& p, void* x, void* d0, void* d1, double thr, dou
     b = t;
   }
   LAUNCH(SR3D_K_OTHER, launch_finalize(p, -2, lambda, rho, 1.0 / (double)p.lr.V(), true));
-  CK(cudaMemcpyAsync(p.res_host, p.result, 11 * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+  if (to_host) CK(cudaMemcpyAsync(p.res_host, p.result, 11 * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
   return SR3D_OK;
 }
 
-// Replays the evaluation block whose dual buffers start as (d0, d1),
-// capturing it first when buffers or parameters changed.  par selects the
-// cached graph (0: first buffer order seen, 1: the swapped order).
-static int admm_eval_block_graph(Plan& p, void* x, void* d0, void* d1, double thr, double rho, double lambda,
-                                 int every, int par) {
+// Keys the cached evaluation-block and tolerance-loop graphs: drops them
+// when the buffers or parameters they were captured with changed.
+static void key_eval_graphs(Plan& p, void* x, void* d0, void* d1, double thr, double rho, double lambda, int every,
+                            int par) {
   if (p.eg_x != x || p.eg_thr != thr || p.eg_rho != rho || p.eg_lam != lambda || p.eg_every != every ||
       p.eg_hist != p.hist || p.eg_partial != p.partial || p.eg_d[par] != d0 || p.eg_d[1 - par] != d1) {
     drop_eval_graphs(p);
@@ -444,6 +447,14 @@ static int admm_eval_block_graph(Plan& p, void* x, void* d0, void* d1, double th
     p.eg_hist = p.hist; p.eg_partial = p.partial;
     p.eg_d[par] = d0; p.eg_d[1 - par] = d1;
   }
+}
+
+// Replays the evaluation block whose dual buffers start as (d0, d1),
+// capturing it first when buffers or parameters changed.  par selects the
+// cached graph (0: first buffer order seen, 1: the swapped order).
+static int admm_eval_block_graph(Plan& p, void* x, void* d0, void* d1, double thr, double rho, double lambda,
+                                 int every, int par) {
+  key_eval_graphs(p, x, d0, d1, thr, rho, lambda, every, par);
   cudaGraphExec_t& ge = p.eval_graph[par];
   if (!ge) {
     long long before[8];
@@ -470,6 +481,111 @@ static int admm_eval_block_graph(Plan& p, void* x, void* d0, void* d1, double th
   }
   CK(cudaGraphLaunch(ge, p.stream));
   for (int k = 0; k < 8; ++k) p.launches[k] += p.eg_launches[par][k];
+  return SR3D_OK;
+}
+
+// Captures work() on the plan's stream into g, an existing graph (a
+// conditional node's body or the loop graph itself); *last, when given,
+// receives the one node the captured work ends on.
+template <class F>
+static int capture_to(Plan& p, cudaGraph_t g, F&& work, cudaGraphNode_t* last) {
+  CK(cudaStreamBeginCaptureToGraph(p.stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int rc = work();
+  if (rc == SR3D_OK && last) {
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    const cudaError_t e = cudaStreamGetCaptureInfo(p.stream, &st, nullptr, nullptr, &deps, nullptr, &nd);
+    if (e != cudaSuccess || nd != 1 || !deps)
+      rc = fail(SR3D_ERR_CUDA, "graph capture: the captured work does not end on one node");
+    else
+      *last = deps[0];
+  }
+  cudaGraph_t out = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(p.stream, &out);
+  if (rc != SR3D_OK) return rc;
+  if (ec != cudaSuccess) return fail(SR3D_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+  return SR3D_OK;
+}
+
+// Adds a conditional node of the given type after dep; *body receives the
+// graph it runs (owned by the node).
+static int add_conditional(cudaGraph_t g, cudaGraphNode_t dep, cudaGraphConditionalHandle h,
+                           cudaGraphConditionalNodeType type, cudaGraph_t* body) {
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = type;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node;
+  CK(cudaGraphAddNode(&node, g, &dep, nullptr, 1, &cp));
+  *body = cp.conditional.phGraph_out[0];
+  return SR3D_OK;
+}
+
+// The tolerance loop of Algorithm 1 as one graph, replayed without the host
+// between blocks: a gate (k_tol_gate) on the evaluation made before it, then
+// a WHILE node whose body runs one evaluation block and the gate again.
+// For odd `every` a block swaps the dual buffers, so the body holds two
+// blocks, the second under an IF node set by the first block's gate, and
+// leaves the buffers in the order it found them.  The caller has written
+// p.tolctl (blocks = 0, the block budget, tol) and p.hcount.
+static int admm_tol_graph(Plan& p, void* x, void* d0, void* d1, double thr, double rho, double lambda, int every,
+                          int par) {
+  key_eval_graphs(p, x, d0, d1, thr, rho, lambda, every, par);
+  cudaGraphExec_t& ge = p.tol_graph[par];
+  if (!ge) {
+    long long base[8], mark[8];
+    for (int k = 0; k < 8; ++k) base[k] = mark[k] = p.launches[k];
+    auto counted = [&](long long* out) {
+      for (int k = 0; k < 8; ++k) {
+        out[k] = p.launches[k] - mark[k];
+        mark[k] = p.launches[k];
+      }
+    };
+    cudaGraph_t g = nullptr;
+    CK(cudaGraphCreate(&g, 0));
+    struct Owner {
+      cudaGraph_t g;
+      ~Owner() { cudaGraphDestroy(g); }
+    } owner{g};
+    cudaGraphConditionalHandle loop;
+    CK(cudaGraphConditionalHandleCreate(&loop, g, 0, 0));
+    cudaGraphNode_t gate = nullptr;
+    TRY(capture_to(p, g, [&]() -> int {
+      LAUNCH(SR3D_K_OTHER, launch_tol_gate(p, 0, loop, loop, false));
+      return SR3D_OK;
+    }, &gate));
+    counted(p.tg_first[par]);
+    cudaGraph_t body = nullptr;
+    TRY(add_conditional(g, gate, loop, cudaGraphCondTypeWhile, &body));
+    const bool two = (every & 1) != 0;
+    cudaGraphConditionalHandle next = 0;
+    if (two) CK(cudaGraphConditionalHandleCreate(&next, body, 0, 0));
+    cudaGraphNode_t end_a = nullptr;
+    TRY(capture_to(p, body, [&]() -> int {
+      TRY(admm_eval_block(p, x, d0, d1, thr, rho, lambda, every, false));
+      LAUNCH(SR3D_K_OTHER, launch_tol_gate(p, 1, loop, next, two));
+      return SR3D_OK;
+    }, two ? &end_a : nullptr));
+    counted(p.tg_block[par]);
+    if (two) {
+      cudaGraph_t second = nullptr;
+      TRY(add_conditional(body, end_a, next, cudaGraphCondTypeIf, &second));
+      TRY(capture_to(p, second, [&]() -> int {
+        TRY(admm_eval_block(p, x, d1, d0, thr, rho, lambda, every, false));
+        LAUNCH(SR3D_K_OTHER, launch_tol_gate(p, 1, loop, loop, false));
+        return SR3D_OK;
+      }, nullptr));
+    }
+    for (int k = 0; k < 8; ++k) p.launches[k] = base[k];
+    const cudaError_t ec = cudaGraphInstantiate(&ge, g, 0);
+    if (ec != cudaSuccess) {
+      ge = nullptr;
+      return fail(SR3D_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+    }
+  }
+  CK(cudaGraphLaunch(ge, p.stream));
   return SR3D_OK;
 }
 
@@ -1011,16 +1127,47 @@ int sr3d_admm_tv(sr3d_plan_t plan, const void* y, void* x, void* d_dev, double l
     if (it < max_iters) TRY(eager());
   }
   // with statistics: after the first evaluation (all kernels loaded), whole
-  // evaluation blocks run as replayed graphs; tol > 0 waits for each block's
-  // residuals, otherwise the blocks are queued back to back
+  // evaluation blocks run as replayed graphs.  With tol > 0 one graph loops
+  // over the blocks and makes the stopping test on the device (the host waits
+  // once, after it); without, the blocks are queued back to back.
   const bool block_graphs = want_stats && every >= 1 && !p.prof_on && p.stream != nullptr;
+  const bool dev_loop = block_graphs && tol > 0;
   if (block_graphs) {
     if (!p.hcount) TRY(dmalloc(p, (void**)&p.hcount, sizeof(int)));
     if (!p.res_host) CK(cudaHostAlloc((void**)&p.res_host, 16 * sizeof(double), cudaHostAllocDefault));
   }
+  if (dev_loop && !p.tolctl) TRY(dmalloc(p, (void**)&p.tolctl, sizeof(TolCtl)));
   void* const d_first = dcur;
   for (int k = it + 1; k <= max_iters; ++k) {
-    if (block_graphs && evals > 0 && (k - 1) % every == 0 && k - 1 + every <= max_iters) {
+    if (dev_loop && evals > 0 && (k - 1) % every == 0 && k - 1 + every <= max_iters) {
+      const TolCtl c = {0, (max_iters - (k - 1)) / every, tol};
+      CK(cudaMemcpyAsync(p.tolctl, &c, sizeof c, cudaMemcpyHostToDevice, p.stream));
+      CK(cudaMemcpyAsync(p.hcount, &evals, sizeof(int), cudaMemcpyHostToDevice, p.stream));
+      const int par = dcur == d_first ? 0 : 1;
+      TRY(admm_tol_graph(p, x, dcur, dnext, thr, rho, lambda, every, par));
+      int* const blocks_host = reinterpret_cast<int*>(p.res_host + 12);
+      CK(cudaMemcpyAsync(p.res_host, p.result, 11 * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
+      CK(cudaMemcpyAsync(blocks_host, &p.tolctl->blocks, sizeof(int), cudaMemcpyDeviceToHost, p.stream));
+      TRY(sync_plan(p));
+      const int b = *blocks_host;
+      for (int j = 0; j < 8; ++j) p.launches[j] += p.tg_first[par][j] + b * p.tg_block[par][j];
+      evals += b;
+      it = k - 1 + b * every;
+      k = it;
+      if ((every & 1) && (b & 1)) {
+        void* t = dcur;
+        dcur = dnext;
+        dnext = t;
+      }
+      memcpy(res, p.res_host, 11 * sizeof(double));
+      if (res[10] != 0.0) return fail(SR3D_ERR_NUMERIC, "NaN/Inf in the objective or residuals at iteration %d", it);
+      if (res[8] < tol && res[9] < tol) {
+        converged = true;
+        break;
+      }
+      continue;  // the block budget is spent: the iterations left run below
+    }
+    if (block_graphs && !dev_loop && evals > 0 && (k - 1) % every == 0 && k - 1 + every <= max_iters) {
       CK(cudaMemcpyAsync(p.hcount, &evals, sizeof(int), cudaMemcpyHostToDevice, p.stream));
       const int par = dcur == d_first ? 0 : 1;
       TRY(admm_eval_block_graph(p, x, dcur, dnext, thr, rho, lambda, every, par));
@@ -1054,7 +1201,8 @@ int sr3d_admm_tv(sr3d_plan_t plan, const void* y, void* x, void* d_dev, double l
     if (eval_now) {
       LAUNCH(SR3D_K_OTHER, launch_finalize(p, evals < p.hist_cap ? evals : -1, lambda, rho, 1.0 / (double)p.lr.V(), true));
       ++evals;
-      if (tol > 0) {
+      // ahead of the device loop its first gate makes this evaluation's test
+      if (tol > 0 && !(dev_loop && k % every == 0 && k + every <= max_iters)) {
         CK(cudaMemcpyAsync(res, p.result, 11 * sizeof(double), cudaMemcpyDeviceToHost, p.stream));
         TRY(sync_plan(p));
         if (res[10] != 0.0) return fail(SR3D_ERR_NUMERIC, "NaN/Inf in the objective or residuals at iteration %d", k);

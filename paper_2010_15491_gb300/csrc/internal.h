@@ -69,6 +69,13 @@ struct Geometry {
   long long spec_elems() const { return (long long)S * N * Mp; }
 };
 
+// Device state of the tolerance loop of sr3d_admm_tv (Algorithm 1, step 5).
+struct TolCtl {
+  int blocks;      // evaluation blocks the loop has run
+  int max_blocks;  // blocks that fit in the iteration budget
+  double tol;      // stop once primal_rel < tol and dual_rel < tol
+};
+
 struct Plan {
   int dtype;     // 0 float, 1 double
   size_t esz;    // element size
@@ -133,6 +140,13 @@ struct Plan {
   int eg_every = 0;
   long long eg_launches[2][8] = {};
   int* hcount = nullptr;       // device: objective-history entries written by graph replays
+  // graphs of the device-side tolerance loop (a WHILE node over evaluation
+  // blocks), one per dual-buffer parity, keyed like eval_graph; the launches
+  // of the gate ahead of the loop and of one block (its gate included)
+  cudaGraphExec_t tol_graph[2] = {nullptr, nullptr};
+  long long tg_first[2][8] = {};
+  long long tg_block[2][8] = {};
+  struct TolCtl* tolctl = nullptr;  // device state of that loop
   // conjugate-gradient comparator (sr3d_tikhonov_cg): r, p, Ap, a temporary,
   // per-CTA FP64 partial sums and the scalars rr, pAp, rr_new
   void* cg_buf[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -170,6 +184,10 @@ int tv_default_ts(const Geometry& g);
 int tv_ts_candidates(const Plan& p, int* out, int cap);
 cudaError_t launch_finalize(const Plan& p, int hist_index, double lam_tv, double mu, double inv_nl,
                             bool with_data);
+// The stopping test of Algorithm 1 (step 5) made on the device for the
+// graph loop of sr3d_admm_tv; see k_tol_gate.
+cudaError_t launch_tol_gate(const Plan& p, int count, cudaGraphConditionalHandle loop,
+                            cudaGraphConditionalHandle next, bool has_next);
 cudaError_t launch_twiddle(const Plan& p, void* tw, int n);
 cudaError_t launch_symbol(const Plan& p, void* sym, int n);
 cudaError_t launch_wrap_psf(const Plan& p, void* out, const double* psf_dev, int pm, int pn, int ps);

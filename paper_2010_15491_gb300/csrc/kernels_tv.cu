@@ -771,6 +771,28 @@ __global__ void k_finalize(const double* __restrict__ ptv, long long ntv, const 
   }
 }
 
+// The stopping test of Algorithm 1 (step 5), made on the device so that a
+// graph can loop over evaluation blocks without the host: after the
+// evaluation in res (k_finalize's output) the loop goes on while a relative
+// residual is at or above tol, nothing is NaN/Inf and blocks are left.
+// count = 0 for the gate ahead of the loop, 1 after a block.  When has_next,
+// the condition of the second block of a two-block body gets the same value.
+__global__ void k_tol_gate(const double* __restrict__ res, TolCtl* __restrict__ c, int count,
+                           cudaGraphConditionalHandle loop, cudaGraphConditionalHandle next, int has_next) {
+  const int b = c->blocks + count;
+  c->blocks = b;
+  const bool converged = res[8] < c->tol && res[9] < c->tol;
+  const unsigned go = (res[10] == 0.0 && !converged && b < c->max_blocks) ? 1u : 0u;
+  cudaGraphSetConditional(loop, go);
+  if (has_next) cudaGraphSetConditional(next, go);
+}
+
+cudaError_t launch_tol_gate(const Plan& p, int count, cudaGraphConditionalHandle loop,
+                            cudaGraphConditionalHandle next, bool has_next) {
+  k_tol_gate<<<1, 1, 0, p.stream>>>(p.result, p.tolctl, count, loop, next, has_next ? 1 : 0);
+  return cudaGetLastError();
+}
+
 // number of CTAs (and partial-sum rows) of the TV variant the plan launches
 static long long tv_launch_blocks(const Plan& p) {
   const Geometry& g = p.hr;

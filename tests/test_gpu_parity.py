@@ -284,6 +284,54 @@ def test_statistics_blocks_replayed_as_graphs_match_eager(lib, every, dtype):
     plan.close()
 
 
+@pytest.mark.parametrize("every", [2, 3])
+def test_device_tolerance_loop_edges_match_eager(lib, every):
+    """With tol > 0 one graph loops over the evaluation blocks and makes the
+    stopping test (Algorithm 1, step 5) on the device.  Its edges against the
+    eager, host-tested path, bit for bit: a tolerance met at the first
+    evaluation (the loop runs no block), a budget spent without convergence
+    with iterations left over after the last whole block, and the same run
+    repeated (the cached graph, the history index reset).  Launch accounting:
+    the same kernels of every kind but "other", where the device loop adds
+    one gate ahead of the loop and one per block."""
+    import torch
+    dims, dec = (128, 32, 16), (2, 2, 1)
+    psf, xt, y = make_problem(dims, dec, seed=33)
+    plan = lib.Plan(dims, dec, psf, "f64")
+    yd = T(y, "f64")
+    cases = [(1.0, 40), (1e-14, 4 * every + 1), (1e-14, 4 * every + 1)]
+    runs = []
+    for prof in (False, True):
+        out = []
+        for tol, iters in cases:
+            plan.profile(prof)
+            x = plan.empty_hr()
+            d = torch.zeros((3,) + plan.hr_shape, dtype=plan.tdtype, device="cuda")
+            st = plan.admm_tv(yd, x, 2e-3, 1e-2, iters, d=d, tol=tol, tau_init=1e-2, eval_every=every, hist_len=64)
+            out.append((x, d, st, plan.profile_read()))
+        runs.append(out)
+    plan.profile(False)
+    for (xa, da, sa, na), (xb, db, sb, nb), (tol, iters) in zip(runs[0], runs[1], cases):
+        assert torch.equal(xa, xb) and torch.equal(da, db), (tol, iters)
+        for k in ("iters", "evals", "converged", "objective", "primal_rel", "dual_rel", "objective_hist"):
+            assert sa[k] == sb[k], (k, tol, iters)
+        for kind in na:
+            if kind != "other":
+                assert na[kind][1] == nb[kind][1], (kind, na[kind], nb[kind])
+        if tol == 1.0:
+            assert sa["converged"] and sa["iters"] == every and sa["evals"] == 1
+            assert na["other"][1] == nb["other"][1] + 1  # the gate ahead of the loop only
+        else:
+            assert not sa["converged"] and sa["iters"] == iters and sa["evals"] == 5
+            assert na["other"][1] == nb["other"][1] + 1 + 3  # the first block is eager: 3 loop blocks
+    x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
+    ref = O.admm_tv(y, psf, dec, 2e-3, 1e-2, 4 * every + 1, x0, record=True)
+    assert rel_l2(H(runs[0][1][0]), ref["x"]) < TOL["f64"]
+    its = [every * j for j in range(1, 5)] + [4 * every + 1]
+    assert np.allclose(runs[0][1][2]["objective_hist"], [ref["hist"]["objective"][k - 1] for k in its], rtol=1e-12)
+    plan.close()
+
+
 def _separable_asym_psf(shape, seed):
     """Outer product of three asymmetric positive 1-D factors (complex Lambda)."""
     rng = np.random.default_rng(seed)
