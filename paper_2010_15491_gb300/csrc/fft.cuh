@@ -7,8 +7,9 @@
 // shared footprint is one tile.  The first stage reads its inputs straight
 // from global memory (all e loads of a thread in flight at once) and the last
 // stage writes straight to global memory, so a two-stage length such as
-// 256 = 16 x 16 crosses shared memory once.  Radices 2, 3, 4, 8 and 16 cover every length
-// 2^a and 3 * 2^a.  The transform is the unnormalised forward DFT
+// 256 = 16 x 16 crosses shared memory once.  Radices 2, 3, 4, 8 and 16 cover
+// every length 2^a and 3 * 2^a (radix 6 serves the compile-time plans of
+// fft_ct.cuh).  The transform is the unnormalised forward DFT
 // X[k] = sum_j x[j] exp(-2 pi i j k / n); inverses conjugate on the way in
 // and out.  Butterfly constants are the exact values cos(2 pi j / 16),
 // sin(2 pi j / 16) and sqrt(3)/2 written as decimal literals.
@@ -49,6 +50,26 @@ template <typename C, typename T> struct Dft<4, C, T> {
     v[2] = a0 - a2;
     v[1] = a1 + a3;
     v[3] = a1 - a3;
+  }
+};
+
+// 6 = 2 x 3: length-3 transforms of the even and odd inputs, the odd ones
+// turned by exp(-2 pi i k / 6), then X[k] = A[k] + B[k], X[k + 3] = A[k] - B[k].
+template <typename C, typename T> struct Dft<6, C, T> {
+  __device__ __forceinline__ static void run(C* v) {
+    const T k = (T)0.86602540378443864676;  // sqrt(3)/2
+    C a[3] = {v[0], v[2], v[4]};
+    C b[3] = {v[1], v[3], v[5]};
+    Dft<3, C, T>::run(a);
+    Dft<3, C, T>::run(b);
+    const C b1 = mkc((T)0.5 * b[1].x + k * b[1].y, (T)0.5 * b[1].y - k * b[1].x);    // * exp(-i pi/3)
+    const C b2 = mkc((T)-0.5 * b[2].x + k * b[2].y, (T)-0.5 * b[2].y - k * b[2].x);  // * exp(-2 i pi/3)
+    v[0] = a[0] + b[0];
+    v[3] = a[0] - b[0];
+    v[1] = a[1] + b1;
+    v[4] = a[1] - b1;
+    v[2] = a[2] + b2;
+    v[5] = a[2] - b2;
   }
 };
 

@@ -1,26 +1,33 @@
-// Compile-time-planned FFT lines for the hot power-of-two lengths (FP32).
+// Compile-time-planned FFT lines for the hot lengths (FP32).
 //
-// Same Stockham formulation as fft.cuh, but the length N, the radices
-// ([N / 16^a, 16, ..., 16]), the threads per line (N / 16) and every index
-// are compile-time constants, so there are no runtime divisions or
-// predicated stage loops, and twiddles come from a shared-memory table.
-// A thread owns 16 elements per stage; the first stage loads them straight
-// from global memory and the last stage stores straight to global memory.
+// Same Stockham formulation as fft.cuh, but the length N, the radices, the
+// threads per line and every index are compile-time constants, so there are
+// no runtime divisions or predicated stage loops, and twiddles come from a
+// shared-memory table.  A thread owns E elements per stage: E = 16 for
+// N = 2^a (radices [N / 16^b, 16, ..., 16]) and E = 12 for N = 3 * 2^a
+// (radices [3 or 6, 4, ..., 4]); N / E threads per line.  The first stage
+// loads straight from global memory and the last stage stores straight to
+// global memory.
 #pragma once
 #include "fft.cuh"
 
 namespace sr3d {
 
-constexpr int ct_rem(int n) { return n % 16 == 0 ? ct_rem(n / 16) : n; }
-constexpr int ct_big(int n) { return n % 16 == 0 ? 1 + ct_big(n / 16) : 0; }
-constexpr int ct_nst(int n) { return ct_big(n) + (ct_rem(n) > 1 ? 1 : 0); }
+constexpr int ct_e(int n) { return n % 3 == 0 ? 12 : 16; }
+constexpr int ct_rem(int n, int p) { return n % p == 0 ? ct_rem(n / p, p) : n; }
+constexpr int ct_big(int n, int p) { return n % p == 0 ? 1 + ct_big(n / p, p) : 0; }
+constexpr int ct_nst(int n) {
+  return ct_e(n) == 16 ? ct_big(n, 16) + (ct_rem(n, 16) > 1 ? 1 : 0) : ct_big(n, 4) + 1;
+}
 // radix of stage i
-constexpr int ct_radix(int n, int i) { return (ct_rem(n) > 1 && i == 0) ? ct_rem(n) : 16; }
+constexpr int ct_radix(int n, int i) {
+  return ct_e(n) == 16 ? ((ct_rem(n, 16) > 1 && i == 0) ? ct_rem(n, 16) : 16) : (i == 0 ? ct_rem(n, 4) : 4);
+}
 // product of the radices before stage i
 constexpr int ct_ns(int n, int i) { return i == 0 ? 1 : ct_ns(n, i - 1) * ct_radix(n, i - 1); }
 
 template <int N> __host__ __device__ constexpr bool ct_supported() {
-  return N == 32 || N == 64 || N == 128 || N == 256 || N == 512;
+  return N == 32 || N == 64 || N == 128 || N == 256 || N == 512 || N == 48 || N == 96 || N == 192;
 }
 
 // Shared-memory position of line element i: with PAD one spare slot follows
@@ -39,17 +46,18 @@ template <bool PAD> __host__ __device__ constexpr int ct_line_pitch(int n) {
 template <int N, int I, bool FIRST, bool LAST, bool PAD, class Ld, class St>
 __device__ __forceinline__ void ct_stage(const Ld& ld, const St& st, float2* line, int es, int tl,
                                          const float2* __restrict__ tws, int twstep) {
+  constexpr int E = ct_e(N);
   constexpr int R = ct_radix(N, I);
   constexpr int NS = ct_ns(N, I);
-  constexpr int TPL = N / 16;
-  constexpr int NB = 16 / R;
+  constexpr int TPL = N / E;
+  constexpr int NB = E / R;
   constexpr int NR = N / R;
   constexpr int STEP = N / (NS * R);
-  float2 v[16];
+  float2 v[E];
 #pragma unroll
   for (int u = 0; u < NB; ++u) {
     const int j = tl + u * TPL;
-    const int jm = j & (NS - 1);
+    const int jm = j % NS;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       float2 a;
@@ -66,7 +74,7 @@ __device__ __forceinline__ void ct_stage(const Ld& ld, const St& st, float2* lin
   for (int u = 0; u < NB; ++u) {
     Dft<R, float2, float>::run(&v[u * R]);
     const int j = tl + u * TPL;
-    const int jm = j & (NS - 1);
+    const int jm = j % NS;
     const int base = (j - jm) * R + jm;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -103,6 +111,50 @@ __device__ __forceinline__ void ct_run_to(const Ld& ld, float2* line, int es, in
   if constexpr (I < END) {
     ct_stage<N, I, I == 0, false, PAD>(ld, CtNone{}, line, es, tl, tws, twstep);
     ct_run_to<N, I + 1, END, PAD>(ld, line, es, tl, tws, twstep);
+  }
+}
+
+// The last stage from the line in shared memory (complete, after a barrier)
+// into registers: v[q] = X[tl + TPL q], q < E.  Its butterfly j = tl + u TPL
+// (u < E / R) reads j + r NS (NS = N / R) and yields output j + r NS =
+// tl + TPL (u + (E / R) r).
+template <int N, bool PAD>
+__device__ __forceinline__ void ct_last_to_regs(const float2* line, int es, int tl, const float2* __restrict__ tws,
+                                                int twstep, float2* v) {
+  constexpr int I = ct_nst(N) - 1;
+  constexpr int E = ct_e(N), R = ct_radix(N, I), NS = ct_ns(N, I), TPL = N / E, NB = E / R;
+  static_assert(NS * R == N, "the last stage spans the line");
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    const int j = tl + u * TPL;
+    float2 w[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float2 a = line[ct_pos<PAD>(j + r * NS) * es];
+      if (r > 0) a = cmul(a, tws[j * r * twstep]);
+      w[r] = a;
+    }
+    Dft<R, float2, float>::run(w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[u + NB * r] = w[r];
+  }
+}
+
+// The first stage (no twiddles) from registers z[q] = x[tl + TPL q], q < E,
+// into the line in shared memory; no barrier.  Butterfly j = tl + u TPL takes
+// inputs j + r N / R0 = tl + TPL (u + (E / R0) r) and writes j R0 + r.
+template <int N, bool PAD>
+__device__ __forceinline__ void ct_first_from_regs(const float2* z, float2* line, int es, int tl) {
+  constexpr int E = ct_e(N), R0 = ct_radix(N, 0), TPL = N / E, NB = E / R0;
+#pragma unroll
+  for (int u = 0; u < NB; ++u) {
+    float2 w[R0];
+#pragma unroll
+    for (int r = 0; r < R0; ++r) w[r] = z[u + r * NB];
+    Dft<R0, float2, float>::run(w);
+    const int j = tl + u * TPL;
+#pragma unroll
+    for (int r = 0; r < R0; ++r) line[ct_pos<PAD>(j * R0 + r) * es] = w[r];
   }
 }
 

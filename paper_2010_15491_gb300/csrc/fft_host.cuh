@@ -50,10 +50,13 @@ static inline bool m_lines_valid(const Geometry& g, int L) {
   return L >= 1 && L <= lmax && (L * tpl) % 32 == 0;
 }
 
-// lengths with a compile-time plan (FP32 only; the s pass takes 256)
+// lengths with a compile-time plan (FP32 only): 2^a with 16 elements per
+// thread, 3 * 2^a with 12, as the runtime plan of the axis has them
 template <typename T> static inline int ct_len(int n, const FftAxis& f) {
-  if (sizeof(T) != 4 || f.e != 16) return 0;
-  return (n == 32 || n == 64 || n == 128 || n == 256 || n == 512) ? n : 0;
+  if (sizeof(T) != 4) return 0;
+  if (f.e == 16) return (n == 32 || n == 64 || n == 128 || n == 256 || n == 512) ? n : 0;
+  if (f.e == 12) return (n == 48 || n == 96 || n == 192) ? n : 0;
+  return 0;
 }
 
 }  // namespace sr3d

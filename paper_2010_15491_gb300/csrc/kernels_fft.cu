@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_fwd(const T* __restrict__ in,
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int H = NC > 0 ? NC : a.H;
-  const int tpl = NC > 0 ? NC / 16 : H / a.f.e;
+  const int tpl = NC > 0 ? NC / ct_e(NC) : H / a.f.e;
   const long long line0 = (long long)blockIdx.x * L;
   const C* inc = reinterpret_cast<const C*>(in);  // (x[2j], x[2j+1]) as one complex
   const C* tw = twM;
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_inv(const cplx<T>* __restrict
   extern __shared__ __align__(16) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int H = NC > 0 ? NC : a.H;
-  const int tpl = NC > 0 ? NC / 16 : H / a.f.e;
+  const int tpl = NC > 0 ? NC / ct_e(NC) : H / a.f.e;
   const C* tw = twM;
   C* slots = sm + L * Hp + (NC > 0 ? 2 * NC : 0);  // NC > 0: the CTA's L slot rows, staged
   short2* stab = reinterpret_cast<short2*>(slots + (NC > 0 ? L * a.Mp : 0));  // NC > 0: k -> (slot, conj)
@@ -167,11 +167,11 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_inv(const cplx<T>* __restrict
 
 // ---------------------------------------------------------------------------
 // m passes with the real-FFT split in registers (FP32, compile-time lengths,
-// d_r = 1 or 2).  After the last radix-16 stage of the half-length transform
-// (length NC = M/2, TPL = NC/16 threads per line), thread tl holds Z[k] for
-// k = tl + TPL r, r < 16.  The split of the real transform pairs Z[g] with
-// Z[NC - g], which sits in lane (TPL - tl) mod TPL at r' = 15 - r (lane 0:
-// itself, r' = 16 - r), so one warp shuffle per pair replaces the shared-
+// d_r = 1 or 2).  After the last stage of the half-length transform (length
+// NC = M/2, E elements and TPL = NC/E threads per line), thread tl holds Z[k]
+// for k = tl + TPL r, r < E.  The split of the real transform pairs Z[g] with
+// Z[NC - g], which sits in lane (TPL - tl) mod TPL at r' = E - 1 - r (lane 0:
+// itself, r' = E - r), so one warp shuffle per pair replaces the shared-
 // memory round trip of the split:
 //   E = (Z[g] + conj Z[NC-g]) / 2,  O = -i (Z[g] - conj Z[NC-g]) / 2,
 //   X[g] = E + W^g O,  X[NC-g] = conj(E - W^g O)   (W = exp(-2 pi i / M)).
@@ -185,7 +185,7 @@ template <int NC, int DR>
 __global__ void __launch_bounds__(256, 2) k_rfft_m_fwd2(const float* __restrict__ in, long long nlines,
                                                       float2* __restrict__ out, int Mp, int L, int Hp,
                                                       const float2* __restrict__ twM) {
-  constexpr int TPL = NC / 16;
+  constexpr int E = ct_e(NC), TPL = NC / E, HE = E / 2;
   constexpr int NST = ct_nst(NC);
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -198,41 +198,34 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_fwd2(const float* __restrict_
   float2* line = sm + l * Hp;
   auto ld = [&](int j) -> float2 { return ok ? __ldg(&src[j]) : make_float2(0.f, 0.f); };
   ct_run_to<NC, 0, NST - 1, true>(ld, line, 1, tl, tws, 2);
-  // last stage (radix 16, NS = TPL) into registers: v[r] = Z[tl + TPL r]
-  float2 v[16];
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    float2 a = line[ct_pos<true>(tl + r * TPL)];
-    if (r > 0) a = cmul(a, tws[tl * r * 2]);
-    v[r] = a;
-  }
-  Dft<16, float2, float>::run(v);
+  float2 v[E];  // v[r] = Z[tl + TPL r]
+  ct_last_to_regs<NC, true>(line, 1, tl, tws, 2, v);
   const int lane = threadIdx.x & 31;
   const int partner = lane - tl + ((TPL - tl) & (TPL - 1));
   float2* orow = out + gl * Mp;
 #pragma unroll
-  for (int r = 0; r <= 8; ++r) {
+  for (int r = 0; r <= HE; ++r) {
     float2 zh;
-    if (r < 8) {
+    if (r < HE) {
       float2 recv;
-      recv.x = __shfl_sync(0xffffffffu, v[15 - r].x, partner);
-      recv.y = __shfl_sync(0xffffffffu, v[15 - r].y, partner);
-      zh = tl == 0 ? v[(16 - r) & 15] : recv;
+      recv.x = __shfl_sync(0xffffffffu, v[E - 1 - r].x, partner);
+      recv.y = __shfl_sync(0xffffffffu, v[E - 1 - r].y, partner);
+      zh = tl == 0 ? v[(E - r) % E] : recv;
     } else {
-      zh = v[8];  // g = NC/2 (lane 0 only)
+      zh = v[HE];  // g = NC/2 (lane 0 only)
     }
     const int g = tl + TPL * r;
     const float2 zc = conjc(zh);
     const float2 e = (v[r] + zc) * 0.5f;
     const float2 o = mul_mi(v[r] - zc) * 0.5f;
-    const float2 t = cmul(tws[r < 8 ? g : NC / 2], o);
-    if (ok && (r < 8 || tl == 0)) {
+    const float2 t = cmul(tws[r < HE ? g : NC / 2], o);
+    if (ok && (r < HE || tl == 0)) {
       const float2 xp = e + t, xm = e - t;
       if constexpr (DR == 2) {
         reinterpret_cast<float4*>(orow)[g] = make_float4(xp.x, xp.y, xm.x, xm.y);
       } else {
         orow[g] = xp;
-        if (r < 8 || tl != 0) orow[NC - g] = conjc(xm);  // g = NC/2: the same slot
+        if (r < HE || tl != 0) orow[NC - g] = conjc(xm);  // g = NC/2: the same slot
       }
     }
   }
@@ -242,9 +235,7 @@ template <int NC, int DR>
 __global__ void __launch_bounds__(256, 2) k_rfft_m_inv2(const float2* __restrict__ in, long long nlines,
                                                       float* __restrict__ out, int Mp, int L, int Hp,
                                                       const float2* __restrict__ twM, float scale) {
-  constexpr int TPL = NC / 16;
-  constexpr int R0 = ct_radix(NC, 0);
-  constexpr int NB = 16 / R0;
+  constexpr int E = ct_e(NC), TPL = NC / E, HE = E / 2;
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   float2* tws = sm + L * Hp;
@@ -254,11 +245,11 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_inv2(const float2* __restrict
   const bool ok = gl < nlines;
   const float2* row = in + gl * Mp;
   // pairs g = tl + TPL m: X[g] and conj(X[NC - g])
-  float2 xk[9], xh[9];
+  float2 xk[HE + 1], xh[HE + 1];
 #pragma unroll
-  for (int m = 0; m <= 8; ++m) {
+  for (int m = 0; m <= HE; ++m) {
     const int g = tl + TPL * m;
-    const bool act = ok && (m < 8 || tl == 0);
+    const bool act = ok && (m < HE || tl == 0);
     xk[m] = make_float2(0.f, 0.f);
     xh[m] = make_float2(0.f, 0.f);
     if (act) {
@@ -273,40 +264,30 @@ __global__ void __launch_bounds__(256, 2) k_rfft_m_inv2(const float2* __restrict
     }
   }
   // inverse inputs (the forward engine on conjugated data): z[m] = Zi[tl + TPL m]
-  float2 z[16];
+  float2 z[E];
   const int lane = threadIdx.x & 31;
   const int partner = lane - tl + ((TPL - tl) & (TPL - 1));
 #pragma unroll
-  for (int m = 0; m <= 8; ++m) {
+  for (int m = 0; m <= HE; ++m) {
     const int g = tl + TPL * m;
     const float2 e = xk[m] + xh[m];
-    const float2 o = cmulc(tws[m < 8 ? g : NC / 2], xk[m] - xh[m]);  // W^-g (X[g] - conj X[NC-g])
-    const float2 zg = conjc(e + mul_i(o));                           // input g
-    const float2 zp = e - mul_i(o);                                  // input NC - g
-    if (m < 8) {
+    const float2 o = cmulc(tws[m < HE ? g : NC / 2], xk[m] - xh[m]);  // W^-g (X[g] - conj X[NC-g])
+    const float2 zg = conjc(e + mul_i(o));                            // input g
+    const float2 zp = e - mul_i(o);                                   // input NC - g
+    if (m < HE) {
       z[m] = zg;
       float2 recv;
       recv.x = __shfl_sync(0xffffffffu, zp.x, partner);
       recv.y = __shfl_sync(0xffffffffu, zp.y, partner);
-      if (tl != 0) z[15 - m] = recv;
-      else if (m >= 1) z[16 - m] = zp;
+      if (tl != 0) z[E - 1 - m] = recv;
+      else if (m >= 1) z[E - m] = zp;
     } else if (tl == 0) {
-      z[8] = zg;
+      z[HE] = zg;
     }
   }
-  // stage 0 (radix R0, no twiddles) from the registers: butterfly j = tl + u TPL
-  // takes inputs j + r NC/R0 = tl + TPL (u + r NB)
+  // stage 0 from the registers
   float2* line = sm + l * Hp;
-#pragma unroll
-  for (int u = 0; u < NB; ++u) {
-    float2 w[R0];
-#pragma unroll
-    for (int r = 0; r < R0; ++r) w[r] = z[u + r * NB];
-    Dft<R0, float2, float>::run(w);
-    const int j = tl + u * TPL;
-#pragma unroll
-    for (int r = 0; r < R0; ++r) line[ct_pos<true>(j * R0 + r)] = w[r];
-  }
+  ct_first_from_regs<NC, true>(z, line, 1, tl);
   __syncthreads();
   float2* outc = reinterpret_cast<float2*>(out) + gl * NC;
   auto st = [&](int j, float2 r) {
@@ -328,7 +309,7 @@ __global__ void __launch_bounds__(256, 2) k_fft_n(cplx<T>* __restrict__ spec, LA
   const int a0 = blockIdx.x * TW;
   const int tv = min(TW, Ms - a0);
   C* base = spec + (long long)blockIdx.y * N * Mp + a0;
-  const int t = threadIdx.x % TW, tl = threadIdx.x / TW, tpl = NC > 0 ? NC / 16 : N / a.f.e;
+  const int t = threadIdx.x % TW, tl = threadIdx.x / TW, tpl = NC > 0 ? NC / ct_e(NC) : N / a.f.e;
   const bool ok = t < tv;
   C* col = base + t;
   auto ld = [&](int k) -> C {
@@ -429,6 +410,9 @@ static cudaError_t rfft2_fwd_len(const Plan& p, const Geometry& g, const void* i
     case 128: return rfft_fwd2_k<128, DR>(p, g, in, out, tw);
     case 256: return rfft_fwd2_k<256, DR>(p, g, in, out, tw);
     case 512: return rfft_fwd2_k<512, DR>(p, g, in, out, tw);
+    case 48: return rfft_fwd2_k<48, DR>(p, g, in, out, tw);
+    case 96: return rfft_fwd2_k<96, DR>(p, g, in, out, tw);
+    case 192: return rfft_fwd2_k<192, DR>(p, g, in, out, tw);
   }
   return cudaErrorNotSupported;
 }
@@ -441,13 +425,15 @@ static cudaError_t rfft2_inv_len(const Plan& p, const Geometry& g, const void* i
     case 128: return rfft_inv2_k<128, DR>(p, g, in, out, tw, scale);
     case 256: return rfft_inv2_k<256, DR>(p, g, in, out, tw, scale);
     case 512: return rfft_inv2_k<512, DR>(p, g, in, out, tw, scale);
+    case 48: return rfft_inv2_k<48, DR>(p, g, in, out, tw, scale);
+    case 96: return rfft_inv2_k<96, DR>(p, g, in, out, tw, scale);
+    case 192: return rfft_inv2_k<192, DR>(p, g, in, out, tw, scale);
   }
   return cudaErrorNotSupported;
 }
 
 template <typename T>
 static cudaError_t rfft_fwd_t(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw) {
-  if (fam3(g.fm)) return rfft_fwd_k<T, Emax<T>::p3, 0>(p, g, in, out, tw);
   if constexpr (sizeof(T) == 4) {
     if (ct_len<T>(g.M / 2, g.fm) > 0 && (g.dr == 1 || g.dr == 2))
       return g.dr == 2 ? rfft2_fwd_len<2>(p, g, in, out, tw) : rfft2_fwd_len<1>(p, g, in, out, tw);
@@ -457,15 +443,18 @@ static cudaError_t rfft_fwd_t(const Plan& p, const Geometry& g, const void* in, 
       case 128: return rfft_fwd_k<T, 16, 128>(p, g, in, out, tw);
       case 256: return rfft_fwd_k<T, 16, 256>(p, g, in, out, tw);
       case 512: return rfft_fwd_k<T, 16, 512>(p, g, in, out, tw);
+      case 48: return rfft_fwd_k<T, 12, 48>(p, g, in, out, tw);
+      case 96: return rfft_fwd_k<T, 12, 96>(p, g, in, out, tw);
+      case 192: return rfft_fwd_k<T, 12, 192>(p, g, in, out, tw);
     }
   }
+  if (fam3(g.fm)) return rfft_fwd_k<T, Emax<T>::p3, 0>(p, g, in, out, tw);
   return rfft_fwd_k<T, Emax<T>::p2, 0>(p, g, in, out, tw);
 }
 
 template <typename T>
 static cudaError_t rfft_inv_t(const Plan& p, const Geometry& g, const void* in, void* out, const void* tw,
                               double scale) {
-  if (fam3(g.fm)) return rfft_inv_k<T, Emax<T>::p3, 0>(p, g, in, out, tw, scale);
   if constexpr (sizeof(T) == 4) {
     if (ct_len<T>(g.M / 2, g.fm) > 0 && (g.dr == 1 || g.dr == 2))
       return g.dr == 2 ? rfft2_inv_len<2>(p, g, in, out, tw, scale) : rfft2_inv_len<1>(p, g, in, out, tw, scale);
@@ -475,8 +464,12 @@ static cudaError_t rfft_inv_t(const Plan& p, const Geometry& g, const void* in, 
       case 128: return rfft_inv_k<T, 16, 128>(p, g, in, out, tw, scale);
       case 256: return rfft_inv_k<T, 16, 256>(p, g, in, out, tw, scale);
       case 512: return rfft_inv_k<T, 16, 512>(p, g, in, out, tw, scale);
+      case 48: return rfft_inv_k<T, 12, 48>(p, g, in, out, tw, scale);
+      case 96: return rfft_inv_k<T, 12, 96>(p, g, in, out, tw, scale);
+      case 192: return rfft_inv_k<T, 12, 192>(p, g, in, out, tw, scale);
     }
   }
+  if (fam3(g.fm)) return rfft_inv_k<T, Emax<T>::p3, 0>(p, g, in, out, tw, scale);
   return rfft_inv_k<T, Emax<T>::p2, 0>(p, g, in, out, tw, scale);
 }
 
@@ -515,13 +508,16 @@ cudaError_t launch_fft_n(const Plan& p, const Geometry& g, void* spec, const voi
   if (p.dtype)
     return f3 ? fft_n_e<double, Emax<double>::p3, 0>(p, g, spec, tw, inverse)
               : fft_n_e<double, Emax<double>::p2, 0>(p, g, spec, tw, inverse);
-  if (f3) return fft_n_e<float, Emax<float>::p3, 0>(p, g, spec, tw, inverse);
   switch (ct_len<float>(g.N, g.fn)) {
     case 64: return fft_n_e<float, 16, 64>(p, g, spec, tw, inverse);
     case 128: return fft_n_e<float, 16, 128>(p, g, spec, tw, inverse);
     case 256: return fft_n_e<float, 16, 256>(p, g, spec, tw, inverse);
     case 512: return fft_n_e<float, 16, 512>(p, g, spec, tw, inverse);
+    case 48: return fft_n_e<float, 12, 48>(p, g, spec, tw, inverse);
+    case 96: return fft_n_e<float, 12, 96>(p, g, spec, tw, inverse);
+    case 192: return fft_n_e<float, 12, 192>(p, g, spec, tw, inverse);
   }
+  if (f3) return fft_n_e<float, Emax<float>::p3, 0>(p, g, spec, tw, inverse);
   return fft_n_e<float, Emax<float>::p2, 0>(p, g, spec, tw, inverse);
 }
 

@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(NC > 0 ? 256 : 512, NC > 0 ? 3 : 1) k_fft_s(cp
   const int nthr = blockDim.x, tid = threadIdx.x;
   const int rowlen = G * TW;
   const long long plane = (long long)Nn * Mp;
-  const int t = tid % TW, gi = (tid / TW) % G, tl = tid / (TW * G), tpl = NC > 0 ? NC / 16 : S / a.f.e;
+  const int t = tid % TW, gi = (tid / TW) % G, tl = tid / (TW * G), tpl = NC > 0 ? NC / ct_e(NC) : S / a.f.e;
   (void)tpl;
   const bool ok = t < tv;
   // tile row gi = gn * dc + pn holds n = b0 / dc + gn + pn * Nl (dc, Nl of the n axis)
@@ -353,14 +353,14 @@ __global__ void __launch_bounds__(NC > 0 ? 256 : 512, NC > 0 ? 3 : 1) k_fft_s(cp
 }
 
 // ---------------------------------------------------------------------------
-// Register-resident s pass of the ADMM x-update (Algorithm 1 step 5a) for
-// 256-point s lines in FP32 with the class shape DR x DC x DS fixed at compile
-// time.  Each 256-point transform is two radix-16 Stockham stages: after the
-// forward transform's second stage, thread tl of a line holds the
-// frequencies k = tl + 16 r (r < 16) in registers, so the DS members
-// k, k + 256/DS, ... of an aliasing class along s are in the same thread, and
-// those frequencies are exactly the inputs of the inverse transform's first
-// stage.  The class's DR x DC members in the (m, n) plane sit in QN = DR * DC
+// Register-resident s pass of the ADMM x-update (Algorithm 1 step 5a) for the
+// compile-time s lengths in FP32 with the class shape DR x DC x DS fixed at
+// compile time.  After the forward transform's last stage, thread tl of a
+// line holds the frequencies k = tl + TPL r (r < E; E = 16 elements and
+// TPL = S/16 threads per line for S = 2^a, E = 12 for S = 3 * 2^a) in
+// registers, so the DS members k, k + S/DS, ... of an aliasing class along s
+// are in the same thread (S/DS = TPL E/DS), and those frequencies are exactly
+// the inputs of the inverse transform's first stage.  The class's DR x DC members in the (m, n) plane sit in QN = DR * DC
 // adjacent lanes of one warp (lane layout q + QN * (gm + GMc * tl), q = pm +
 // DR * pn), and the solve exchanges only per-class scalars by warp shuffles
 // (the Sherman-Morrison sums of the other lanes' members, as the butterfly
@@ -381,10 +381,10 @@ __device__ __forceinline__ float rcp_nr(float x) {
 template <int S, bool STATS, int DR, int DC, int DS>
 __global__ void __launch_bounds__(256, 3) k_fft_s_admm_reg(float2* __restrict__ spec, int Ms, int Mp, int Nn, int TW,
                                                          SolveArgs sv, const float2* __restrict__ twS, int nNl) {
-  constexpr int TPL = S / 16, NST = ct_nst(S), R0 = ct_radix(S, 0), NB = 16 / R0;
-  constexpr int QN = DR * DC, D = DR * DC * DS, RS = 16 / DS, SL = S / DS;
+  constexpr int E = ct_e(S), TPL = S / E, NST = ct_nst(S);
+  constexpr int QN = DR * DC, D = DR * DC * DS, RS = E / DS, SL = S / DS;
   static_assert(QN == 1 || QN == 2 || QN == 4, "class members in the (m, n) plane: 1, 2 or 4 lanes");
-  static_assert(16 % DS == 0, "the s members of a class must share a thread");
+  static_assert(E % DS == 0, "the s members of a class must share a thread");
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
   const int GMc = TW / DR;
@@ -408,19 +408,13 @@ __global__ void __launch_bounds__(256, 3) k_fft_s_admm_reg(float2* __restrict__ 
   float2* tws = sm + S * rowlen;
   ct_load_twiddles(tws, twS, S);
 
-  float2 v[16];
+  float2 v[E];
   // forward transform: every stage but the last through shared memory (the
-  // first one loads straight from global memory, 16 loads in flight)
+  // first one loads straight from global memory, E loads in flight), the last
+  // into registers: v[r] = frequency tl + TPL r
   auto ld = [&](int j) -> float2 { return cls_ok ? col[(long long)j * plane] : make_float2(0.f, 0.f); };
   ct_run_to<S, 0, NST - 1, false>(ld, line, rowlen, tl, tws, 1);
-  // last stage (radix 16, NS = TPL) into registers: v[r] = frequency tl + TPL r
-#pragma unroll
-  for (int r = 0; r < 16; ++r) {
-    float2 a = line[(tl + TPL * r) * rowlen];
-    if (r > 0) a = cmul(a, tws[tl * r]);
-    v[r] = a;
-  }
-  Dft<16, float2, float>::run(v);
+  ct_last_to_regs<S, false>(line, rowlen, tl, tws, 1, v);
 
   // per-class solve
   const int g = cls_ok ? a0 / DR + gm : 0;
@@ -550,19 +544,9 @@ __global__ void __launch_bounds__(256, 3) k_fft_s_admm_reg(float2* __restrict__ 
       if (lane == 0) sv.partial[bc] = s_;
     }
   }
-  // inverse transform, stage 0 (radix R0, no twiddles) from the registers:
-  // butterfly j = tl + u TPL takes inputs j + r S/R0 = tl + TPL (u + r NB)
+  // inverse transform, stage 0 from the registers
   __syncthreads();  // every thread has read its forward last-stage inputs
-#pragma unroll
-  for (int u = 0; u < NB; ++u) {
-    float2 w[R0];
-#pragma unroll
-    for (int r = 0; r < R0; ++r) w[r] = v[u + r * NB];
-    Dft<R0, float2, float>::run(w);
-    const int j = tl + u * TPL;
-#pragma unroll
-    for (int r = 0; r < R0; ++r) line[(j * R0 + r) * rowlen] = w[r];
-  }
+  ct_first_from_regs<S, false>(v, line, rowlen, tl);
   __syncthreads();
   // the store addresses are formed again here rather than kept live (in
   // registers) from the loads through the whole solve
@@ -584,7 +568,7 @@ static cudaError_t fft_s_admm_reg(const Plan& p, const Geometry& g, void* spec, 
   dim3 grid((g.Ms + TW - 1) / TW, (g.N / DC) * nb);
   cudaError_t e;
   if ((e = allow_smem(k_fft_s_admm_reg<S, STATS, DR, DC, DS>, smem)) != cudaSuccess) return e;
-  k_fft_s_admm_reg<S, STATS, DR, DC, DS><<<grid, TW * DC * (S / 16), smem, p.stream>>>(
+  k_fft_s_admm_reg<S, STATS, DR, DC, DS><<<grid, TW * DC * (S / ct_e(S)), smem, p.stream>>>(
       (float2*)spec, g.Ms, g.Mp, g.N, TW, svb, (const float2*)tw, g.Nl);
   return cudaGetLastError();
 }
@@ -631,6 +615,14 @@ static cudaError_t fft_s_e(const Plan& p, const Geometry& g, void* spec, const v
     case S_TIK_GEN: return fft_s_k<T, EMAX, S_TIK_GEN, false, 0>(p, g, spec, tw, sv);
     case S_TIK_USER: return fft_s_k<T, EMAX, S_TIK_USER, false, 0>(p, g, spec, tw, sv);
     case S_ADMM:
+      if constexpr (sizeof(T) == 4 && EMAX == 12) {
+        const int sl = ct_len<T>(g.S, g.fs);
+        if ((sl == 96 || sl == 192) && g.tw_s * g.g_s * (sl / 12) <= 256) {
+          const cudaError_t r = sl == 192 ? fft_s_admm_reg_shape<192>(p, g, spec, tw, stats, sv)
+                                          : fft_s_admm_reg_shape<96>(p, g, spec, tw, stats, sv);
+          if (r != cudaErrorNotSupported) return r;
+        }
+      }
       if constexpr (sizeof(T) == 4 && EMAX == 16) {
         const int sl = ct_len<T>(g.S, g.fs);
         if ((sl == 64 || sl == 128 || sl == 256) && g.tw_s * g.g_s * (sl / 16) <= 256) {

@@ -30,6 +30,13 @@ CASES = [
     ((64, 16, 256), (2, 2, 2), "f32"),
     ((512, 32, 16), (1, 1, 4), "f32"),
     ((32, 512, 8), (1, 2, 1), "f32"),
+    # compile-time plans of 3 * 2^a lengths (12 elements per thread): m half-lengths
+    # 48 / 96 / 192, n 96 / 192, register-resident s passes of 96 and 192 points
+    ((96, 96, 96), (2, 2, 2), "f32"),
+    ((96, 96, 96), (2, 2, 1), "f32"),
+    ((192, 32, 96), (1, 1, 4), "f32"),
+    ((64, 192, 192), (2, 2, 2), "f32"),
+    ((384, 16, 48), (4, 1, 1), "f32"),
 ]
 IDS = [f"{d[0]}x{d[1]}x{d[2]}_d{c[0]}{c[1]}{c[2]}_{t}" for d, c, t in CASES]
 
