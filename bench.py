@@ -50,12 +50,12 @@ STEP_BYTES = 80
 # with the kernel's entry of the tile schedule in that capture; valid while the
 # plan runs that entry and the kernel's sources hash to the recorded value
 NCU_TRAFFIC = {
-    "tv": (497.21e6, {"tv_planes": 37}, ('kernels_tv.cu', 'common.cuh'), "c99c7def601b9eef"),
-    "rfft_m_fwd": (83.63e6, {"m_fwd_lines": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "6f2096cce7b6697b"),
-    "fft_n_fwd": (77.54e6, {"n_pass_slots": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "6f2096cce7b6697b"),
-    "fft_s": (87.11e6, {"s_pass_slots": 8}, ('kernels_fft_s.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "043618cbd171395a"),
-    "fft_n_inv": (77.49e6, {"n_pass_slots": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "6f2096cce7b6697b"),
-    "rfft_m_inv": (85.35e6, {"m_inv_lines": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "6f2096cce7b6697b"),
+    "tv": (497.18e6, {"tv_planes": 37}, ('kernels_tv.cu', 'common.cuh'), "931e3ec90df7cbdc"),
+    "rfft_m_fwd": (83.85e6, {"m_fwd_lines": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "be6b25943a19954d"),
+    "fft_n_fwd": (77.52e6, {"n_pass_slots": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "be6b25943a19954d"),
+    "fft_s": (87.23e6, {"s_pass_slots": 8}, ('kernels_fft_s.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "c5033b5a8e1a8d49"),
+    "fft_n_inv": (77.48e6, {"n_pass_slots": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "be6b25943a19954d"),
+    "rfft_m_inv": (85.35e6, {"m_inv_lines": 16}, ('kernels_fft.cu', 'fft.cuh', 'fft_ct.cuh', 'fft_host.cuh', 'common.cuh'), "be6b25943a19954d"),
 }
 
 
