@@ -1483,6 +1483,14 @@ struct BatchGraph {
   std::vector<BatchGroup> groups;
   std::vector<const void*> gkey_ptr;
   std::vector<double> gkey_val;
+  // the set-up graph (per-volume set-up, the copies into the group buffers
+  // and, for an odd iteration count, the first iteration), its key, launch
+  // counts, and whether the grouping has run its set-up eagerly once
+  cudaGraphExec_t setup_exec = nullptr;
+  std::vector<const void*> skey_ptr;
+  std::vector<double> skey_val;
+  long long setup_launches[8] = {0};
+  bool setup_warm = false;
 };
 static std::mutex g_batch_mu;
 static BatchGraph g_batch;
@@ -1605,10 +1613,12 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
       gv.push_back(rho[i]);
     }
     if (gp != g_batch.gkey_ptr || gv != g_batch.gkey_val) {
-      if (g_batch.exec) {
-        cudaGraphExecDestroy(g_batch.exec);
-        g_batch.exec = nullptr;
-      }
+      for (cudaGraphExec_t* ge : {&g_batch.exec, &g_batch.setup_exec})
+        if (*ge) {
+          cudaGraphExecDestroy(*ge);
+          *ge = nullptr;
+        }
+      g_batch.setup_warm = false;
       g_batch.gkey_ptr.clear();
       TRY(build_groups(n, plans, lambda, rho));
       g_batch.gkey_ptr = gp;
@@ -1619,44 +1629,48 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
   for (int k = 0; k < (int)g_batch.groups.size(); ++k)
     for (int v : g_batch.groups[k].vols) group_of[v] = k;
   std::vector<void*> dcur(n), dnext(n);
-  // set-up on every plan's stream, after whatever the stream holds
-  for (int i = 0; i < n; ++i) {
-    Plan& p = plans[i]->p;
-    TRY(ensure_admm_buffers(p, false));
-    dcur[i] = p.dbuf[0];
-    dnext[i] = p.dbuf[1];
-    p.kind_override = SR3D_K_SETUP;
-    struct Reset { Plan& p; ~Reset() { p.kind_override = -1; } } reset{p};
-    TRY(lr_spectrum(p, y[i]));
-    if (tau_init[i] > 0) TRY(tikhonov_core(p, SR3D_XBAR_NEAREST, tau_init[i], x[i]));
-    CK(cudaMemsetAsync(dcur[i], 0, (size_t)3 * p.hr.V() * p.esz, p.stream));
-    LAUNCH(SR3D_K_TV, launch_tv(p, x[i], dcur[i], nullptr, p.theta, p.psi, lambda[i] / rho[i], 1, false));
-  }
-  // group members' state into the group buffers, on the lead's stream after
-  // each member's set-up
-  for (BatchGroup& G : g_batch.groups) {
-    Plan& L = const_cast<Plan&>(G.lead->p);
-    const Geometry& g = L.hr;
-    const size_t csz = 2 * L.esz, vb = (size_t)g.V() * L.esz;
-    for (size_t j = 0; j < G.vols.size(); ++j) {
-      Plan& p = plans[G.vols[j]]->p;
-      if (&p != &L) {
-        CK(cudaEventRecord(g_batch.ev[G.vols[j]], p.stream));
-        CK(cudaStreamWaitEvent(L.stream, g_batch.ev[G.vols[j]], 0));
-      }
-      unsigned char* xb = (unsigned char*)G.x + j * vb;
-      unsigned char* tb = (unsigned char*)G.theta + j * vb;
-      unsigned char* yb = (unsigned char*)G.yhat + j * (size_t)solve_yhat_elems(g) * csz;
-      CK(cudaMemcpyAsync(xb, x[G.vols[j]], vb, cudaMemcpyDeviceToDevice, L.stream));
-      CK(cudaMemcpyAsync(tb, p.theta, vb, cudaMemcpyDeviceToDevice, L.stream));
-      CK(cudaMemcpyAsync(yb, p.yhat_solve, (size_t)solve_yhat_elems(g) * csz, cudaMemcpyDeviceToDevice, L.stream));
-      CK(cudaMemcpyAsync((unsigned char*)G.lam[0] + j * g.M * csz, p.lamM1, g.M * csz, cudaMemcpyDeviceToDevice, L.stream));
-      CK(cudaMemcpyAsync((unsigned char*)G.lam[1] + j * g.N * csz, p.lamN1, g.N * csz, cudaMemcpyDeviceToDevice, L.stream));
-      CK(cudaMemcpyAsync((unsigned char*)G.lam[2] + j * g.S * csz, p.lamS1, g.S * csz, cudaMemcpyDeviceToDevice, L.stream));
+  // set-up on every plan's stream, then the group members' state into the
+  // group buffers on the lead's stream after each member's set-up
+  auto setup_all = [&]() -> int {
+    for (int i = 0; i < n; ++i) {
+      Plan& p = plans[i]->p;
+      p.kind_override = SR3D_K_SETUP;
+      struct Reset { Plan& p; ~Reset() { p.kind_override = -1; } } reset{p};
+      TRY(lr_spectrum(p, y[i]));
+      if (tau_init[i] > 0) TRY(tikhonov_core(p, SR3D_XBAR_NEAREST, tau_init[i], x[i]));
+      CK(cudaMemsetAsync(dcur[i], 0, (size_t)3 * p.hr.V() * p.esz, p.stream));
+      LAUNCH(SR3D_K_TV, launch_tv(p, x[i], dcur[i], nullptr, p.theta, p.psi, lambda[i] / rho[i], 1, false));
     }
-    CK(cudaMemsetAsync(G.d[0], 0, 3 * G.vols.size() * vb, L.stream));
-    G.cur = 0;
+    for (BatchGroup& G : g_batch.groups) {
+      Plan& L = const_cast<Plan&>(G.lead->p);
+      const Geometry& g = L.hr;
+      const size_t csz = 2 * L.esz, vb = (size_t)g.V() * L.esz;
+      for (size_t j = 0; j < G.vols.size(); ++j) {
+        Plan& p = plans[G.vols[j]]->p;
+        if (&p != &L) {
+          CK(cudaEventRecord(g_batch.ev[G.vols[j]], p.stream));
+          CK(cudaStreamWaitEvent(L.stream, g_batch.ev[G.vols[j]], 0));
+        }
+        unsigned char* xb = (unsigned char*)G.x + j * vb;
+        unsigned char* tb = (unsigned char*)G.theta + j * vb;
+        unsigned char* yb = (unsigned char*)G.yhat + j * (size_t)solve_yhat_elems(g) * csz;
+        CK(cudaMemcpyAsync(xb, x[G.vols[j]], vb, cudaMemcpyDeviceToDevice, L.stream));
+        CK(cudaMemcpyAsync(tb, p.theta, vb, cudaMemcpyDeviceToDevice, L.stream));
+        CK(cudaMemcpyAsync(yb, p.yhat_solve, (size_t)solve_yhat_elems(g) * csz, cudaMemcpyDeviceToDevice, L.stream));
+        CK(cudaMemcpyAsync((unsigned char*)G.lam[0] + j * g.M * csz, p.lamM1, g.M * csz, cudaMemcpyDeviceToDevice, L.stream));
+        CK(cudaMemcpyAsync((unsigned char*)G.lam[1] + j * g.N * csz, p.lamN1, g.N * csz, cudaMemcpyDeviceToDevice, L.stream));
+        CK(cudaMemcpyAsync((unsigned char*)G.lam[2] + j * g.S * csz, p.lamS1, g.S * csz, cudaMemcpyDeviceToDevice, L.stream));
+      }
+      CK(cudaMemsetAsync(G.d[0], 0, 3 * G.vols.size() * vb, L.stream));
+    }
+    return SR3D_OK;
+  };
+  for (int i = 0; i < n; ++i) {
+    TRY(ensure_admm_buffers(plans[i]->p, false));
+    dcur[i] = plans[i]->p.dbuf[0];
+    dnext[i] = plans[i]->p.dbuf[1];
   }
+  for (BatchGroup& G : g_batch.groups) G.cur = 0;
   // the chains: a group (its lead's index) or a single volume
   std::vector<int> chain;
   for (int i = 0; i < n; ++i)
@@ -1676,14 +1690,96 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
     for (int i : chain) TRY(chain_iteration(i));
     return SR3D_OK;
   };
-  int it = 0;
-  // the first iteration runs eagerly (kernels loaded before any capture)
-  if (iters > 0) {
-    TRY(eager_iteration());
-    it = 1;
-  }
   bool profiling = false;
   for (int i = 0; i < n; ++i) profiling |= plans[i]->p.prof_on;
+  // main waits for every plan's queued work / every plan's stream waits for main
+  auto join_to_main = [&]() -> int {
+    for (int i = 0; i < n; ++i) {
+      CK(cudaEventRecord(g_batch.ev[i], plans[i]->p.stream));
+      CK(cudaStreamWaitEvent(g_batch.main, g_batch.ev[i], 0));
+    }
+    return SR3D_OK;
+  };
+  auto fork_from_main = [&]() -> int {
+    CK(cudaEventRecord(g_batch.ev[n], g_batch.main));
+    for (int i = 0; i < n; ++i) CK(cudaStreamWaitEvent(plans[i]->p.stream, g_batch.ev[n], 0));
+    return SR3D_OK;
+  };
+  int it = 0;
+  if (profiling || !g_batch.setup_warm) {
+    // eager: the first call of a grouping loads and configures every kernel
+    // before any capture; the first iteration runs eagerly too
+    TRY(setup_all());
+    if (iters > 0) {
+      TRY(eager_iteration());
+      it = 1;
+    }
+    if (!profiling) g_batch.setup_warm = true;
+  } else {
+    // the set-up as one graph from the main stream, with the first iteration
+    // when the count is odd (the pairs then cover the rest)
+    const int first = iters & 1;
+    std::vector<const void*> kp;
+    std::vector<double> kv;
+    for (int i = 0; i < n; ++i) {
+      kp.push_back(y[i]);
+      kp.push_back(x[i]);
+      kp.push_back(dcur[i]);
+      kv.push_back(tau_init[i]);
+    }
+    for (const BatchGroup& G : g_batch.groups) kp.push_back(G.x);
+    kv.push_back((double)first);
+    if (!g_batch.setup_exec || kp != g_batch.skey_ptr || kv != g_batch.skey_val) {
+      if (g_batch.setup_exec) {
+        cudaGraphExecDestroy(g_batch.setup_exec);
+        g_batch.setup_exec = nullptr;
+      }
+      std::vector<long long> before(8 * (size_t)n);
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 8; ++k) before[8 * i + k] = plans[i]->p.launches[k];
+      cudaGraph_t graph = nullptr;
+      CK(cudaStreamBeginCapture(g_batch.main, cudaStreamCaptureModeThreadLocal));
+      int rc = fork_from_main();
+      if (rc == SR3D_OK) rc = setup_all();
+      if (rc == SR3D_OK && first) rc = eager_iteration();
+      if (rc == SR3D_OK) rc = join_to_main();
+      const cudaError_t ee = cudaStreamEndCapture(g_batch.main, &graph);
+      if (rc != SR3D_OK || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (rc != SR3D_OK) return rc;
+        return fail(SR3D_ERR_CUDA, "batched set-up graph capture: %s", cudaGetErrorString(ee));
+      }
+      const cudaError_t ei = cudaGraphInstantiate(&g_batch.setup_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) {
+        g_batch.setup_exec = nullptr;
+        return fail(SR3D_ERR_CUDA, "batched set-up graph instantiate: %s", cudaGetErrorString(ei));
+      }
+      for (int k = 0; k < 8; ++k) g_batch.setup_launches[k] = 0;
+      for (int i = 0; i < n; ++i)
+        for (int k = 0; k < 8; ++k) {
+          g_batch.setup_launches[k] += plans[i]->p.launches[k] - before[8 * i + k];
+          plans[i]->p.launches[k] = before[8 * i + k];
+        }
+      g_batch.skey_ptr = kp;
+      g_batch.skey_val = kv;
+    } else if (first) {
+      // the captured iteration advanced the dual buffers of every chain
+      for (int i : chain) {
+        if (group_of[i] >= 0) {
+          BatchGroup& G = g_batch.groups[group_of[i]];
+          G.cur = 1 - G.cur;
+        } else {
+          std::swap(dcur[i], dnext[i]);
+        }
+      }
+    }
+    TRY(join_to_main());
+    CK(cudaGraphLaunch(g_batch.setup_exec, g_batch.main));
+    for (int k = 0; k < 8; ++k) plans[0]->p.launches[k] += g_batch.setup_launches[k];
+    TRY(fork_from_main());
+    it = first;
+  }
   const int pairs = profiling ? 0 : (iters - it) / 2;  // per-launch events are not captured
   if (pairs > 0) {
     std::vector<const void*> kp;
@@ -1708,29 +1804,66 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
       std::vector<long long> before(8 * (size_t)n);
       for (int i = 0; i < n; ++i)
         for (int k = 0; k < 8; ++k) before[8 * i + k] = plans[i]->p.launches[k];
+      // each chain's two iterations captured into one graph after a common
+      // root; a chain's kernels get a priority that rises as its work falls,
+      // so the CTAs of the short, latency-bound chains are dispatched ahead of
+      // the queued CTAs of the long ones instead of in their tails
       cudaGraph_t graph = nullptr;
-      CK(cudaStreamBeginCapture(g_batch.main, cudaStreamCaptureModeThreadLocal));
-      int rc = SR3D_OK;
-      cudaError_t ec = cudaEventRecord(g_batch.ev[n], g_batch.main);
-      for (size_t c = 0; c < chain.size() && rc == SR3D_OK && ec == cudaSuccess; ++c) {
+      CK(cudaGraphCreate(&graph, 0));
+      struct Owner {
+        cudaGraph_t g;
+        ~Owner() { cudaGraphDestroy(g); }
+      } owner{graph};
+      cudaGraphNode_t root;
+      CK(cudaGraphAddEmptyNode(&root, graph, nullptr, 0));
+      int prio_least = 0, prio_greatest = 0;
+      CK(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
+      std::vector<double> work(chain.size());
+      for (size_t c = 0; c < chain.size(); ++c) {
+        const int i = chain[c];
+        if (group_of[i] >= 0)
+          work[c] = (double)g_batch.groups[group_of[i]].vols.size() * (double)plans[i]->p.hr.V();
+        else
+          work[c] = (double)plans[i]->p.hr.V();
+      }
+      std::vector<int> rank(chain.size());  // 0 = least work
+      for (size_t c = 0; c < chain.size(); ++c) {
+        int r = 0;
+        for (size_t o = 0; o < chain.size(); ++o) r += (work[o] < work[c] || (work[o] == work[c] && o < c)) ? 1 : 0;
+        rank[c] = r;
+      }
+      std::vector<cudaGraphNode_t> seen{root};
+      for (size_t c = 0; c < chain.size(); ++c) {
         const int i = chain[c];
         Plan& p = plans[i]->p;
-        ec = cudaStreamWaitEvent(p.stream, g_batch.ev[n], 0);
-        if (ec != cudaSuccess) break;
-        rc = chain_iteration(i);
+        CK(cudaStreamBeginCaptureToGraph(p.stream, graph, &root, nullptr, 1, cudaStreamCaptureModeThreadLocal));
+        int rc = chain_iteration(i);
         if (rc == SR3D_OK) rc = chain_iteration(i);
-        if (rc == SR3D_OK) ec = cudaEventRecord(g_batch.ev[i], p.stream);
-        if (ec == cudaSuccess && rc == SR3D_OK) ec = cudaStreamWaitEvent(g_batch.main, g_batch.ev[i], 0);
-      }
-      cudaError_t ee = cudaStreamEndCapture(g_batch.main, &graph);
-      if (rc != SR3D_OK || ec != cudaSuccess || ee != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
+        cudaGraph_t out = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(p.stream, &out);
         if (rc != SR3D_OK) return rc;
-        return fail(SR3D_ERR_CUDA, "batched graph capture: %s",
-                    cudaGetErrorString(ec != cudaSuccess ? ec : ee));
+        if (ee != cudaSuccess) return fail(SR3D_ERR_CUDA, "batched graph capture: %s", cudaGetErrorString(ee));
+        const int prio = chain.size() > 1
+                             ? prio_greatest + (int)((long long)(prio_least - prio_greatest) * rank[c] /
+                                                     (long long)(chain.size() - 1))
+                             : prio_least;
+        size_t nn = 0;
+        CK(cudaGraphGetNodes(graph, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        CK(cudaGraphGetNodes(graph, nodes.data(), &nn));
+        for (cudaGraphNode_t nd : nodes) {
+          if (std::find(seen.begin(), seen.end(), nd) != seen.end()) continue;
+          seen.push_back(nd);
+          cudaGraphNodeType t;
+          CK(cudaGraphNodeGetType(nd, &t));
+          if (t != cudaGraphNodeTypeKernel) continue;
+          cudaLaunchAttributeValue v;
+          memset(&v, 0, sizeof(v));
+          v.priority = prio;
+          CK(cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributePriority, &v));
+        }
       }
-      ee = cudaGraphInstantiate(&g_batch.exec, graph, 0);
-      cudaGraphDestroy(graph);
+      cudaError_t ee = cudaGraphInstantiate(&g_batch.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
       if (ee != cudaSuccess) {
         g_batch.exec = nullptr;
         return fail(SR3D_ERR_CUDA, "batched graph instantiate: %s", cudaGetErrorString(ee));
@@ -1744,18 +1877,14 @@ extern "C" int sr3d_admm_tv_batched(int n, sr3d_plan_t* plans, const void* const
       g_batch.key_ptr = kp;
       g_batch.key_val = kv;
     }
-    // the graph starts after every plan's queued work
-    for (int i = 0; i < n; ++i) {
-      CK(cudaEventRecord(g_batch.ev[i], plans[i]->p.stream));
-      CK(cudaStreamWaitEvent(g_batch.main, g_batch.ev[i], 0));
-    }
+    // the graph starts after every plan's queued work; later work on the
+    // plans' streams starts after it
+    TRY(join_to_main());
     for (int r = 0; r < pairs; ++r) {
       CK(cudaGraphLaunch(g_batch.exec, g_batch.main));
       for (int k = 0; k < 8; ++k) plans[0]->p.launches[k] += g_batch.launches[k];
     }
-    // later work on the plans' streams starts after the graph
-    CK(cudaEventRecord(g_batch.ev[n], g_batch.main));
-    for (int i = 0; i < n; ++i) CK(cudaStreamWaitEvent(plans[i]->p.stream, g_batch.ev[n], 0));
+    TRY(fork_from_main());
     it += 2 * pairs;
   }
   while (it < iters) {
