@@ -114,23 +114,25 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b
 }
 
 // ---------------------------------------------------------------------------
-// first layer (one input channel, 16 outputs): a 32 x 8 tile of voxels per
+// first layer (one input channel, 16 outputs): a 128 x 8 tile of voxels per
 // CTA marches over s with a ring of three x planes (with halo) in shared
-// memory; each thread forms its voxel's 16 outputs from the 27 neighbours in
-// FP32 (432 FMAs; the weights are read as shared-memory broadcasts) and
-// stores them as two 16-byte BF16 vectors.  The contraction is too thin for
-// the tensor cores (K = 27, one input channel).
+// memory; each thread forms the 16 outputs of four consecutive voxels along m
+// from their 27 neighbours in FP32 (432 FMAs per voxel, every weight vector
+// read as a shared-memory broadcast once per four voxels, the six x values of
+// a neighbour row as one float4 and one float2) and stores them as 16-byte
+// BF16 vectors.  The contraction is too thin for the tensor cores (K = 27,
+// one input channel).
 // ---------------------------------------------------------------------------
-constexpr int F_TM = 32, F_TN = 8, F_TS = 8;
+constexpr int F_TM = 32, F_TN = 8, F_TS = 8, F_VM = 4;  // threads along m and n, planes per CTA, voxels per thread
 __global__ void __launch_bounds__(F_TM * F_TN, 2) k_conv_first(const bf16* __restrict__ x, const float* __restrict__ W,
                                                             const float* __restrict__ bias, bf16* __restrict__ out,
                                                             int M, int N, int S) {
-  constexpr int HW = F_TM + 2, HH = F_TN + 2;
-  __shared__ float xs[3][HH * HW];
-  __shared__ float ws[27][16];
+  constexpr int HM = F_TM * F_VM + 2, HW = HM + 2, HH = F_TN + 2;  // halo row m0-1 .. m0+128, padded to 16 bytes
+  __shared__ __align__(16) float xs[3][HH * HW];
+  __shared__ __align__(16) float ws[27][16];
   __shared__ float bs[16];
   const int tx = threadIdx.x % F_TM, ty = threadIdx.x / F_TM, tid = threadIdx.x;
-  const int m0 = blockIdx.x * F_TM, n0 = blockIdx.y * F_TN, s0 = blockIdx.z * F_TS;
+  const int m0 = blockIdx.x * F_TM * F_VM, n0 = blockIdx.y * F_TN, s0 = blockIdx.z * F_TS;
   const int s_end = min(S, s0 + F_TS);
   for (int i = tid; i < 27 * 16; i += F_TM * F_TN) ws[i % 27][i / 27] = W[i];  // W is [co][tap]
   if (tid < 16) bs[tid] = bias[tid];
@@ -138,44 +140,67 @@ __global__ void __launch_bounds__(F_TM * F_TN, 2) k_conv_first(const bf16* __res
     for (int i = tid; i < HH * HW; i += F_TM * F_TN) {
       const int hn = i / HW, hm = i - hn * HW, m = m0 - 1 + hm, n = n0 - 1 + hn;
       float v = 0.f;
-      if (ps >= 0 && ps < S && n >= 0 && n < N && m >= 0 && m < M)
+      if (hm < HM && ps >= 0 && ps < S && n >= 0 && n < N && m >= 0 && m < M)
         v = __bfloat162float(x[((long long)ps * N + n) * M + m]);
       buf[i] = v;
     }
   };
   load_plane(s0 - 1, xs[0]);
   load_plane(s0, xs[1]);
-  const int m = m0 + tx, n = n0 + ty;
+  const int n = n0 + ty;
   int r0 = 0;  // ring slot of plane s-1; s in r0+1, s+1 in r0+2 (mod 3)
   for (int s = s0; s < s_end; ++s) {
     load_plane(s + 1, xs[(r0 + 2) % 3]);
     __syncthreads();
-    float acc[16];
+    float acc[F_VM][16];
 #pragma unroll
-    for (int c = 0; c < 16; ++c) acc[c] = bs[c];
+    for (int v = 0; v < F_VM; ++v)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[v][c] = bs[c];
 #pragma unroll
     for (int ds = 0; ds < 3; ++ds) {
       const float* xp = xs[(r0 + ds) % 3];
 #pragma unroll
-      for (int dn = 0; dn < 3; ++dn)
+      for (int dn = 0; dn < 3; ++dn) {
+        const float* xr = xp + (ty + dn) * HW + tx * F_VM;
+        const float4 xa = *reinterpret_cast<const float4*>(xr);
+        const float2 xb = *reinterpret_cast<const float2*>(xr + 4);
+        const float xv[F_VM + 2] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y};
 #pragma unroll
         for (int dm = 0; dm < 3; ++dm) {
-          const float v = xp[(ty + dn) * HW + tx + dm];
-          const float* w = ws[(ds * 3 + dn) * 3 + dm];
+          const float4* w4 = reinterpret_cast<const float4*>(ws[(ds * 3 + dn) * 3 + dm]);
+          float w[16];
 #pragma unroll
-          for (int c = 0; c < 16; ++c) acc[c] = fmaf(w[c], v, acc[c]);
+          for (int q = 0; q < 4; ++q) {
+            const float4 t = w4[q];
+            w[4 * q] = t.x;
+            w[4 * q + 1] = t.y;
+            w[4 * q + 2] = t.z;
+            w[4 * q + 3] = t.w;
+          }
+#pragma unroll
+          for (int v = 0; v < F_VM; ++v)
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[v][c] = fmaf(w[c], xv[v + dm], acc[v][c]);
         }
-    }
-    if (m < M && n < N) {
-      uint32_t pk[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(fmaxf(acc[2 * q], 0.f), fmaxf(acc[2 * q + 1], 0.f));
-        pk[q] = *reinterpret_cast<const uint32_t*>(&h);
       }
-      uint4* o = reinterpret_cast<uint4*>(out + (((long long)s * N + n) * M + m) * 16);
-      o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+    }
+    if (n < N) {
+#pragma unroll
+      for (int v = 0; v < F_VM; ++v) {
+        const int m = m0 + tx * F_VM + v;
+        if (m >= M) break;
+        uint32_t pk[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const __nv_bfloat162 h =
+              __floats2bfloat162_rn(fmaxf(acc[v][2 * q], 0.f), fmaxf(acc[v][2 * q + 1], 0.f));
+          pk[q] = *reinterpret_cast<const uint32_t*>(&h);
+        }
+        uint4* o = reinterpret_cast<uint4*>(out + (((long long)s * N + n) * M + m) * 16);
+        o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+      }
     }
     __syncthreads();
     r0 = (r0 + 1) % 3;
@@ -696,25 +721,52 @@ __global__ void k_relu_mask(bf16* __restrict__ g, const bf16* __restrict__ y, lo
     if (!(__bfloat162float(y[i]) > 0.f)) g[i] = __float2bfloat16(0.f);
 }
 
-// 2x2x2 max pooling of x (full size M, N, S, C channels); the first maximum
-// in (s, n, m) order wins
+// 2x2x2 max pooling of x (full size M, N, S, C channels, C a multiple of 8);
+// the first maximum in (s, n, m) order wins.  A thread takes 8 channels of
+// one pooled voxel: 16-byte loads of the 8 children, one 16-byte store of the
+// maxima and one 8-byte store of their child indices.
 __global__ void k_maxpool(const bf16* __restrict__ x, bf16* __restrict__ y, unsigned char* __restrict__ idx, int M,
                           int N, int S, int C) {
-  const long long total = (long long)(M / 2) * (N / 2) * (S / 2) * C;
+  const int CG = C / 8;
+  const long long total = (long long)(M / 2) * (N / 2) * (S / 2) * CG;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(i % C);
-    const long long v = i / C;
+    const int c0 = (int)(i % CG) * 8;
+    const long long v = i / CG;
     const int m2 = (int)(v % (M / 2)), n2 = (int)((v / (M / 2)) % (N / 2)), s2 = (int)(v / ((long long)(M / 2) * (N / 2)));
-    float best = -INFINITY;
-    int bi = 0;
+    float best[8];
+    int bi[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      best[k] = -INFINITY;
+      bi[k] = 0;
+    }
+#pragma unroll
     for (int q = 0; q < 8; ++q) {
       const int s = 2 * s2 + (q >> 2), n = 2 * n2 + ((q >> 1) & 1), m = 2 * m2 + (q & 1);
-      const float val = __bfloat162float(x[(((long long)s * N + n) * M + m) * C + c]);
-      if (val > best) { best = val; bi = q; }
+      const uint4 raw = __ldg(reinterpret_cast<const uint4*>(x + (((long long)s * N + n) * M + m) * C + c0));
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 f = __bfloat1622float2(h[k]);
+        if (f.x > best[2 * k]) { best[2 * k] = f.x; bi[2 * k] = q; }
+        if (f.y > best[2 * k + 1]) { best[2 * k + 1] = f.y; bi[2 * k + 1] = q; }
+      }
     }
-    y[i] = __float2bfloat16(best);
-    idx[i] = (unsigned char)bi;
+    uint32_t pk[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __nv_bfloat162 h2 = __floats2bfloat162_rn(best[2 * k], best[2 * k + 1]);
+      pk[k] = *reinterpret_cast<const uint32_t*>(&h2);
+    }
+    *reinterpret_cast<uint4*>(y + v * C + c0) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    uint32_t ix0 = 0, ix1 = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ix0 |= (uint32_t)bi[k] << (8 * k);
+      ix1 |= (uint32_t)bi[k + 4] << (8 * k);
+    }
+    *reinterpret_cast<uint2*>(idx + v * C + c0) = make_uint2(ix0, ix1);
   }
 }
 
@@ -760,9 +812,14 @@ __global__ void k_head_fwd(const bf16* __restrict__ d1, const float* __restrict_
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
     float acc = wh[C];
 #pragma unroll
-    for (int c = 0; c < C; c += 2) {
-      const float2 dv = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(d1 + v * C + c));
-      acc += wh[c] * dv.x + wh[c + 1] * dv.y;
+    for (int c8 = 0; c8 < C; c8 += 8) {
+      const uint4 raw = __ldg(reinterpret_cast<const uint4*>(d1 + v * C + c8));
+      const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&raw);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float2 dv = __bfloat1622float2(h[k]);
+        acc += wh[c8 + 2 * k] * dv.x + wh[c8 + 2 * k + 1] * dv.y;
+      }
     }
     out[v] = acc + x[v];
   }
@@ -962,7 +1019,7 @@ static int ensure_size(sr3d_unet_s* u, int M, int N, int S) {
 // first layer: one input channel, 16 outputs, bias and ReLU
 static cudaError_t conv_first(cudaStream_t st, const bf16* x, const float* W, const float* bias, bf16* out, int M,
                               int N, int S) {
-  dim3 grid((M + F_TM - 1) / F_TM, (N + F_TN - 1) / F_TN, (S + F_TS - 1) / F_TS);
+  dim3 grid((M + F_TM * F_VM - 1) / (F_TM * F_VM), (N + F_TN - 1) / F_TN, (S + F_TS - 1) / F_TS);
   k_conv_first<<<grid, F_TM * F_TN, 0, st>>>(x, W, bias, out, M, N, S);
   return cudaGetLastError();
 }
@@ -1098,10 +1155,10 @@ static int unet_forward(sr3d_unet_s* u, const float* x) {
   UCK(cudaGetLastError());
   UCK(conv_first(st, u->xb, u->p + u->off_w[0], bias(0), u->e1a, M, N, S));
   UCK(conv_layer(u, 1, false, cin(u->e1a, C1, 0, nullptr, 0, M, N, S), bias(1), 1, u->e1));
-  k_maxpool<<<grid_for(V2 * C1), 256, 0, st>>>(u->e1, u->p1, u->i1, M, N, S, C1);
+  k_maxpool<<<grid_for(V2 * C1 / 8), 256, 0, st>>>(u->e1, u->p1, u->i1, M, N, S, C1);
   UCK(conv_layer(u, 2, false, cin(u->p1, C1, 0, nullptr, 0, M / 2, N / 2, S / 2), bias(2), 1, u->e2a));
   UCK(conv_layer(u, 3, false, cin(u->e2a, C2, 0, nullptr, 0, M / 2, N / 2, S / 2), bias(3), 1, u->e2));
-  k_maxpool<<<grid_for(V4 * C2), 256, 0, st>>>(u->e2, u->p2, u->i2, M / 2, N / 2, S / 2, C2);
+  k_maxpool<<<grid_for(V4 * C2 / 8), 256, 0, st>>>(u->e2, u->p2, u->i2, M / 2, N / 2, S / 2, C2);
   UCK(conv_layer(u, 4, false, cin(u->p2, C2, 0, nullptr, 0, M / 4, N / 4, S / 4), bias(4), 1, u->e3a));
   UCK(conv_layer(u, 5, false, cin(u->e3a, C3, 0, nullptr, 0, M / 4, N / 4, S / 4), bias(5), 1, u->e3));
   UCK(conv_layer(u, 6, false, cin(u->e3, C3, 1, u->e2, C2, M / 2, N / 2, S / 2), bias(6), 1, u->d2a));
