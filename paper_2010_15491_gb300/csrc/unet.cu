@@ -369,8 +369,10 @@ __global__ void __launch_bounds__(256) k_conv3(ConvIn in, const bf16* __restrict
 // in the canonical no-swizzle K-major layout (8 voxels x 16 bytes per core
 // matrix, 16-byte rows consecutive along m, channel chunks a fixed stride
 // apart), so a shifted tap is just a shifted descriptor start address.  Two
-// TMEM accumulators alternate: while the tensor core works on line s, the four
-// warps drain line s-1 (tcgen05.ld, bias, ReLU, BF16 stores).  Every wait on
+// TMEM accumulators alternate: while the tensor core works on line s, warps
+// 0-3 drain line s-1 (tcgen05.ld of their TMEM lane quarter, bias, ReLU,
+// BF16 stores) and a fifth warp, whose lane 0 issues the MMAs, shares the
+// plane loads, so issuing and draining overlap.  Every wait on
 // the MMA-completion barrier is bounded (about one second of clock); on
 // timeout the CTA sets *err and skips its stores.
 // ---------------------------------------------------------------------------
@@ -454,8 +456,9 @@ struct Cfg {
 }  // namespace tc
 
 // wu: [27][CIN/8][COUT][8] BF16 (UMMA K-major slices)
+constexpr int TC_THREADS = 160;  // four epilogue warps and the MMA-issuing warp
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(128, 1) k_conv3_tc(ConvIn in, const bf16* __restrict__ wu,
+__global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(ConvIn in, const bf16* __restrict__ wu,
                                                      const float* __restrict__ bias, int relu, bf16* __restrict__ out,
                                                      int SC, int* __restrict__ err) {
   using C = tc::Cfg<CIN, COUT>;
@@ -485,11 +488,11 @@ __global__ void __launch_bounds__(128, 1) k_conv3_tc(ConvIn in, const bf16* __re
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // resident weights
-  for (int i = tid; i < 27 * C::CH * COUT; i += 128) cpz16(wsm + i * 16, wu + (long long)i * 8, true);
+  for (int i = tid; i < 27 * C::CH * COUT; i += TC_THREADS) cpz16(wsm + i * 16, wu + (long long)i * 8, true);
   // one input plane (rows n-1..n+1, m0-1..m0+128) into its ring slot; zero outside the volume
   auto load_plane = [&](int ps) {
     const int slot = ((ps % C::RING) + C::RING) % C::RING;
-    for (int i = tid; i < 3 * C::HMP * C::CH; i += 128) {
+    for (int i = tid; i < 3 * C::HMP * C::CH; i += TC_THREADS) {
       const int c = i % C::CH, rest = i / C::CH, hm = rest % C::HMP, li = rest / C::HMP;
       const int m = m0 - 1 + hm, nn = n - 1 + li;
       const bool ok = ps >= 0 && ps < in.S && nn >= 0 && nn < in.N && m >= 0 && m < in.M;
@@ -511,6 +514,7 @@ __global__ void __launch_bounds__(128, 1) k_conv3_tc(ConvIn in, const bf16* __re
   bool ok = true;
 
   auto epilogue = [&](int jj, int s) {
+    if (warp >= 4) return true;  // the MMA-issuing warp holds no TMEM lanes
     if (!tc::wait_bar(&bars[jj & 1], (uint32_t)((jj >> 1) & 1))) return false;
     tc::fence_after();
     const int m = m0 + 32 * warp + lane;
@@ -549,19 +553,31 @@ __global__ void __launch_bounds__(128, 1) k_conv3_tc(ConvIn in, const bf16* __re
   for (int s = s0; s < s_end; ++s, ++j) {
     if (s + 1 < s_end) load_plane(s + 2);  // needed by line s+1; its slot held plane s-3, drained at step j-1
     cp_commit_();
-    if (tid == 0) {
+    if (warp == 4 && lane == 0) {
+      // The issuing thread bounds the step (every thread meets it at the
+      // step's barrier), so the descriptors are formed from per-step bases
+      // with the taps unrolled: the address field of each is
+      // one add on the base of its ring plane (or of the weights) plus a
+      // compile-time offset, the other fields are constant.
       const uint32_t d = tmem + (uint32_t)((j & 1) * 64);
-      uint32_t acc = 0;
-#pragma unroll 1
+      const int slot0 = (((s - 1) % C::RING) + C::RING) % C::RING;
+      uint32_t abase[3];  // address field (>> 4) of ring row (plane s+ds-1, dn = 0, dm = 0, chunk 0)
+#pragma unroll
+      for (int ds = 0; ds < 3; ++ds) {
+        const int slot = slot0 + ds >= C::RING ? slot0 + ds - C::RING : slot0 + ds;
+        abase[ds] = (hbase >> 4) + (uint32_t)(slot * 3 * C::HMP);
+      }
+      const uint32_t wb4 = wbase >> 4;
+      const uint64_t ahi = tc::sdesc(0, C::LBO_A, 128), bhi = tc::sdesc(0, COUT * 16, 128);
+#pragma unroll
       for (int tap = 0; tap < 27; ++tap) {
         const int dm = tap % 3, dn = (tap / 3) % 3, ds = tap / 9;
-        const int line = (((s + ds - 1) % C::RING + C::RING) % C::RING) * 3 + dn;
 #pragma unroll
         for (int kk = 0; kk < CIN / 16; ++kk) {
-          const uint64_t a = tc::sdesc(hbase + (uint32_t)(((2 * kk * C::LINES + line) * C::HMP + dm) * 16), C::LBO_A, 128);
-          const uint64_t bd = tc::sdesc(wbase + (uint32_t)((tap * C::CH + 2 * kk) * COUT * 16), COUT * 16, 128);
-          tc::mma(d, a, bd, C::IDESC, acc);
-          acc = 1;
+          const uint32_t a4 = abase[ds] + (uint32_t)((2 * kk * C::LINES + dn) * C::HMP + dm);
+          const uint32_t b4 = wb4 + (uint32_t)((tap * C::CH + 2 * kk) * COUT);
+          tc::mma(d, ahi | (uint64_t)(a4 & 0x3FFF), bhi | (uint64_t)(b4 & 0x3FFF), C::IDESC,
+                  (tap | kk) != 0 ? 1u : 0u);
         }
       }
       tc::commit(&bars[j & 1]);
@@ -1046,7 +1062,7 @@ static cudaError_t conv3_tc_t(cudaStream_t st, const ConvIn& in, const bf16* wu,
   sc = sc < 8 ? 8 : (sc > 64 ? 64 : sc);
   if (sc > in.S) sc = in.S;
   const long long blocks = (long long)(in.M / 128) * in.N * ((in.S + sc - 1) / sc);
-  k_conv3_tc<CIN, COUT><<<(unsigned)blocks, 128, C::SMEM, st>>>(in, wu, bias, relu, out, sc, err);
+  k_conv3_tc<CIN, COUT><<<(unsigned)blocks, TC_THREADS, C::SMEM, st>>>(in, wu, bias, relu, out, sc, err);
   return cudaGetLastError();
 }
 
