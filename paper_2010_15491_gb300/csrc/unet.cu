@@ -136,22 +136,40 @@ __global__ void __launch_bounds__(F_TM * F_TN, 2) k_conv_first(const bf16* __res
   const int s_end = min(S, s0 + F_TS);
   for (int i = tid; i < 27 * 16; i += F_TM * F_TN) ws[i % 27][i / 27] = W[i];  // W is [co][tap]
   if (tid < 16) bs[tid] = bias[tid];
-  auto load_plane = [&](int ps, float* buf) {
-    for (int i = tid; i < HH * HW; i += F_TM * F_TN) {
+  // a plane's halo tile is fetched into registers (FP = its values per
+  // thread) one step ahead and stored to its ring slot after the step's
+  // compute, so the loads' latency overlaps the FMAs
+  constexpr int FP = (HH * HW + F_TM * F_TN - 1) / (F_TM * F_TN);
+  float pre[FP];
+  auto fetch_plane = [&](int ps) {
+#pragma unroll
+    for (int k = 0; k < FP; ++k) {
+      const int i = tid + k * F_TM * F_TN;
       const int hn = i / HW, hm = i - hn * HW, m = m0 - 1 + hm, n = n0 - 1 + hn;
       float v = 0.f;
-      if (hm < HM && ps >= 0 && ps < S && n >= 0 && n < N && m >= 0 && m < M)
+      if (i < HH * HW && hm < HM && ps >= 0 && ps < S && n >= 0 && n < N && m >= 0 && m < M)
         v = __bfloat162float(x[((long long)ps * N + n) * M + m]);
-      buf[i] = v;
+      pre[k] = v;
     }
   };
-  load_plane(s0 - 1, xs[0]);
-  load_plane(s0, xs[1]);
+  auto store_plane = [&](float* buf) {
+#pragma unroll
+    for (int k = 0; k < FP; ++k) {
+      const int i = tid + k * F_TM * F_TN;
+      if (i < HH * HW) buf[i] = pre[k];
+    }
+  };
+  fetch_plane(s0 - 1);
+  store_plane(xs[0]);
+  fetch_plane(s0);
+  store_plane(xs[1]);
+  fetch_plane(s0 + 1);
+  store_plane(xs[2]);
   const int n = n0 + ty;
   int r0 = 0;  // ring slot of plane s-1; s in r0+1, s+1 in r0+2 (mod 3)
   for (int s = s0; s < s_end; ++s) {
-    load_plane(s + 1, xs[(r0 + 2) % 3]);
-    __syncthreads();
+    __syncthreads();  // plane s+1 is stored (in the slot that held plane s-2)
+    if (s + 2 < s_end + 1) fetch_plane(s + 2);
     float acc[F_VM][16];
 #pragma unroll
     for (int v = 0; v < F_VM; ++v)
@@ -202,7 +220,8 @@ __global__ void __launch_bounds__(F_TM * F_TN, 2) k_conv_first(const bf16* __res
         o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
       }
     }
-    __syncthreads();
+    __syncthreads();  // every thread is done with plane s-1's slot
+    if (s + 2 < s_end + 1) store_plane(xs[r0]);  // plane s+2 into the slot of plane s-1
     r0 = (r0 + 1) % 3;
   }
 }
