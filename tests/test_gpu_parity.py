@@ -390,6 +390,35 @@ def test_separable_psf_path(lib, dtype):
     plan.close()
 
 
+@pytest.mark.parametrize("dims,dec", [((96, 48, 192), (2, 2, 2)), ((384, 16, 96), (2, 2, 1)),
+                                      ((192, 96, 96), (1, 1, 4))])
+def test_separable_psf_3x2a_compile_time_plans(lib, dims, dec):
+    """The separable-PSF class solve on the compile-time plans of 3 * 2^a
+    lengths (12 elements per thread): m half-lengths 48, 192 and 96 through
+    the register real-FFT split (d_r 2, 2, 1), n lengths 48 and 96, and the
+    register-resident s pass at 192 and 96 points for the three class shapes
+    (Lambda formed from the three 1-D factors inside the solve).  Tikhonov and
+    six ADMM-TV iterates against the oracle in FP32."""
+    import torch
+    psf = _separable_asym_psf((5, 3, 7), 91)
+    _, xt, _ = make_problem(dims, dec, seed=92)
+    clean = O.forward(xt, psf, dec)
+    import synth
+    y = clean + synth.noise_sigma(clean, 40.0) * synth.noise_field(clean.shape, 93)
+    plan = lib.Plan(dims, dec, psf, "f32")
+    assert plan.separable()
+    yd = T(y, "f32")
+    xk = plan.tikhonov(yd, 1e-2, xbar="nearest")
+    xa = plan.empty_hr()
+    d = torch.zeros((3,) + plan.hr_shape, dtype=plan.tdtype, device="cuda")
+    plan.admm_tv(yd, xa, 2e-3, 1e-2, 6, d=d, tau_init=1e-2)
+    x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
+    ref = O.admm_tv(y, psf, dec, 2e-3, 1e-2, 6, x0)
+    assert rel_l2(H(xk), x0) < TOL["f32"]
+    assert rel_l2(H(xa), ref["x"]) < TOL["f32"]
+    plan.close()
+
+
 # ---------------------------------------------------------------------------
 # other regularisers through the same x-update
 # ---------------------------------------------------------------------------
