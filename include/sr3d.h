@@ -315,8 +315,8 @@ int sr3d_unet_train_step(sr3d_unet_t net, int m, int n, int s, const float* x_de
  * persistent CTA per row marching over s) takes levels whose m extent is a
  * multiple of 128 with 16, 32 or 48 input and output channels; the mma.sync
  * kernel takes every shape.  SR3D_UNET_PATH_TCGEN05 (default): tcgen05 for
- * the shapes where it is the faster one (16 -> 16 channels), mma.sync for the
- * rest; SR3D_UNET_PATH_MMA: mma.sync everywhere; SR3D_UNET_PATH_TCGEN05_ALL:
+ * the shapes where it is the faster one (16 -> 16 and 16 -> 32 channels),
+ * mma.sync for the rest; SR3D_UNET_PATH_MMA: mma.sync everywhere; SR3D_UNET_PATH_TCGEN05_ALL:
  * tcgen05 wherever it applies.  All compute the same convolution with FP32
  * accumulation (the order of the sums differs).  A tcgen05 wait that runs out
  * (about one second) makes the calling entry point return SR3D_ERR_TIMEOUT. */

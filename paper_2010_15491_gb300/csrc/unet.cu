@@ -1088,13 +1088,15 @@ static cudaError_t conv3_tc_t(cudaStream_t st, const ConvIn& in, const bf16* wu,
 // the tcgen05 kernel takes levels whose m extent is a multiple of 128 and
 // 16, 32 or 48 input and output channels; returns cudaErrorNotSupported
 // otherwise.  With all_shapes false only the shapes where it beats the
-// mma.sync kernel are taken: measured at 256^3, (16, 16) 1.15 ms against
-// 1.28 ms, while N = 32 or 48-column MMAs per 128 voxels leave the other
-// shapes slower ((48, 16) 6.4 ms against 2.9 ms).
+// mma.sync kernel are taken: (16, 16) and (16, 32).  Measured in the U-Net
+// forward at 256^3 (levels 256^3 and 128^3): (16, 16) 0.70 ms against 1.29 ms,
+// (16, 32) 0.16 against 0.23 ms, while the rings of 32 and 48 input channels
+// leave one CTA per SM ((32, 32) 0.42 against 0.33 ms, (48, 16) 5.0 against
+// 2.9 ms).
 static cudaError_t conv3_tc(cudaStream_t st, int cin, int cout, const ConvIn& in, const bf16* wu, const float* bias,
                             int relu, bf16* out, int* err, bool all_shapes) {
   if (in.M % 128 != 0) return cudaErrorNotSupported;
-  if (!all_shapes && !(cin == 16 && cout == 16)) return cudaErrorNotSupported;
+  if (!all_shapes && !(cin == 16 && (cout == 16 || cout == 32))) return cudaErrorNotSupported;
 #define SR3D_CONV3_TC(CI, CO) \
   if (cin == CI && cout == CO) return conv3_tc_t<CI, CO>(st, in, wu, bias, relu, out, err);
   SR3D_CONV3_TC(16, 16)
