@@ -244,14 +244,22 @@ __device__ __forceinline__ void cp_commit_() { asm volatile("cp.async.commit_gro
 template <int N>
 __device__ __forceinline__ void cp_wait_() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-template <int CIN, int COUT, int MT>
+template <int CIN, int COUT, int MT, int UPC = 0>
 struct Conv3Cfg {
   static constexpr int TM = 16, TN = 4, TS = 2 * MT;
   static constexpr int HM = TM + 2, HN = TN + 2, HS = TS + 2;
   static constexpr int HV = HM * HN * HS;
   static constexpr int CH = CIN / 8;           // 16-byte chunks per voxel row
   static constexpr int VST = CIN * 2 + 16;     // padded row: an odd number of chunks, conflict-free ldmatrix
-  static constexpr int HALO = HV * VST;
+  // UPC > 0: the first UPC input channels are a nearest-upsampled source; its
+  // brick (with halo) is kept at the source's own half resolution, and the
+  // full-resolution brick holds the other CIN - UPC channels
+  static constexpr int CF = CIN - UPC;
+  static constexpr int VSTF = CF * 2 + 16;
+  static constexpr int HMH = TM / 2 + 2, HNH = TN / 2 + 2, HSH = TS / 2 + 2;
+  static constexpr int HVH = UPC > 0 ? HMH * HNH * HSH : 0;
+  static constexpr int VSTU = UPC * 2 + 16;
+  static constexpr int HALO = HV * VSTF + HVH * VSTU;
   static constexpr int WBYTES = COUT * VST;    // one tap's weights, rows n (out), CIN wide
   static constexpr int SMEM = HALO + 2 * WBYTES;
 };
@@ -277,13 +285,18 @@ __device__ __forceinline__ void conv3_load_w(unsigned char* dst, const bf16* __r
   }
 }
 
-// wt: [27][COUT][CIN] BF16 (tap-major slices, rows = output channel)
-template <int CIN, int COUT, int MT>
+// wt: [27][COUT][CIN] BF16 (tap-major slices, rows = output channel).  With
+// UPC > 0 the input is (nearest-upsampled src0 with UPC channels, src1) and
+// M, N, S are even: the upsampled channels are read from their half-resolution
+// brick, each lane addressing the source voxel of its own voxel row, so the
+// products and their order are those of the plain kernel.
+template <int CIN, int COUT, int MT, int UPC = 0>
 __global__ void __launch_bounds__(256) k_conv3(ConvIn in, const bf16* __restrict__ wt, const float* __restrict__ bias,
                                                int relu, bf16* __restrict__ out) {
-  using C = Conv3Cfg<CIN, COUT, MT>;
+  using C = Conv3Cfg<CIN, COUT, MT, UPC>;
   extern __shared__ __align__(16) unsigned char smem[];
-  unsigned char* halo = smem;
+  unsigned char* halo = smem;                    // full resolution, channels UPC .. CIN-1
+  unsigned char* uhalo = smem + C::HV * C::VSTF;  // UPC > 0: the upsampled source at its resolution
   unsigned char* wbuf = smem + C::HALO;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
@@ -294,12 +307,27 @@ __global__ void __launch_bounds__(256) k_conv3(ConvIn in, const bf16* __restrict
   const int n0 = (b % tilesN) * C::TN;
   const int s0 = (b / tilesN) * C::TS;
 
-  for (int i = threadIdx.x; i < C::HV * C::CH; i += 256) {
-    const int hv = i / C::CH, c = i - hv * C::CH;
+  constexpr int CHF = C::CF / 8;
+  for (int i = threadIdx.x; i < C::HV * CHF; i += 256) {
+    const int hv = i / CHF, c = i - hv * CHF;
     const int hm = hv % C::HM, r = hv / C::HM;
     const int m = m0 + hm - 1, n = n0 + r % C::HN - 1, s = s0 + r / C::HN - 1;
     const bool ok = m >= 0 && m < in.M && n >= 0 && n < in.N && s >= 0 && s < in.S;
-    cpz16(halo + hv * C::VST + c * 16, ok ? chunk_ptr(in, s, n, m, c * 8) : in.src0, ok);
+    cpz16(halo + hv * C::VSTF + c * 16, ok ? chunk_ptr(in, s, n, m, UPC + c * 8) : in.src0, ok);
+  }
+  if constexpr (UPC > 0) {
+    // source voxels (m0/2 - 1 ..) x (n0/2 - 1 ..) x (s0/2 - 1 ..); zero outside
+    constexpr int CHU = UPC / 8;
+    const int Mh = in.M >> 1, Nh = in.N >> 1, Sh = in.S >> 1;
+    const int mh0 = (m0 >> 1) - 1, nh0 = (n0 >> 1) - 1, sh0 = (s0 >> 1) - 1;
+    for (int i = threadIdx.x; i < C::HVH * CHU; i += 256) {
+      const int hv = i / CHU, c = i - hv * CHU;
+      const int hm = hv % C::HMH, r = hv / C::HMH;
+      const int mh = mh0 + hm, nh = nh0 + r % C::HNH, sh = sh0 + r / C::HNH;
+      const bool ok = mh >= 0 && mh < Mh && nh >= 0 && nh < Nh && sh >= 0 && sh < Sh;
+      cpz16(uhalo + hv * C::VSTU + c * 16, ok ? in.src0 + (((long long)sh * Nh + nh) * Mh + mh) * in.c0 + c * 8 : in.src0,
+            ok);
+    }
   }
   conv3_load_w<CIN, COUT, MT>(wbuf, wt, 0);
   cp_commit_();
@@ -322,11 +350,14 @@ __global__ void __launch_bounds__(256) k_conv3(ConvIn in, const bf16* __restrict
     __syncthreads();
     const unsigned char* wb = wbuf + (tap & 1) * C::WBYTES;
     const int dm = tap % 3, dn = (tap / 3) % 3, ds = tap / 9;  // halo offsets (0..2)
-    int arow[MT];
+    int arow[MT], urow[MT];
 #pragma unroll
     for (int i = 0; i < MT; ++i) {
       const int r = warp * MT + i;  // row of 16 voxels: n = r % 4, s = r / 4 within the brick
-      arow[i] = (((r >> 2) + ds) * C::HN + (r & 3) + dn) * C::HM + lr + dm;
+      const int hs = (r >> 2) + ds, hn = (r & 3) + dn, hm = lr + dm;  // full-resolution halo position
+      arow[i] = (hs * C::HN + hn) * C::HM + hm;
+      // its source voxel in the half-resolution brick (halo position h -> ((h - 1) >> 1) + 1)
+      urow[i] = ((((hs - 1) >> 1) + 1) * C::HNH + (((hn - 1) >> 1) + 1)) * C::HMH + (((hm - 1) >> 1) + 1);
     }
 #pragma unroll
     for (int kk = 0; kk < CIN / 16; ++kk) {
@@ -337,7 +368,10 @@ __global__ void __launch_bounds__(256) k_conv3(ConvIn in, const bf16* __restrict
 #pragma unroll
       for (int i = 0; i < MT; ++i) {
         uint32_t a[4];
-        ldsm_x4(a, reinterpret_cast<const bf16*>(halo + arow[i] * C::VST + (kk * 16 + lc) * 2));
+        if (kk * 16 < UPC)
+          ldsm_x4(a, reinterpret_cast<const bf16*>(uhalo + urow[i] * C::VSTU + (kk * 16 + lc) * 2));
+        else
+          ldsm_x4(a, reinterpret_cast<const bf16*>(halo + arow[i] * C::VSTF + (kk * 16 - UPC + lc) * 2));
 #pragma unroll
         for (int np = 0; np < COUT / 16; ++np) {
           mma16816(acc[i][2 * np], a, bfr[np][0], bfr[np][1]);
@@ -1059,14 +1093,15 @@ static cudaError_t conv_first(cudaStream_t st, const bf16* x, const float* W, co
   return cudaGetLastError();
 }
 
-template <int CIN, int COUT, int MT>
+template <int CIN, int COUT, int MT, int UPC = 0>
 static cudaError_t conv3_t(cudaStream_t st, const ConvIn& in, const bf16* wt, const float* bias, int relu, bf16* out) {
-  using C = Conv3Cfg<CIN, COUT, MT>;
-  cudaError_t e = cudaFuncSetAttribute(k_conv3<CIN, COUT, MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+  using C = Conv3Cfg<CIN, COUT, MT, UPC>;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_conv3<CIN, COUT, MT, UPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
   if (e != cudaSuccess) return e;
   const long long blocks = (long long)((in.M + C::TM - 1) / C::TM) * ((in.N + C::TN - 1) / C::TN) *
                            ((in.S + C::TS - 1) / C::TS);
-  k_conv3<CIN, COUT, MT><<<(unsigned)blocks, 256, C::SMEM, st>>>(in, wt, bias, relu, out);
+  k_conv3<CIN, COUT, MT, UPC><<<(unsigned)blocks, 256, C::SMEM, st>>>(in, wt, bias, relu, out);
   return cudaGetLastError();
 }
 
@@ -1112,6 +1147,11 @@ static cudaError_t conv3_tc(cudaStream_t st, int cin, int cout, const ConvIn& in
 // 3x3x3 convolution with cin = in.c0 + in.c1 input channels (a multiple of 16)
 static cudaError_t conv3(cudaStream_t st, int cin, int cout, const ConvIn& in, const bf16* wt, const float* bias,
                          int relu, bf16* out) {
+  // the decoder layers whose first source is upsampled: that source's brick at its own resolution
+  if (in.up0 && in.c1 > 0 && in.M % 2 == 0 && in.N % 2 == 0 && in.S % 2 == 0) {
+    if (cin == 48 && cout == 16 && in.c0 == 32) return conv3_t<48, 16, 2, 32>(st, in, wt, bias, relu, out);
+    if (cin == 96 && cout == 32 && in.c0 == 64) return conv3_t<96, 32, 1, 64>(st, in, wt, bias, relu, out);
+  }
 #define SR3D_CONV3(CI, CO, MT_) \
   if (cin == CI && cout == CO) return conv3_t<CI, CO, MT_>(st, in, wt, bias, relu, out);
   SR3D_CONV3(16, 16, 2)
