@@ -1150,7 +1150,7 @@ static cudaError_t conv3(cudaStream_t st, int cin, int cout, const ConvIn& in, c
   // the decoder layers whose first source is upsampled: that source's brick at its own resolution
   if (in.up0 && in.c1 > 0 && in.M % 2 == 0 && in.N % 2 == 0 && in.S % 2 == 0) {
     if (cin == 48 && cout == 16 && in.c0 == 32) return conv3_t<48, 16, 4, 32>(st, in, wt, bias, relu, out);
-    if (cin == 96 && cout == 32 && in.c0 == 64) return conv3_t<96, 32, 1, 64>(st, in, wt, bias, relu, out);
+    if (cin == 96 && cout == 32 && in.c0 == 64) return conv3_t<96, 32, 2, 64>(st, in, wt, bias, relu, out);
   }
 #define SR3D_CONV3(CI, CO, MT_) \
   if (cin == CI && cout == CO) return conv3_t<CI, CO, MT_>(st, in, wt, bias, relu, out);
