@@ -114,45 +114,74 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b
 }
 
 // ---------------------------------------------------------------------------
-// first layer (one input channel, 16 outputs): a 128 x 8 tile of voxels per
-// CTA marches over s with a ring of three x planes (with halo) in shared
-// memory; each thread forms the 16 outputs of four consecutive voxels along m
-// from their 27 neighbours in FP32 (432 FMAs per voxel, every weight vector
-// read as a shared-memory broadcast once per four voxels, the six x values of
-// a neighbour row as one float4 and one float2) and stores them as 16-byte
-// BF16 vectors.  The contraction is too thin for the tensor cores (K = 27,
-// one input channel).
+// first layer (one input channel, 16 outputs) as an implicit GEMM on the
+// tensor cores: rows = 16 voxels along m, K = the 27 taps (padded to 32, two
+// m16n8k16 chunks), N = the 16 output channels.  A 128 x 8 tile of voxels
+// per CTA marches over s with a ring of three BF16 x planes (with halo) in
+// shared memory; each warp owns one row of 128 voxels, and each lane gathers
+// the tap values of its A fragment (voxel rows g, g+8; taps 2t, 2t+1, 2t+8,
+// 2t+9 of each chunk) straight from the ring.  The weights are rounded to
+// BF16 once per CTA into the lanes' B fragments, as the other layers' are;
+// accumulation in FP32.  The next plane is fetched into registers during the
+// step's MMAs.
 // ---------------------------------------------------------------------------
-constexpr int F_TM = 32, F_TN = 8, F_TS = 8, F_VM = 4;  // threads along m and n, planes per CTA, voxels per thread
+constexpr int F_TM = 32, F_TN = 8, F_TS = 8, F_VM = 4;  // 128 x 8 voxels per CTA (256 threads), planes per CTA
 __global__ void __launch_bounds__(F_TM * F_TN, 2) k_conv_first(const bf16* __restrict__ x, const float* __restrict__ W,
                                                             const float* __restrict__ bias, bf16* __restrict__ out,
                                                             int M, int N, int S) {
-  constexpr int HM = F_TM * F_VM + 2, HW = HM + 2, HH = F_TN + 2;  // halo row m0-1 .. m0+128, padded to 16 bytes
-  __shared__ __align__(16) float xs[3][HH * HW];
-  __shared__ __align__(16) float ws[27][16];
-  __shared__ float bs[16];
-  const int tx = threadIdx.x % F_TM, ty = threadIdx.x / F_TM, tid = threadIdx.x;
-  const int m0 = blockIdx.x * F_TM * F_VM, n0 = blockIdx.y * F_TN, s0 = blockIdx.z * F_TS;
+  constexpr int TMV = F_TM * F_VM;                // voxels along m per row
+  constexpr int HM = TMV + 2, HW = HM + 6, HH = F_TN + 2;  // halo row m0-1 .. m0+128 (padded)
+  __shared__ __align__(16) bf16 xs[3][HH * HW];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int m0 = blockIdx.x * TMV, n0 = blockIdx.y * F_TN, s0 = blockIdx.z * F_TS;
   const int s_end = min(S, s0 + F_TS);
-  for (int i = tid; i < 27 * 16; i += F_TM * F_TN) ws[i % 27][i / 27] = W[i];  // W is [co][tap]
-  if (tid < 16) bs[tid] = bias[tid];
-  // a plane's halo tile is fetched into registers (FP = its values per
-  // thread) one step ahead and stored to its ring slot after the step's
-  // compute, so the loads' latency overlaps the FMAs
+  // B fragments: chunk c, n8 tile j: (b0, b1) = W[8j + g][16c + 2t (+1)], W[8j + g][16c + 2t + 8 (+9)]
+  uint32_t bw[2][2][2];
+  auto wv = [&](int co, int tap) -> float { return tap < 27 ? W[co * 27 + tap] : 0.f; };
+  auto pk = [](float a, float b) -> uint32_t {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  };
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int co = 8 * j + g, k0 = 16 * c + 2 * t;
+      bw[c][j][0] = pk(wv(co, k0), wv(co, k0 + 1));
+      bw[c][j][1] = pk(wv(co, k0 + 8), wv(co, k0 + 9));
+    }
+  const float b_lo0 = bias[2 * t], b_lo1 = bias[2 * t + 1], b_hi0 = bias[8 + 2 * t], b_hi1 = bias[9 + 2 * t];
+  // the lane's taps: k = 16c + 2t + {0, 1, 8, 9}; offset of tap k from the voxel's
+  // (ring row, halo column) and its plane (0..2); taps 27..31 are padding
+  int toff[2][4], tpl[2][4];
+  bool tok[2][4];
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 16 * c + 2 * t + (q & 1) + 8 * (q >> 1);
+      tok[c][q] = k < 27;
+      const int kk = k < 27 ? k : 0;
+      toff[c][q] = ((kk / 3) % 3) * HW + kk % 3;
+      tpl[c][q] = kk / 9;
+    }
+  // a plane's halo tile is fetched into registers (FP values per thread) one
+  // step ahead and stored to its ring slot after the step's MMAs
   constexpr int FP = (HH * HW + F_TM * F_TN - 1) / (F_TM * F_TN);
-  float pre[FP];
+  bf16 pre[FP];
   auto fetch_plane = [&](int ps) {
 #pragma unroll
     for (int k = 0; k < FP; ++k) {
       const int i = tid + k * F_TM * F_TN;
       const int hn = i / HW, hm = i - hn * HW, m = m0 - 1 + hm, n = n0 - 1 + hn;
-      float v = 0.f;
+      bf16 v = __float2bfloat16(0.f);
       if (i < HH * HW && hm < HM && ps >= 0 && ps < S && n >= 0 && n < N && m >= 0 && m < M)
-        v = __bfloat162float(x[((long long)ps * N + n) * M + m]);
+        v = x[((long long)ps * N + n) * M + m];
       pre[k] = v;
     }
   };
-  auto store_plane = [&](float* buf) {
+  auto store_plane = [&](bf16* buf) {
 #pragma unroll
     for (int k = 0; k < FP; ++k) {
       const int i = tid + k * F_TM * F_TN;
@@ -165,62 +194,59 @@ __global__ void __launch_bounds__(F_TM * F_TN, 2) k_conv_first(const bf16* __res
   store_plane(xs[1]);
   fetch_plane(s0 + 1);
   store_plane(xs[2]);
-  const int n = n0 + ty;
+  const int n = n0 + warp;
   int r0 = 0;  // ring slot of plane s-1; s in r0+1, s+1 in r0+2 (mod 3)
   for (int s = s0; s < s_end; ++s) {
     __syncthreads();  // plane s+1 is stored (in the slot that held plane s-2)
     if (s + 2 < s_end + 1) fetch_plane(s + 2);
-    float acc[F_VM][16];
+    // the lane's eight tap pointers for this step (plane of the ring + offset)
+    const bf16* tb[2][4];
 #pragma unroll
-    for (int v = 0; v < F_VM; ++v)
+    for (int c = 0; c < 2; ++c)
 #pragma unroll
-      for (int c = 0; c < 16; ++c) acc[v][c] = bs[c];
+      for (int q = 0; q < 4; ++q) {
+        const int pl = tpl[c][q];
+        tb[c][q] = (pl == 0 ? xs[r0] : pl == 1 ? xs[(r0 + 1) % 3] : xs[(r0 + 2) % 3]) + toff[c][q];
+      }
+#pragma unroll 2
+    for (int tile = 0; tile < TMV / 16; ++tile) {
+      const int rb = warp * HW + tile * 16;  // ring row warp (voxel row n - 1 + dn with dn = 0), column of voxel 0 - 1
+      float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-    for (int ds = 0; ds < 3; ++ds) {
-      const float* xp = xs[(r0 + ds) % 3];
+      for (int c = 0; c < 2; ++c) {
+        uint32_t a[4];
 #pragma unroll
-      for (int dn = 0; dn < 3; ++dn) {
-        const float* xr = xp + (ty + dn) * HW + tx * F_VM;
-        const float4 xa = *reinterpret_cast<const float4*>(xr);
-        const float2 xb = *reinterpret_cast<const float2*>(xr + 4);
-        const float xv[F_VM + 2] = {xa.x, xa.y, xa.z, xa.w, xb.x, xb.y};
+        for (int h = 0; h < 2; ++h) {  // a[0], a[1]: rows g, g+8 of taps 2t, 2t+1; a[2], a[3]: taps 2t+8, 2t+9
 #pragma unroll
-        for (int dm = 0; dm < 3; ++dm) {
-          const float4* w4 = reinterpret_cast<const float4*>(ws[(ds * 3 + dn) * 3 + dm]);
-          float w[16];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 t = w4[q];
-            w[4 * q] = t.x;
-            w[4 * q + 1] = t.y;
-            w[4 * q + 2] = t.z;
-            w[4 * q + 3] = t.w;
+          for (int r = 0; r < 2; ++r) {
+            const int row = rb + g + 8 * r;
+            const int q0 = 2 * h, q1 = 2 * h + 1;
+            const bf16 v0 = tok[c][q0] ? tb[c][q0][row] : __float2bfloat16(0.f);
+            const bf16 v1 = tok[c][q1] ? tb[c][q1][row] : __float2bfloat16(0.f);
+            __nv_bfloat162 pr;
+            pr.x = v0;
+            pr.y = v1;
+            a[2 * h + r] = *reinterpret_cast<const uint32_t*>(&pr);
           }
+        }
+        mma16816(acc[0], a, bw[c][0][0], bw[c][0][1]);
+        mma16816(acc[1], a, bw[c][1][0], bw[c][1][1]);
+      }
+      if (n < N) {
 #pragma unroll
-          for (int v = 0; v < F_VM; ++v)
-#pragma unroll
-            for (int c = 0; c < 16; ++c) acc[v][c] = fmaf(w[c], xv[v + dm], acc[v][c]);
+        for (int r = 0; r < 2; ++r) {
+          const int m = m0 + tile * 16 + g + 8 * r;
+          if (m < M) {
+            bf16* o = out + (((long long)s * N + n) * M + m) * 16;
+            *reinterpret_cast<uint32_t*>(o + 2 * t) =
+                pk(fmaxf(acc[0][2 * r] + b_lo0, 0.f), fmaxf(acc[0][2 * r + 1] + b_lo1, 0.f));
+            *reinterpret_cast<uint32_t*>(o + 8 + 2 * t) =
+                pk(fmaxf(acc[1][2 * r] + b_hi0, 0.f), fmaxf(acc[1][2 * r + 1] + b_hi1, 0.f));
+          }
         }
       }
     }
-    if (n < N) {
-#pragma unroll
-      for (int v = 0; v < F_VM; ++v) {
-        const int m = m0 + tx * F_VM + v;
-        if (m >= M) break;
-        uint32_t pk[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const __nv_bfloat162 h =
-              __floats2bfloat162_rn(fmaxf(acc[v][2 * q], 0.f), fmaxf(acc[v][2 * q + 1], 0.f));
-          pk[q] = *reinterpret_cast<const uint32_t*>(&h);
-        }
-        uint4* o = reinterpret_cast<uint4*>(out + (((long long)s * N + n) * M + m) * 16);
-        o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-        o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
-      }
-    }
-    __syncthreads();  // every thread is done with plane s-1's slot
+    __syncthreads();  // every warp is done with plane s-1's slot
     if (s + 2 < s_end + 1) store_plane(xs[r0]);  // plane s+2 into the slot of plane s-1
     r0 = (r0 + 1) % 3;
   }
@@ -564,7 +590,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_conv3_tc(ConvIn in, const bf1
   tc::fence_after();
   const uint32_t tmem = *tslot;
   const uint32_t hbase = tc::su32(halo), wbase = tc::su32(wsm);
-  bool ok = true;
 
   auto epilogue = [&](int jj, int s) {
     if (warp >= 4) return true;  // the MMA-issuing warp holds no TMEM lanes
