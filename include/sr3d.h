@@ -128,7 +128,8 @@ int sr3d_tikhonov(sr3d_plan_t plan, const void* y_dev, const void* xbar_dev, dou
  *   d_dev   NULL: d0 = 0 and the final d is discarded; else in: d0, out: d.
  *   u0 = L x0.  max_iters >= 0 iterations; tol > 0 stops early when both
  *   relative residuals fall below tol (tested every max(1, eval_every)
- *   iterations; NOT_CONVERGED if max_iters is reached first); tol <= 0 runs
+ *   iterations, on the device: the call waits once for the loop, not once
+ *   per test; NOT_CONVERGED if max_iters is reached first); tol <= 0 runs
  *   exactly max_iters iterations.  stats may be NULL.
  * Errors: INVALID_ARG, SINGULAR (sum of PSF taps zero), NUMERIC, CUDA,
  * NOT_CONVERGED. */

@@ -199,6 +199,40 @@ def test_grouped_volumes_equal_single_volume_solves(lib):
         p.close()
 
 
+def test_batched_one_and_zero_iterations_through_the_setup_graph(lib):
+    """Iteration counts 1 and 0 after a grouping has run once: the set-up
+    graph then carries the only iteration (count 1) or none (count 0) and no
+    iteration graph is replayed; counts 2 and 3 follow on the same grouping.
+    Every call equals the single-plan solves bit for bit (0 iterations: the
+    Tikhonov start), and the 0-iteration result matches the oracle's eq. 12."""
+    import torch
+    vols = GROUPED[:5]  # a group of three 64x64x32 d222 volumes and a group of two 96x96x64 d221
+    plans, ys, xs, probs = [], [], [], []
+    for k, (dims, dec, sg, tau) in enumerate(vols):
+        psf, xt, y = make_problem(dims, dec, sigma=(sg, 0.9 * sg, 1.1 * sg), seed=170 + k)
+        p = lib.Plan(dims, dec, psf, "f32", stream=torch.cuda.Stream())
+        plans.append(p)
+        ys.append(torch.tensor(y, dtype=torch.float32, device="cuda"))
+        xs.append(p.empty_hr())
+        probs.append((psf, y, dec, tau))
+    lams, rhos, taus = [2e-3] * len(plans), [1e-2] * len(plans), [v[3] for v in vols]
+    for rep, iters in enumerate((3, 1, 1, 1, 0, 0, 2, 2, 3, 3)):
+        for x in xs:
+            x.fill_(float("nan"))
+        lib.admm_tv_batched(plans, ys, xs, lams, rhos, taus, iters)
+        for k, p in enumerate(plans):
+            single = p.empty_hr()
+            p.admm_tv(ys[k], single, lams[k], rhos[k], iters, tau_init=taus[k])
+            assert torch.equal(single, xs[k]), (rep, iters, k)
+        if iters == 0:
+            x_tik = [x.clone() for x in xs]
+    for k in (0, 3):
+        psf, y, dec, tau = probs[k]
+        assert rel_l2(x_tik[k].cpu().numpy(), O.tikhonov(y, psf, dec, tau, O.nearest_neighbour(y, dec))) < 1e-5, k
+    for p in plans:
+        p.close()
+
+
 @pytest.mark.slow
 def test_full_ragged_batch_against_single_solves(lib):
     """The 64-volume ragged draw of the batch benchmark (sizes 64^3,

@@ -334,6 +334,7 @@ def test_device_tolerance_loop_edges_match_eager(lib, every):
     x0 = O.tikhonov(y, psf, dec, 1e-2, O.nearest_neighbour(y, dec))
     ref = O.admm_tv(y, psf, dec, 2e-3, 1e-2, 4 * every + 1, x0, record=True)
     assert rel_l2(H(runs[0][1][0]), ref["x"]) < TOL["f64"]
+    assert rel_l2(H(runs[0][1][1]), ref["d"]) < TOL["f64"]  # the caller's dual buffer, returned by the loop
     its = [every * j for j in range(1, 5)] + [4 * every + 1]
     assert np.allclose(runs[0][1][2]["objective_hist"], [ref["hist"]["objective"][k - 1] for k in its], rtol=1e-12)
     plan.close()
