@@ -9,7 +9,7 @@ residuals below 1e-4 from three starts:
   warm      Tikhonov -> trained U-Net -> consistent dual.
 The warm start must reach the same tolerance, at the same objective value, in
 fewer iterations than both others and in less wall-clock time than cold,
-the network's inference included.  Cold-start ADMM stays the judge.
+the network's inference included.  Cold-start ADMM stays the reference solution.
 """
 import os
 import time
