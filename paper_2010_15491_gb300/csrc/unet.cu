@@ -435,6 +435,158 @@ __global__ void __launch_bounds__(256) k_conv3(ConvIn in, const bf16* __restrict
   }
 }
 
+// Row-stationary variant for the decoder layer whose input is
+// (nearest-upsampled source with UPC channels, 16 full-resolution channels):
+// a 16 (m) x 4 (n) x 8 (s) output brick, each warp the four n rows of one s
+// plane.  The taps run in nine stages (ds, dm); in each, the weight fragments
+// of the three dn taps sit in registers and each of the warp's six input rows
+// (its four rows and their n halo) is loaded once per channel chunk and feeds
+// every output row it reaches (i = n_in - dn): 9 ldmatrix per 24 MMAs where
+// the tap-by-tap order takes 15.  The full-resolution brick has unpadded
+// 32-byte voxel rows whose two 16-byte chunks are swapped on every other
+// group of four voxels (chunk c of voxel v at c ^ ((v >> 2) & 1)), so the
+// eight consecutive voxels of an ldmatrix matrix fall on distinct banks and
+// three CTAs fit on an SM.  The sums run in another order than k_conv3's.
+template <int CIN, int COUT, int UPC>
+__global__ void __launch_bounds__(256) k_conv3_rs(ConvIn in, const bf16* __restrict__ wt,
+                                                  const float* __restrict__ bias, int relu, bf16* __restrict__ out) {
+  static_assert(CIN - UPC == 16 && UPC > 0 && UPC % 16 == 0 && COUT % 16 == 0, "16 full-resolution channels");
+  constexpr int TM = 16, TN = 4, TS = 8, MT = 4;
+  constexpr int HM = TM + 2, HN = TN + 2, HS = TS + 2, HV = HM * HN * HS;
+  constexpr int HMH = TM / 2 + 2, HNH = TN / 2 + 2, HSH = TS / 2 + 2, HVH = HMH * HNH * HSH;
+  constexpr int VSTU = UPC * 2 + 16;  // upsampled source rows (padded)
+  constexpr int VST = CIN * 2 + 16;   // weight rows (padded)
+  constexpr int WSL = COUT * VST;     // one tap's weights
+  constexpr int WST = 3 * WSL;        // one stage: the taps dn = 0, 1, 2
+  constexpr int FB = HV * 32, UB = HVH * VSTU;
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned char* halo = smem;        // [HV][2 chunks], swizzled
+  unsigned char* uhalo = smem + FB;  // [HVH][VSTU]
+  unsigned char* wbuf = smem + FB + UB;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  const int tilesM = (in.M + TM - 1) / TM, tilesN = (in.N + TN - 1) / TN;
+  int b = blockIdx.x;
+  const int m0 = (b % tilesM) * TM;
+  b /= tilesM;
+  const int n0 = (b % tilesN) * TN;
+  const int s0 = (b / tilesN) * TS;
+
+  for (int i = threadIdx.x; i < HV * 2; i += 256) {
+    const int hv = i >> 1, c = i & 1;
+    const int hm = hv % HM, r = hv / HM;
+    const int m = m0 + hm - 1, n = n0 + r % HN - 1, s = s0 + r / HN - 1;
+    const bool ok = m >= 0 && m < in.M && n >= 0 && n < in.N && s >= 0 && s < in.S;
+    cpz16(halo + hv * 32 + (c ^ ((hv >> 2) & 1)) * 16, ok ? chunk_ptr(in, s, n, m, UPC + c * 8) : in.src0, ok);
+  }
+  {
+    constexpr int CHU = UPC / 8;
+    const int Mh = in.M >> 1, Nh = in.N >> 1, Sh = in.S >> 1;
+    const int mh0 = (m0 >> 1) - 1, nh0 = (n0 >> 1) - 1, sh0 = (s0 >> 1) - 1;
+    for (int i = threadIdx.x; i < HVH * CHU; i += 256) {
+      const int hv = i / CHU, c = i - hv * CHU;
+      const int hm = hv % HMH, r = hv / HMH;
+      const int mh = mh0 + hm, nh = nh0 + r % HNH, sh = sh0 + r / HNH;
+      const bool ok = mh >= 0 && mh < Mh && nh >= 0 && nh < Nh && sh >= 0 && sh < Sh;
+      cpz16(uhalo + hv * VSTU + c * 16, ok ? in.src0 + (((long long)sh * Nh + nh) * Mh + mh) * in.c0 + c * 8 : in.src0,
+            ok);
+    }
+  }
+  // stage st = ds * 3 + dm: the weight slices of taps (ds, dn, dm), dn = 0..2
+  auto load_stage = [&](unsigned char* dst, int st) {
+    const int ds = st / 3, dm = st - 3 * ds;
+    constexpr int CH = CIN / 8;
+    for (int i = threadIdx.x; i < 3 * COUT * CH; i += 256) {
+      const int dn = i / (COUT * CH), rem = i - dn * (COUT * CH);
+      const int n = rem / CH, c = rem - n * CH;
+      const int tap = (ds * 3 + dn) * 3 + dm;
+      cpz16(dst + dn * WSL + n * VST + c * 16, wt + ((long long)tap * COUT + n) * CIN + c * 8, true);
+    }
+  };
+  load_stage(wbuf, 0);
+  cp_commit_();
+
+  float acc[MT][COUT / 8][4];
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < COUT / 8; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+  const int lr = (lane & 7) + 8 * ((lane >> 3) & 1), lc = 8 * (lane >> 4);  // A: voxel row, channel block
+  const int bn = (lane & 7) + 8 * (lane >> 4), bk = 8 * ((lane >> 3) & 1);  // B: out-channel row, k block
+  const int sl = warp;  // the warp's s plane in the brick; its rows i are n = n0 + i
+#pragma unroll 1
+  for (int st = 0; st < 9; ++st) {
+    if (st + 1 < 9) load_stage(wbuf + ((st + 1) & 1) * WST, st + 1);
+    cp_commit_();
+    cp_wait_<1>();
+    __syncthreads();
+    const unsigned char* wb = wbuf + (st & 1) * WST;
+    const int ds = st / 3, dm = st - 3 * ds;
+    const int hs = sl + ds, hm = lr + dm;
+    const int ush = ((hs - 1) >> 1) + 1, umh = ((hm - 1) >> 1) + 1;
+#pragma unroll
+    for (int kk = 0; kk < CIN / 16; ++kk) {
+      uint32_t bfr[3][COUT / 16][4];
+#pragma unroll
+      for (int dn = 0; dn < 3; ++dn)
+#pragma unroll
+        for (int np = 0; np < COUT / 16; ++np)
+          ldsm_x4(bfr[dn][np], reinterpret_cast<const bf16*>(wb + dn * WSL + (np * 16 + bn) * VST + (kk * 16 + bk) * 2));
+#pragma unroll
+      for (int nin = 0; nin < TN + 2; ++nin) {
+        uint32_t a[4];
+        if (kk * 16 < UPC) {
+          const int urow = (ush * HNH + (((nin - 1) >> 1) + 1)) * HMH + umh;
+          ldsm_x4(a, reinterpret_cast<const bf16*>(uhalo + urow * VSTU + (kk * 16 + lc) * 2));
+        } else {
+          const int hv = (hs * HN + nin) * HM + hm;
+          ldsm_x4(a, reinterpret_cast<const bf16*>(halo + hv * 32 + (((lc >> 3) ^ ((hv >> 2) & 1)) * 16)));
+        }
+#pragma unroll
+        for (int dn = 0; dn < 3; ++dn) {
+          const int i = nin - dn;  // output row reached through tap dn
+          if (i >= 0 && i < MT) {
+#pragma unroll
+            for (int np = 0; np < COUT / 16; ++np) {
+              mma16816(acc[i][2 * np], a, bfr[dn][np][0], bfr[dn][np][1]);
+              mma16816(acc[i][2 * np + 1], a, bfr[dn][np][2], bfr[dn][np][3]);
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < MT; ++i) {
+    const int n = n0 + i, s = s0 + sl;
+    if (n >= in.N || s >= in.S) continue;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int m = m0 + g + 8 * half;
+      if (m >= in.M) continue;
+      bf16* o = out + (((long long)s * in.N + n) * in.M + m) * COUT;
+#pragma unroll
+      for (int nt = 0; nt < COUT / 8; ++nt) {
+        const int co = nt * 8 + 2 * t;
+        float x0 = acc[i][nt][2 * half], x1 = acc[i][nt][2 * half + 1];
+        if (bias) {
+          x0 += bias[co];
+          x1 += bias[co + 1];
+        }
+        if (relu) {
+          x0 = fmaxf(x0, 0.f);
+          x1 = fmaxf(x1, 0.f);
+        }
+        *reinterpret_cast<__nv_bfloat162*>(o + co) = __floats2bfloat162_rn(x0, x1);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // tcgen05 (5th-generation tensor core) convolution for levels whose m extent
 // is a multiple of 128 and CIN, COUT in {16, 32, 48}.  A CTA owns one line of
@@ -1130,6 +1282,18 @@ static cudaError_t conv3_t(cudaStream_t st, const ConvIn& in, const bf16* wt, co
   return cudaGetLastError();
 }
 
+template <int CIN, int COUT, int UPC>
+static cudaError_t conv3_rs_t(cudaStream_t st, const ConvIn& in, const bf16* wt, const float* bias, int relu,
+                              bf16* out) {
+  constexpr int HV = 18 * 6 * 10, HVH = 10 * 4 * 6;
+  constexpr int SMEM = HV * 32 + HVH * (UPC * 2 + 16) + 2 * 3 * COUT * (CIN * 2 + 16);
+  cudaError_t e = cudaFuncSetAttribute(k_conv3_rs<CIN, COUT, UPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+  if (e != cudaSuccess) return e;
+  const long long blocks = (long long)((in.M + 15) / 16) * ((in.N + 3) / 4) * ((in.S + 7) / 8);
+  k_conv3_rs<CIN, COUT, UPC><<<(unsigned)blocks, 256, SMEM, st>>>(in, wt, bias, relu, out);
+  return cudaGetLastError();
+}
+
 template <int CIN, int COUT>
 static cudaError_t conv3_tc_t(cudaStream_t st, const ConvIn& in, const bf16* wu, const float* bias, int relu,
                               bf16* out, int* err) {
@@ -1174,7 +1338,7 @@ static cudaError_t conv3(cudaStream_t st, int cin, int cout, const ConvIn& in, c
                          int relu, bf16* out) {
   // the decoder layers whose first source is upsampled: that source's brick at its own resolution
   if (in.up0 && in.c1 > 0 && in.M % 2 == 0 && in.N % 2 == 0 && in.S % 2 == 0) {
-    if (cin == 48 && cout == 16 && in.c0 == 32) return conv3_t<48, 16, 4, 32>(st, in, wt, bias, relu, out);
+    if (cin == 48 && cout == 16 && in.c0 == 32) return conv3_rs_t<48, 16, 32>(st, in, wt, bias, relu, out);
     if (cin == 96 && cout == 32 && in.c0 == 64) return conv3_t<96, 32, 2, 64>(st, in, wt, bias, relu, out);
   }
 #define SR3D_CONV3(CI, CO, MT_) \
