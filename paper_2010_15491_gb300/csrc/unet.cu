@@ -435,10 +435,10 @@ __global__ void __launch_bounds__(256) k_conv3(ConvIn in, const bf16* __restrict
   }
 }
 
-// Row-stationary variant for the decoder layer whose input is
-// (nearest-upsampled source with UPC channels, 16 full-resolution channels):
-// a 16 (m) x 4 (n) x 8 (s) output brick, each warp the four n rows of one s
-// plane.  The taps run in nine stages (ds, dm); in each, the weight fragments
+// Row-stationary variant for layers with 16 full-resolution input channels,
+// after UPC channels of a nearest-upsampled source (UPC = 0: none; the
+// decoder's 48 -> 16 layer has UPC = 32): a 16 (m) x 4 (n) x 8 (s) output
+// brick, each warp the four n rows of one s plane.  The taps run in nine stages (ds, dm); in each, the weight fragments
 // of the three dn taps sit in registers and each of the warp's six input rows
 // (its four rows and their n halo) is loaded once per channel chunk and feeds
 // every output row it reaches (i = n_in - dn): 9 ldmatrix per 24 MMAs where
@@ -450,10 +450,10 @@ __global__ void __launch_bounds__(256) k_conv3(ConvIn in, const bf16* __restrict
 template <int CIN, int COUT, int UPC>
 __global__ void __launch_bounds__(256) k_conv3_rs(ConvIn in, const bf16* __restrict__ wt,
                                                   const float* __restrict__ bias, int relu, bf16* __restrict__ out) {
-  static_assert(CIN - UPC == 16 && UPC > 0 && UPC % 16 == 0 && COUT % 16 == 0, "16 full-resolution channels");
+  static_assert(CIN - UPC == 16 && UPC % 16 == 0 && COUT % 16 == 0, "16 full-resolution channels");
   constexpr int TM = 16, TN = 4, TS = 8, MT = 4;
   constexpr int HM = TM + 2, HN = TN + 2, HS = TS + 2, HV = HM * HN * HS;
-  constexpr int HMH = TM / 2 + 2, HNH = TN / 2 + 2, HSH = TS / 2 + 2, HVH = HMH * HNH * HSH;
+  constexpr int HMH = TM / 2 + 2, HNH = TN / 2 + 2, HSH = TS / 2 + 2, HVH = UPC > 0 ? HMH * HNH * HSH : 0;
   constexpr int VSTU = UPC * 2 + 16;  // upsampled source rows (padded)
   constexpr int VST = CIN * 2 + 16;   // weight rows (padded)
   constexpr int WSL = COUT * VST;     // one tap's weights
@@ -479,7 +479,7 @@ __global__ void __launch_bounds__(256) k_conv3_rs(ConvIn in, const bf16* __restr
     const bool ok = m >= 0 && m < in.M && n >= 0 && n < in.N && s >= 0 && s < in.S;
     cpz16(halo + hv * 32 + (c ^ ((hv >> 2) & 1)) * 16, ok ? chunk_ptr(in, s, n, m, UPC + c * 8) : in.src0, ok);
   }
-  {
+  if constexpr (UPC > 0) {
     constexpr int CHU = UPC / 8;
     const int Mh = in.M >> 1, Nh = in.N >> 1, Sh = in.S >> 1;
     const int mh0 = (m0 >> 1) - 1, nh0 = (n0 >> 1) - 1, sh0 = (s0 >> 1) - 1;
@@ -1285,7 +1285,7 @@ static cudaError_t conv3_t(cudaStream_t st, const ConvIn& in, const bf16* wt, co
 template <int CIN, int COUT, int UPC>
 static cudaError_t conv3_rs_t(cudaStream_t st, const ConvIn& in, const bf16* wt, const float* bias, int relu,
                               bf16* out) {
-  constexpr int HV = 18 * 6 * 10, HVH = 10 * 4 * 6;
+  constexpr int HV = 18 * 6 * 10, HVH = UPC > 0 ? 10 * 4 * 6 : 0;
   constexpr int SMEM = HV * 32 + HVH * (UPC * 2 + 16) + 2 * 3 * COUT * (CIN * 2 + 16);
   cudaError_t e = cudaFuncSetAttribute(k_conv3_rs<CIN, COUT, UPC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
   if (e != cudaSuccess) return e;
@@ -1340,6 +1340,11 @@ static cudaError_t conv3(cudaStream_t st, int cin, int cout, const ConvIn& in, c
   if (in.up0 && in.c1 > 0 && in.M % 2 == 0 && in.N % 2 == 0 && in.S % 2 == 0) {
     if (cin == 48 && cout == 16 && in.c0 == 32) return conv3_rs_t<48, 16, 32>(st, in, wt, bias, relu, out);
     if (cin == 96 && cout == 32 && in.c0 == 64) return conv3_t<96, 32, 2, 64>(st, in, wt, bias, relu, out);
+  }
+  // one full-resolution source of 16 channels: row-stationary
+  if (!in.up0 && in.c1 == 0 && cin == 16) {
+    if (cout == 16) return conv3_rs_t<16, 16, 0>(st, in, wt, bias, relu, out);
+    if (cout == 32) return conv3_rs_t<16, 32, 0>(st, in, wt, bias, relu, out);
   }
 #define SR3D_CONV3(CI, CO, MT_) \
   if (cin == CI && cout == CO) return conv3_t<CI, CO, MT_>(st, in, wt, bias, relu, out);
